@@ -1,0 +1,114 @@
+"""Pins of the oracle's Green-operator fixed point (Sec. 3, last paragraph) against
+closed forms: homogeneous media, the elastic laminate, the uniaxial modulus and the
+prescribed macroscopic strain."""
+import numpy as np
+import pytest
+
+from oracle import rve_oracle as orc
+
+ELASTIC = dict(r0_ord=1e9, r0_sup=1e9, r0_twin=1e9)
+
+
+def test_homogeneous_strain_control_one_iteration_equals_material_point():
+    gid = np.zeros((4, 4, 6), dtype=np.int64)
+    euler = np.array([[0.4, 1.1, 2.3]])
+    rve = orc.OracleRVE(gid, euler)
+    rate = np.array([-3e-4, -2e-4, 1e-3, 1e-4, 0.0, 2e-4])
+    rve.set_load(orc.Load(Edot=rate, strain_ctrl=np.ones(6, bool), dt=1.0))
+    R = orc.bunge_rotation(euler)
+    ep, v, al, en = np.zeros((1, 3, 3)), np.zeros((1, 16)), np.zeros((1, 12)), np.zeros((1, 3, 3))
+    for k in range(3):
+        rec = rve.step()
+        assert rec["iterations"] == 1 and rec["residual"] < 1e-14
+        e = np.zeros((3, 3))
+        for c, (i, j) in enumerate(orc._MANDEL_IDX):
+            e[i, j] = e[j, i] = rate[c] * (k + 1)
+        sig, ep, v, al = orc.material_point_increment(orc.Material(), R, en, e[None], ep, v, al, 1.0, 8)
+        en = e[None]
+        assert np.allclose(rve.sigma_n, sig[0], rtol=0, atol=1e-12 * np.abs(sig).max())
+    assert rve.history[-1]["mean_v"] > 0  # the homogeneous crystal did flow
+
+
+def test_uniaxial_stress_modulus_single_crystal():
+    """Elastic single crystal with c along z under uniaxial stress: slope 1/S33 = 135385.2 MPa,
+    lateral stresses driven to zero by the mixed-load update."""
+    gid = np.zeros((4, 4, 4), dtype=np.int64)
+    rve = orc.OracleRVE(gid, np.zeros((1, 3)), orc.Material(**ELASTIC), orc.Options(tol=1e-12))
+    rve.set_load(orc.Load(dt=1.0))
+    rec = rve.step()
+    assert abs(rec["S"][2] / rec["E"][2] - 135385.2) < 0.05
+    assert np.max(np.abs(np.delete(rec["S"], 2))) < 1e-9 * rec["S"][2]
+
+
+@pytest.mark.parametrize("scheme", ["willot", "ms"])
+def test_elastic_laminate_closed_form(scheme):
+    """Two orientations in layers normal to z: in-plane strain (11, 22, 12) uniform,
+    traction (33, 13, 23) uniform; with the free mean stresses zero and E33 prescribed
+    this is a 10 x 10 linear system."""
+    nz = 8
+    gid = np.zeros((nz, 4, 4), dtype=np.int64)
+    gid[nz // 2:] = 1
+    euler = np.array([[0.3, 0.9, 1.7], [2.1, 1.2, 0.4]])
+    mat = orc.Material(**ELASTIC)
+    rve = orc.OracleRVE(gid, euler, mat, orc.Options(tol=1e-12, scheme=scheme))
+    rve.set_load(orc.Load(dt=1.0))
+    rec = rve.step()
+    E33 = 1e-3
+    C = orc.stiffness_tensor(mat)
+    Rs = orc.bunge_rotation(euler)
+    Cs = [np.einsum("ia,jb,kc,ld,abcd->ijkl", R, R, R, R, C) for R in Rs]
+    # unknowns: E11 E22 E12 | eA33 eA13 eA23 | eB33 eB13 eB23 | s33
+    def strain(layer, x):
+        e = np.zeros((3, 3))
+        e[0, 0], e[1, 1] = x[0], x[1]
+        e[0, 1] = e[1, 0] = x[2]
+        o = 3 + 3 * layer
+        e[2, 2] = x[o]
+        e[0, 2] = e[2, 0] = x[o + 1]
+        e[1, 2] = e[2, 1] = x[o + 2]
+        return e
+
+    def residual(x):
+        sA = np.einsum("ijkl,kl->ij", Cs[0], strain(0, x))
+        sB = np.einsum("ijkl,kl->ij", Cs[1], strain(1, x))
+        r = []
+        for s in (sA, sB):
+            r += [s[2, 2] - x[9], s[0, 2], s[1, 2]]
+        r.append(0.5 * (x[3] + x[6]) - E33)
+        m = 0.5 * (sA + sB)
+        r += [m[0, 0], m[1, 1], m[0, 1]]
+        return np.array(r)
+
+    A = np.stack([residual(np.eye(10)[i]) - residual(np.zeros(10)) for i in range(10)], axis=1)
+    x = np.linalg.solve(A, -residual(np.zeros(10)))
+    sig = rve.fields()["sigma"]
+    eps = rve.fields()["eps"]
+    for layer, sl in ((0, slice(0, nz // 2)), (1, slice(nz // 2, nz))):
+        e_ref = strain(layer, x)
+        s_ref = np.einsum("ijkl,kl->ij", Cs[layer], e_ref)
+        assert np.allclose(eps[sl], e_ref, atol=1e-13)
+        assert np.allclose(sig[sl], s_ref, atol=1e-8)
+    assert abs(rec["S"][2] - x[9]) < 1e-8
+
+
+def test_mean_strain_is_prescribed_and_stress_constraint_met():
+    rng = np.random.default_rng(9)
+    gid = rng.integers(0, 3, size=(4, 6, 8))
+    euler = rng.uniform(0, 3, size=(3, 3))
+    rve = orc.OracleRVE(gid, euler)
+    rve.set_load(orc.Load(dt=1.0))
+    for _ in range(3):
+        rec = rve.step()
+        eps_mean = rve.eps_n.mean(axis=0)
+        assert abs(eps_mean[2, 2] - rec["E"][2]) < 1e-15
+        assert np.allclose([eps_mean[0, 0], eps_mean[1, 1], eps_mean[1, 2], eps_mean[0, 2], eps_mean[0, 1]],
+                           rec["E"][[0, 1, 3, 4, 5]], atol=1e-15)
+        assert rec["residual"] < 1e-6 and rec["stress_residual"] < 1e-6
+    assert abs(rec["E"][2] - 3e-3) < 1e-15
+
+
+def test_fixed_iteration_mode_counts():
+    gid = np.zeros((4, 4, 4), dtype=np.int64)
+    gid[2:] = 1
+    rve = orc.OracleRVE(gid, np.array([[0.1, 0.2, 0.3], [1.0, 2.0, 0.5]]), opts=orc.Options(fixed_iters=3))
+    assert [r["iterations"] for r in rve.run(2)] == [3, 3]

@@ -1,0 +1,322 @@
+"""Benchmark: voxel-iterations/s of the FFT Green-operator / Meric-Cailletaud fixed point.
+
+Workload (N = 1): the twinned 128^3 RVE -- 200 Voronoi grains, each split into parent
+and twin with probability 0.5 -- in FP32 fields with FP64 norms, uniaxial tension along
+z at 1e-3/s with the other mean stresses held at zero, increments of 0.5 s (the 40
+increments to 2 % of the workload description).  One benchmark step is one load
+increment (all hot-path steps: increment, fixed-point iterations of constitutive update,
+polarisation, forward FFT, Green operator, residual, inverse FFT, mixed-load update,
+commit).  Warm-up steps are the first increments of the loading path; the timed steps
+follow them.  A voxel-iteration is one voxel passing once through one fixed-point
+iteration; the rate counts committed iterations only.
+
+Multi-GPU (torchrun): replicas only -- every rank solves its own realization (seed offset
+by the rank), no data-path collective; value = all ranks' voxel-iterations / max time.
+
+--impl reference times the FP64 CPU oracle (numpy) on a bounded sample of the same
+workload (a 32^3 block of the 128^3 grain map, one fixed-point iteration per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "voxel-iterations/s"
+WORKLOAD = "twinned RVE 128^3, 200 Voronoi grains (p_twin 0.5), FP32 fields + FP64 norms, uniaxial tension 1e-3/s, dt 0.5 s"
+# algorithmic work per voxel-iteration (per-unit figures of the design notes)
+BYTES_PER_VOXIT_FP32 = 260          # state + strain/stress traffic of the fused iteration
+FLOPS_RHS = 1100                    # one evaluation of the constitutive right-hand side
+FP32_LANES_PER_SM, N_SM = 128, 152  # GB300
+
+
+def flops_per_voxit(n_sub):
+    return 4 * n_sub * FLOPS_RHS + 200
+
+
+def aggregate_ranks(dist, work, ms, device="cpu"):
+    """(sum of work over ranks, max of ms over ranks); identity without a process group."""
+    if dist is None:
+        return work, ms
+    import torch
+
+    w = torch.tensor([work], dtype=torch.float64, device=device)
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(w, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(w.item()), float(t.item())
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+
+        backend = os.environ.get("RVE_BENCH_BACKEND", "nccl")
+        dist.init_process_group(backend)
+        return dist, rank, ws
+    return None, 0, 1
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            import tempfile
+
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) >= 9:
+                rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def make_workload(rank):
+    from paper_2402_09996_gb300 import inputs
+
+    inp = inputs.make_inputs((128, 128, 128), 200, 0.5, seed=1000 * 1 + rank)
+    return inp
+
+
+def run_gpu(args):
+    import torch
+
+    from paper_2402_09996_gb300 import build_lib, rve
+
+    dist, rank, ws = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    build_lib.build()
+    inp = make_workload(rank)
+    gid = rve.label_voronoi(inp)
+    dt = 0.5
+    n_sub = 4
+    solver = rve.RVE(gid, inp.euler, precision=rve.FP32, timing=True, n_sub=0)
+    solver.set_mixed_load(dt=dt)
+    nvox = solver.nvox
+    # warm-up: the first increments of the loading path
+    solver.step(args.warmup)
+    solver.kernel_times(reset=True)
+    stream = torch.cuda.current_stream()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    iters = solver.step(args.steps)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = t0.elapsed_time(t1)
+    ktimes = solver.kernel_times()
+    hist = solver.history()
+    solver.close()
+    # aggregate over ranks: total voxel-iterations, max time
+    tot = np.array(aggregate_ranks(dist, float(nvox * iters), ms, device="cuda"))
+    value = tot[0] / (tot[1] * 1e-3)
+
+    # end-to-end through the public API from host buffers: create (H2D of the grain map
+    # and orientations), warm-up + timed increments, effective curve and stress field D2H
+    e2e = None
+    if rank == 0 or True:
+        gid_host = np.ascontiguousarray(np.asarray(gid, dtype=np.uint32))
+        pinned_gid = torch.from_numpy(gid_host.reshape(-1).view(np.int32)).pin_memory()
+        torch.cuda.synchronize()
+        c0 = time.perf_counter()
+        s2 = rve.RVE(pinned_gid.numpy().view(np.uint32).reshape(gid_host.shape), inp.euler, precision=rve.FP32, n_sub=0)
+        s2.set_mixed_load(dt=dt)
+        it2 = s2.step(args.warmup + args.steps)
+        h2 = s2.history()
+        sig = s2.field(rve.FIELD_STRESS)
+        torch.cuda.synchronize()
+        c1 = time.perf_counter()
+        s2.close()
+        n_steps = args.warmup + args.steps
+        e2e = {"value": nvox * it2 / (c1 - c0), "unit": METRIC,
+               "h2d_bytes_per_step": int((gid_host.nbytes + inp.euler.nbytes) / n_steps),
+               "d2h_bytes_per_step": int((sig.nbytes + len(h2) * 160) / n_steps),
+               "what": f"create from host grain map + {n_steps} increments from rest + stress field to host"}
+    if rank != 0:
+        return
+    # roofline of the dominant kernel (x pass: constitutive update fused with the x-FFTs)
+    kx_ms, kx_n = ktimes["xpass"]
+    avg = kx_ms / max(kx_n, 1)
+    flops = flops_per_voxit(n_sub) * nvox
+    peak_mhz = 2070.0
+    peak = FP32_LANES_PER_SM * N_SM * 2 * peak_mhz * 1e6 / 1e12
+    achieved = flops / (avg * 1e-3) / 1e12
+    launches = int(sum(n for _, n in ktimes.values()))
+    total_k_ms = sum(m for m, _ in ktimes.values())
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": METRIC,
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": tot[1] / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "voxels": nvox, "grains": int(inp.n_grains),
+                   "increments_timed": f"{args.warmup + 1}..{args.warmup + args.steps}",
+                   "fixed_point_iterations_timed": int(iters), "n_sub": n_sub,
+                   "l2": "inputs larger than L2 (per-iteration state ~390 MB)",
+                   "parallelism": f"replicas x{ws}"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "k_xpass", "avg_launch_ms": avg,
+                     "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz"},
+        "kernel_share": {k: round(m / total_k_ms, 4) for k, (m, _) in ktimes.items() if total_k_ms > 0},
+        "kernel_avg_ms": {k: (m / n if n else None) for k, (m, n) in ktimes.items()},
+        "hbm": {"bytes_per_voxit": BYTES_PER_VOXIT_FP32, "achieved_gbs": BYTES_PER_VOXIT_FP32 * value / 1e9,
+                "peak_gbs_measured": _measured_hbm()},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "e2e": e2e,
+        "effective_last": {"E33": hist[-1]["E"][2], "S33": hist[-1]["S"][2], "iterations": hist[-1]["iterations"]},
+    }
+    if not args.no_cpu_baseline and ws == 1:
+        line["cpu_baseline"] = cpu_baseline(seconds=args.cpu_seconds)
+    print(json.dumps(line))
+
+
+def _measured_hbm():
+    try:
+        return json.load(open(ROOT / "MEASURED_PEAKS.json"))["hbm_gbs"]
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def _oracle_sample():
+    """A 32^3 block of the 128^3 workload's grain map (ids compacted), as a periodic RVE."""
+    from oracle.rve_oracle import Material, OracleRVE, Options, Load
+    from oracle.voronoi import voronoi_labels
+
+    inp = make_workload(0)
+    n = 32
+    k, j, i = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    vox = (i + 128 * (j + 128 * k)).reshape(-1)
+    parents = voronoi_labels(inp.shape, inp.seeds, voxels=vox).reshape(n, n, n)
+    ids, gid = np.unique(parents, return_inverse=True)
+    rve = OracleRVE(gid.reshape(n, n, n), inp.euler[ids], Material(), Options(fixed_iters=1))
+    rve.set_load(Load(dt=0.5))
+    return rve
+
+
+def cpu_baseline(seconds=20.0, steps=None):
+    """The oracle as it stands on a bounded sample: fixed-point iterations of a 32^3 block."""
+    rve = _oracle_sample()
+    done = 0
+    t0 = time.perf_counter()
+    while True:
+        rve.step()
+        done += 1
+        el = time.perf_counter() - t0
+        if (steps is not None and done >= steps) or (steps is None and el > seconds):
+            break
+    value = rve.N * done / el
+    return {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": f"{done} fixed-point iterations (one increment each) of a 32^3 block of the 128^3 grain map, "
+                      f"numpy FP64, {el:.1f} s"}
+
+
+def run_reference(args):
+    dist, rank, ws = _dist()
+    if rank != 0:
+        return
+    rve = _oracle_sample()
+    for _ in range(args.warmup):
+        rve.step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        rve.step()
+    el = time.perf_counter() - t0
+    value = rve.N * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": "32^3 block of the 128^3 grain map, one fixed-point "
+                                                     "iteration per step"},
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} iterations of a 32^3 block"},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=15)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    return args
+
+
+def main():
+    args = main_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

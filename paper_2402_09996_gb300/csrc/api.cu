@@ -1,0 +1,1078 @@
+// C ABI and host-side driver of the Green-operator fixed-point solver.
+//
+// The increment loop (paper Sec. 5: quasi-static strain steps) runs on the host; each
+// fixed-point iteration is four kernel launches on the handle's stream (see
+// solver_kernels.cuh) followed by one read of a small status record.  All arithmetic on
+// fields happens in the kernels; the host only forms the 6-component macroscopic
+// increment and decides convergence from values the kernels computed in FP64.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/rve.h"
+#include "launch.h"
+#include "solver_kernels.cuh"
+
+using namespace rve;
+
+namespace {
+
+thread_local std::string g_err;
+
+constexpr double kPi = 3.14159265358979323846;
+const double kMw[6] = {1.0, 1.0, 1.0, 1.41421356237309504880, 1.41421356237309504880, 1.41421356237309504880};
+
+bool factor_radices(int n, FftDim* d) {
+  if (n < 1 || n > 512) return false;
+  d->n = n;
+  d->nst = 0;
+  int m = n;
+  while (m % 4 == 0) { d->radix[d->nst++] = 4; m /= 4; }
+  while (m % 2 == 0) { d->radix[d->nst++] = 2; m /= 2; }
+  while (m % 3 == 0) { d->radix[d->nst++] = 3; m /= 3; }
+  while (m % 5 == 0) { d->radix[d->nst++] = 5; m /= 5; }
+  return m == 1 && d->nst <= 12;
+}
+
+// Jacobi eigenvalues of a symmetric 6x6 matrix (host, for the reference medium).
+void sym_eigvals6(const double A_in[36], double ev[6]) {
+  double A[36];
+  std::memcpy(A, A_in, sizeof(A));
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0;
+    for (int p = 0; p < 6; ++p)
+      for (int q = p + 1; q < 6; ++q) off += A[p * 6 + q] * A[p * 6 + q];
+    if (off < 1e-30) break;
+    for (int p = 0; p < 6; ++p)
+      for (int q = p + 1; q < 6; ++q) {
+        const double apq = A[p * 6 + q];
+        if (std::fabs(apq) < 1e-300) continue;
+        const double theta = (A[q * 6 + q] - A[p * 6 + p]) / (2.0 * apq);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < 6; ++k) {
+          const double akp = A[k * 6 + p], akq = A[k * 6 + q];
+          A[k * 6 + p] = c * akp - s * akq;
+          A[k * 6 + q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < 6; ++k) {
+          const double apk = A[p * 6 + k], aqk = A[q * 6 + k];
+          A[p * 6 + k] = c * apk - s * aqk;
+          A[q * 6 + k] = s * apk + c * aqk;
+        }
+      }
+  }
+  for (int i = 0; i < 6; ++i) ev[i] = A[i * 6 + i];
+}
+
+// In-place inverse of an n x n matrix (Gauss-Jordan with partial pivoting).
+bool invert(double* M, int n) {
+  std::vector<double> a(M, M + n * n), inv(n * n, 0.0);
+  for (int i = 0; i < n; ++i) inv[i * n + i] = 1.0;
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(a[r * n + c]) > std::fabs(a[piv * n + c])) piv = r;
+    if (std::fabs(a[piv * n + c]) < 1e-300) return false;
+    if (piv != c)
+      for (int k = 0; k < n; ++k) {
+        std::swap(a[c * n + k], a[piv * n + k]);
+        std::swap(inv[c * n + k], inv[piv * n + k]);
+      }
+    const double d = a[c * n + c];
+    for (int k = 0; k < n; ++k) {
+      a[c * n + k] /= d;
+      inv[c * n + k] /= d;
+    }
+    for (int r = 0; r < n; ++r)
+      if (r != c) {
+        const double f = a[r * n + c];
+        if (f == 0.0) continue;
+        for (int k = 0; k < n; ++k) {
+          a[r * n + k] -= f * a[c * n + k];
+          inv[r * n + k] -= f * inv[c * n + k];
+        }
+      }
+  }
+  std::memcpy(M, inv.data(), sizeof(double) * n * n);
+  return true;
+}
+
+void bunge(const double* e, double R[9]) {
+  const double c1 = std::cos(e[0]), s1 = std::sin(e[0]);
+  const double c = std::cos(e[1]), s = std::sin(e[1]);
+  const double c2 = std::cos(e[2]), s2 = std::sin(e[2]);
+  // Rz(phi1) Rx(Phi) Rz(phi2), crystal -> sample
+  R[0] = c1 * c2 - s1 * c * s2;
+  R[1] = -c1 * s2 - s1 * c * c2;
+  R[2] = s1 * s;
+  R[3] = s1 * c2 + c1 * c * s2;
+  R[4] = -s1 * s2 + c1 * c * c2;
+  R[5] = -c1 * s;
+  R[6] = s * s2;
+  R[7] = s * c2;
+  R[8] = c;
+}
+
+// Isotropic reference medium: 3 k0 = 2 mu0 = (min + max Mandel eigenvalue of C) / 2.
+void reference_medium(const rve_material& m, double* lam0, double* mu0) {
+  double A[36] = {0};
+  A[0] = A[7] = m.C11;
+  A[14] = m.C33;
+  A[1] = A[6] = m.C12;
+  A[2] = A[12] = A[8] = A[13] = m.C13;
+  A[21] = 2.0 * m.C44;
+  A[28] = 2.0 * m.C44;
+  A[35] = 2.0 * m.C66;
+  double ev[6];
+  sym_eigvals6(A, ev);
+  const double lo = *std::min_element(ev, ev + 6), hi = *std::max_element(ev, ev + 6);
+  const double two_mu = 0.5 * (lo + hi);
+  *mu0 = 0.5 * two_mu;
+  *lam0 = two_mu / 3.0 - 2.0 * (*mu0) / 3.0;
+}
+
+void c0_mandel(double lam, double mu, double M[36]) {
+  std::memset(M, 0, 36 * sizeof(double));
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) M[i * 6 + j] = lam + (i == j ? 2.0 * mu : 0.0);
+  for (int i = 3; i < 6; ++i) M[i * 6 + i] = 2.0 * mu;
+}
+
+int is_small_int(double x) {
+  const double r = std::round(x);
+  return (std::fabs(x - r) == 0.0 && r >= 1.0 && r <= 64.0) ? (int)r : 0;
+}
+
+// m = 1 / log2(1/u1) with u1^n + u1 = 1 (bisection): the exponent that makes the
+// smooth minimum (1 + beta^m)^(-1/m) exact at beta = 1 for the rate root's start.
+double smooth_min_exponent(double n) {
+  double lo = 0.0, hi = 1.0;
+  for (int i = 0; i < 200; ++i) {
+    const double mid = 0.5 * (lo + hi);
+    if (std::pow(mid, n) + mid - 1.0 > 0.0) hi = mid;
+    else lo = mid;
+  }
+  return 1.0 / std::log2(1.0 / (0.5 * (lo + hi)));
+}
+
+int default_nsub(double dt) {
+  int n = 1;
+  while (dt / n > 0.125 * (1.0 + 1e-12) && n < (1 << 20)) n *= 2;
+  return n;
+}
+
+}  // namespace
+
+struct rve_s {
+  int nx = 0, ny = 0, nz = 0, H = 0;
+  long long nvox = 0, NL = 0;
+  int n_grains = 0;
+  rve_options opt{};
+  rve_material mat{};
+  double Edot[6] = {0, 0, 1e-3, 0, 0, 0};
+  uint8_t ctrl[6] = {0, 0, 1, 0, 0, 0};
+  double Sigma[6] = {0, 0, 0, 0, 0, 0};
+  double dt = 1.0;
+  cudaStream_t stream = nullptr;
+  int tsize = 8;
+  FftDim dx{}, dy{}, dz{};
+  std::vector<double> euler;
+  // device buffers
+  void *spec_cur = nullptr, *spec_nxt = nullptr, *P_prev = nullptr, *P_scr = nullptr, *backup = nullptr;
+  void *ep = nullptr, *v = nullptr, *al = nullptr, *eps_n = nullptr, *sig_n = nullptr;
+  uint32_t* grain = nullptr;
+  void* Rg = nullptr;
+  void *tw_x = nullptr, *tw_y = nullptr, *tw_z = nullptr;
+  void *kx = nullptr, *ky = nullptr, *kz = nullptr;
+  double* partial = nullptr;
+  unsigned int* counter = nullptr;
+  IterStatus* st = nullptr;
+  IterStatus* st_host = nullptr;  // pinned
+  std::vector<void*> owned;
+  // launch geometry
+  int L = 1, xgrid = 0;
+  size_t xsmem = 0, ysmem = 0, zsmem = 0;
+  int yHC = 1, zHC = 1;
+  double lam0 = 0, mu0 = 0;
+  // host state
+  double E_n[6] = {0}, E_prev[6] = {0};
+  double time = 0.0;
+  int increment = 0;
+  std::vector<rve_effective> hist;
+  std::string err;
+  // optional per-kernel event timing
+  cudaEvent_t ev_a[RVE_K_COUNT] = {}, ev_b[RVE_K_COUNT] = {};
+  bool ev_used[RVE_K_COUNT] = {};
+  double k_ms[RVE_K_COUNT] = {};
+  long long k_n[RVE_K_COUNT] = {};
+  std::vector<double> res_e, res_c;  // convergence history of the latest increment
+};
+
+namespace {
+
+rve_status fail(rve_s* h, rve_status s, const std::string& msg) {
+  if (h) h->err = msg;
+  g_err = msg;
+  return s;
+}
+
+rve_status cuda_fail(rve_s* h, cudaError_t e, const char* where) {
+  return fail(h, RVE_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define RVE_CUDA(h, call)                                   \
+  do {                                                      \
+    cudaError_t _e = (call);                                \
+    if (_e != cudaSuccess) return cuda_fail((h), _e, #call); \
+  } while (0)
+
+rve_status dalloc(rve_s* h, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (h->opt.alloc) {
+    *p = h->opt.alloc(bytes, h->opt.alloc_ctx);
+    if (!*p) return fail(h, RVE_ERR_OOM, "allocator callback returned NULL");
+  } else {
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, RVE_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+  }
+  h->owned.push_back(*p);
+  return RVE_OK;
+}
+
+void tstart(rve_s* h, int k) {
+  if (h->opt.timing) cudaEventRecord(h->ev_a[k], h->stream);
+}
+void tstop(rve_s* h, int k) {
+  if (!h->opt.timing) return;
+  cudaEventRecord(h->ev_b[k], h->stream);
+  h->ev_used[k] = true;
+}
+// After a stream synchronisation: fold the recorded launches into the totals.
+void tcollect(rve_s* h) {
+  if (!h->opt.timing) return;
+  for (int k = 0; k < RVE_K_COUNT; ++k)
+    if (h->ev_used[k]) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, h->ev_a[k], h->ev_b[k]) == cudaSuccess) {
+        h->k_ms[k] += ms;
+        h->k_n[k] += 1;
+      }
+      h->ev_used[k] = false;
+    }
+}
+
+void release(rve_s* h) {
+  for (int k = 0; k < RVE_K_COUNT; ++k) {
+    if (h->ev_a[k]) cudaEventDestroy(h->ev_a[k]);
+    if (h->ev_b[k]) cudaEventDestroy(h->ev_b[k]);
+    h->ev_a[k] = h->ev_b[k] = nullptr;
+  }
+  for (void* p : h->owned) {
+    if (h->opt.free) h->opt.free(p, h->opt.alloc_ctx);
+    else cudaFree(p);
+  }
+  h->owned.clear();
+  if (h->st_host) cudaFreeHost(h->st_host);
+  h->st_host = nullptr;
+}
+
+template <typename T>
+MatDev<T> make_mat(const rve_s* h) {
+  const rve_material& m = h->mat;
+  MatDev<T> M;
+  M.C11 = (T)m.C11; M.C12 = (T)m.C12; M.C13 = (T)m.C13; M.C33 = (T)m.C33; M.C44 = (T)m.C44; M.C66 = (T)m.C66;
+  const char kinds[12] = {'s', 's', 'o', 's', 's', 'o', 's', 's', 'o', 's', 's', 'o'};
+  for (int s = 0; s < 12; ++s) M.r0[s] = (T)(kinds[s] == 'o' ? m.r0_ord : m.r0_sup);
+  for (int s = 12; s < 16; ++s) M.r0[s] = (T)m.r0_twin;
+  M.K = (T)m.K; M.n = (T)m.n; M.Kt = (T)m.Kt; M.nt = (T)m.nt;
+  M.Q_s = (T)m.Q_s; M.Q_b = (T)m.Q_b; M.b_s = (T)m.b_s; M.b_b = (T)m.b_b;
+  M.h_diag = (T)m.h_diag; M.h_off = (T)m.h_off; M.c = (T)m.c; M.d = (T)m.d;
+  M.Kc = (T)m.Kc; M.fm = (T)m.fm; M.eta = (T)m.eta;
+  M.n_int = is_small_int(m.n);
+  M.nt_int = is_small_int(m.nt);
+  M.lam0 = (T)h->lam0;
+  M.mu0 = (T)h->mu0;
+  M.inv_n = (T)(1.0 / m.n);
+  M.inv_nt = (T)(1.0 / m.nt);
+  M.sm = (T)smooth_min_exponent(m.n);
+  M.smt = (T)smooth_min_exponent(m.nt);
+  M.lg_K = (T)std::log2(m.K);
+  M.lg_Kt = (T)std::log2(m.Kt);
+  M.lg_eta = (T)(m.eta > 0 ? std::log2(m.eta) : 0.0);
+  return M;
+}
+
+rve_status check_material(rve_s* h, const rve_material& m) {
+  const double vals[] = {m.C11, m.C12, m.C13, m.C33, m.C44, m.C66, m.r0_ord, m.r0_sup, m.r0_twin, m.K, m.n, m.Kt,
+                         m.nt, m.Q_s, m.Q_b, m.b_s, m.b_b, m.h_diag, m.h_off, m.c, m.d, m.Kc, m.fm, m.eta};
+  for (double x : vals)
+    if (!std::isfinite(x)) return fail(h, RVE_ERR_INVALID_ARG, "material constant is not finite");
+  if (m.K <= 0 || m.Kt <= 0 || m.n < 1 || m.nt < 1 || m.eta < 0)
+    return fail(h, RVE_ERR_INVALID_ARG, "need K, Kt > 0, n, nt >= 1 and eta >= 0");
+  // positive definite stiffness: the Mandel eigenvalues must be positive
+  double A[36] = {0};
+  A[0] = A[7] = m.C11;
+  A[14] = m.C33;
+  A[1] = A[6] = m.C12;
+  A[2] = A[12] = A[8] = A[13] = m.C13;
+  A[21] = A[28] = 2.0 * m.C44;
+  A[35] = 2.0 * m.C66;
+  double ev[6];
+  sym_eigvals6(A, ev);
+  for (double e : ev)
+    if (!(e > 0)) return fail(h, RVE_ERR_INVALID_ARG, "elastic stiffness is not positive definite");
+  return RVE_OK;
+}
+
+template <typename T>
+rve_status upload_tables(rve_s* h) {
+  // twiddles e^{-2 pi i m / n}
+  auto tw = [&](int n, void** dst) -> rve_status {
+    std::vector<T> t(2 * n);
+    for (int m = 0; m < n; ++m) {
+      const double a = 2.0 * kPi * (double)m / (double)n;
+      t[2 * m] = (T)std::cos(a);
+      t[2 * m + 1] = (T)(-std::sin(a));
+    }
+    rve_status s = dalloc(h, dst, t.size() * sizeof(T));
+    if (s) return s;
+    RVE_CUDA(h, cudaMemcpyAsync(*dst, t.data(), t.size() * sizeof(T), cudaMemcpyHostToDevice, h->stream));
+    RVE_CUDA(h, cudaStreamSynchronize(h->stream));
+    return RVE_OK;
+  };
+  rve_status s;
+  if ((s = tw(h->nx, &h->tw_x))) return s;
+  if ((s = tw(h->ny, &h->tw_y))) return s;
+  if ((s = tw(h->nz, &h->tw_z))) return s;
+  // wave-vector tables per dimension
+  auto kt = [&](int n, int count, void** dst) -> rve_status {
+    std::vector<T> t(2 * count);
+    for (int i = 0; i < count; ++i) {
+      if (h->opt.green == RVE_GREEN_WILLOT) {
+        // sin and cos of pi i / n, exact at the Nyquist index (cos = 0, so kappa vanishes
+        // where two or more components sit at Nyquist)
+        const double a = kPi * (double)i / (double)n;
+        t[2 * i] = (T)(2 * i == n ? 1.0 : std::sin(a));
+        t[2 * i + 1] = (T)(2 * i == n ? 0.0 : std::cos(a));
+      } else {
+        double f = (i <= n / 2) ? (double)i : (double)(i - n);
+        if (n % 2 == 0 && i == n / 2) f = 0.0;
+        t[2 * i] = (T)(2.0 * kPi * f / (double)n);
+        t[2 * i + 1] = (T)0;
+      }
+    }
+    rve_status s2 = dalloc(h, dst, t.size() * sizeof(T));
+    if (s2) return s2;
+    RVE_CUDA(h, cudaMemcpyAsync(*dst, t.data(), t.size() * sizeof(T), cudaMemcpyHostToDevice, h->stream));
+    RVE_CUDA(h, cudaStreamSynchronize(h->stream));
+    return RVE_OK;
+  };
+  if ((s = kt(h->nx, h->H, &h->kx))) return s;
+  if ((s = kt(h->ny, h->ny, &h->ky))) return s;
+  if ((s = kt(h->nz, h->nz, &h->kz))) return s;
+  // per-grain rotations
+  std::vector<T> Rg((size_t)h->n_grains * 9);
+  for (int g = 0; g < h->n_grains; ++g) {
+    double R[9];
+    bunge(&h->euler[3 * g], R);
+    for (int i = 0; i < 9; ++i) Rg[(size_t)g * 9 + i] = (T)R[i];
+  }
+  if ((s = dalloc(h, &h->Rg, Rg.size() * sizeof(T)))) return s;
+  RVE_CUDA(h, cudaMemcpyAsync(h->Rg, Rg.data(), Rg.size() * sizeof(T), cudaMemcpyHostToDevice, h->stream));
+  RVE_CUDA(h, cudaStreamSynchronize(h->stream));
+  return RVE_OK;
+}
+
+template <typename T>
+rve_status alloc_fields(rve_s* h) {
+  const size_t spec = (size_t)6 * h->NL * h->H * 2 * sizeof(T);
+  const size_t fld = (size_t)h->nvox * sizeof(T);
+  rve_status s;
+  void** bufs[] = {&h->spec_cur, &h->spec_nxt, &h->P_prev, &h->P_scr};
+  for (void** b : bufs) {
+    if ((s = dalloc(h, b, spec))) return s;
+    RVE_CUDA(h, cudaMemsetAsync(*b, 0, spec, h->stream));
+  }
+  if ((s = dalloc(h, &h->backup, (size_t)6 * h->NL * 2 * sizeof(T)))) return s;
+  struct {
+    void** p;
+    int comps;
+  } fl[] = {{&h->ep, 6}, {&h->v, 16}, {&h->al, 12}, {&h->eps_n, 6}, {&h->sig_n, 6}};
+  for (auto& f : fl) {
+    if ((s = dalloc(h, f.p, fld * f.comps))) return s;
+    RVE_CUDA(h, cudaMemsetAsync(*f.p, 0, fld * f.comps, h->stream));
+  }
+  // launch geometry
+  h->L = std::max(1, x_threads() / h->nx);
+  h->xgrid = (int)((h->NL + h->L - 1) / h->L);
+  h->xsmem = (size_t)(h->nx + 6 * h->L * h->nx) * 2 * sizeof(T);
+  const size_t budget = 96 * 1024;
+  h->yHC = (int)std::max<size_t>(1, std::min<size_t>(16, (budget / (2 * 2 * sizeof(T))) / h->ny));
+  h->yHC = std::min(h->yHC, h->H);
+  h->ysmem = (size_t)(h->ny + 2 * h->yHC * (h->ny + 1)) * 2 * sizeof(T);
+  h->zHC = (int)std::max<size_t>(1, std::min<size_t>(16, (budget / (2 * 2 * sizeof(T) * 6)) / h->nz));
+  h->zHC = std::min(h->zHC, h->H);
+  h->zsmem = (size_t)(h->nz + 12 * h->zHC * (h->nz + 1)) * 2 * sizeof(T);
+  const int zgrid = ((h->H + h->zHC - 1) / h->zHC) * h->ny;
+  const int maxgrid = std::max(h->xgrid, zgrid);
+  if ((s = dalloc(h, (void**)&h->partial, (size_t)maxgrid * kNumRed * sizeof(double)))) return s;
+  if ((s = dalloc(h, (void**)&h->counter, 64))) return s;
+  RVE_CUDA(h, cudaMemsetAsync(h->counter, 0, 64, h->stream));
+  if ((s = dalloc(h, (void**)&h->st, sizeof(IterStatus)))) return s;
+  RVE_CUDA(h, cudaMemsetAsync(h->st, 0, sizeof(IterStatus), h->stream));
+  RVE_CUDA(h, cudaMallocHost((void**)&h->st_host, sizeof(IterStatus)));
+  return RVE_OK;
+}
+
+template <typename T>
+XArgs<T> x_args(rve_s* h, const void* in, void* out, int it) {
+  XArgs<T> a;
+  a.nx = h->nx; a.ny = h->ny; a.nz = h->nz; a.H = h->H; a.L = h->L;
+  a.nvox = h->nvox;
+  a.dx = h->dx;
+  a.tw = (const C2<T>*)h->tw_x;
+  a.spec_in = (const C2<T>*)in;
+  a.spec_out = (C2<T>*)out;
+  a.ep = (T*)h->ep; a.v = (T*)h->v; a.al = (T*)h->al; a.eps_n = (T*)h->eps_n; a.sig_n = (T*)h->sig_n;
+  a.grain = h->grain;
+  a.Rg = (const T*)h->Rg;
+  a.M = make_mat<T>(h);
+  // mixed load
+  double M0[36];
+  c0_mandel(h->lam0, h->mu0, M0);
+  std::memset(&a.ld, 0, sizeof(a.ld));
+  int fi[6], nf = 0;
+  for (int c = 0; c < 6; ++c) {
+    a.ld.free_mask[c] = h->ctrl[c] ? 0 : 1;
+    a.ld.Sigma_m[c] = h->Sigma[c] * kMw[c];
+    if (!h->ctrl[c]) fi[nf++] = c;
+  }
+  a.ld.any_free = nf > 0;
+  if (nf > 0) {
+    std::vector<double> Mff(nf * nf);
+    for (int i = 0; i < nf; ++i)
+      for (int j = 0; j < nf; ++j) Mff[i * nf + j] = M0[fi[i] * 6 + fi[j]];
+    invert(Mff.data(), nf);
+    for (int i = 0; i < nf; ++i)
+      for (int j = 0; j < nf; ++j) a.ld.Minv[fi[i] * 6 + fi[j]] = Mff[i * nf + j];
+  }
+  a.dt = (T)h->dt;
+  a.nsub = h->opt.n_sub > 0 ? h->opt.n_sub : default_nsub(h->dt);
+  a.partial = h->partial;
+  a.counter = h->counter;
+  a.st = h->st;
+  a.it = it;
+  return a;
+}
+
+template <typename T>
+LineArgs<T> y_args(rve_s* h, void* spec) {
+  LineArgs<T> a;
+  a.d = h->dy;
+  a.tw = (const C2<T>*)h->tw_y;
+  a.spec = (C2<T>*)spec;
+  a.H = h->H;
+  a.HC = h->yHC;
+  a.n_o2 = h->nz;
+  a.stride = h->H;
+  a.A = (long long)h->nz * h->ny * h->H;
+  a.B = (long long)h->ny * h->H;
+  return a;
+}
+
+template <typename T>
+ZArgs<T> z_args(rve_s* h, void* spec, const void* Pp, void* Po, int it) {
+  ZArgs<T> a;
+  a.nx = h->nx; a.ny = h->ny; a.nz = h->nz; a.H = h->H; a.HC = h->zHC;
+  a.nvox = h->nvox;
+  a.dz = h->dz;
+  a.tw = (const C2<T>*)h->tw_z;
+  a.spec = (C2<T>*)spec;
+  a.P_prev = (const C2<T>*)Pp;
+  a.P_out = (C2<T>*)Po;
+  a.kx = (const T*)h->kx;
+  a.ky = (const T*)h->ky;
+  a.kzt = (const T*)h->kz;
+  a.scheme = h->opt.green;
+  a.lam0 = (T)h->lam0;
+  a.mu0 = (T)h->mu0;
+  a.invN = (T)(1.0 / (double)h->nvox);
+  a.partial = h->partial;
+  a.counter = h->counter;
+  a.st = h->st;
+  a.it = it;
+  return a;
+}
+
+double vm_of(const double* s) {
+  const double p = (s[0] + s[1] + s[2]) / 3.0;
+  const double a = s[0] - p, b = s[1] - p, c = s[2] - p;
+  return std::sqrt(1.5 * (a * a + b * b + c * c + 2.0 * (s[3] * s[3] + s[4] * s[4] + s[5] * s[5])));
+}
+
+// a1: macroscopic increment and initial guess (first increment: C0-consistent free
+// components; later ones: the previous increment's macroscopic step).
+void initial_increment(rve_s* h, double dE0[6]) {
+  int fi[6], ci[6], nf = 0, nc = 0;
+  for (int c = 0; c < 6; ++c) (h->ctrl[c] ? ci[nc++] : fi[nf++]) = c;
+  if (h->increment == 0) {
+    double dm[6] = {0};
+    for (int c = 0; c < 6; ++c) dm[c] = h->ctrl[c] ? h->Edot[c] * h->dt * kMw[c] : 0.0;
+    if (nf > 0) {
+      double M0[36];
+      c0_mandel(h->lam0, h->mu0, M0);
+      std::vector<double> Mff(nf * nf);
+      for (int i = 0; i < nf; ++i)
+        for (int j = 0; j < nf; ++j) Mff[i * nf + j] = M0[fi[i] * 6 + fi[j]];
+      invert(Mff.data(), nf);
+      double rhs[6] = {0};
+      for (int i = 0; i < nf; ++i)
+        for (int j = 0; j < nc; ++j) rhs[i] += M0[fi[i] * 6 + ci[j]] * dm[ci[j]];
+      for (int i = 0; i < nf; ++i) {
+        double x = 0.0;
+        for (int j = 0; j < nf; ++j) x += Mff[i * nf + j] * rhs[j];
+        dm[fi[i]] = -x;
+      }
+    }
+    for (int c = 0; c < 6; ++c) dE0[c] = dm[c] / kMw[c];
+  } else {
+    for (int c = 0; c < 6; ++c) dE0[c] = h->ctrl[c] ? h->Edot[c] * h->dt : h->E_n[c] - h->E_prev[c];
+  }
+}
+
+template <typename T>
+rve_status step_one(rve_s* h, long long* iters) {
+  cudaStream_t s = h->stream;
+  double dE0[6];
+  initial_increment(h, dE0);
+  // E^(0) into slot 0 of the device status record
+  for (int c = 0; c < 6; ++c) h->st_host->E[0][c] = h->E_n[c] + dE0[c];
+  h->st_host->nan_flag = 0;
+  RVE_CUDA(h, cudaMemcpyAsync(h->st->E[0], h->st_host->E[0], 6 * sizeof(double), cudaMemcpyHostToDevice, s));
+  RVE_CUDA(h, cudaMemsetAsync(&h->st->nan_flag, 0, sizeof(int), s));
+  tstart(h, RVE_K_SHIFT);
+  RVE_CUDA(h, launch_shift<T>((C2<T>*)h->spec_cur, (C2<T>*)h->backup, h->NL, h->H, dE0, false, s));
+  tstop(h, RVE_K_SHIFT);
+  h->res_e.clear();
+  h->res_c.clear();
+  const int zgrid_x = (h->H + h->zHC - 1) / h->zHC;
+  const int ygrid_x = (h->H + h->yHC - 1) / h->yHC;
+  const int max_iter = h->opt.max_iter > 0 ? h->opt.max_iter : 1000;
+  for (int it = 0;; ++it) {
+    XArgs<T> xa = x_args<T>(h, h->spec_cur, h->spec_nxt, it);
+    tstart(h, RVE_K_XPASS);
+    RVE_CUDA(h, launch_xpass<T>(xa, false, h->xgrid, h->xsmem, s));
+    tstop(h, RVE_K_XPASS);
+    LineArgs<T> ya = y_args<T>(h, h->spec_nxt);
+    tstart(h, RVE_K_YFWD);
+    RVE_CUDA(h, launch_line<T>(ya, -1, dim3(ygrid_x, 6 * h->nz), h->ysmem, s));
+    tstop(h, RVE_K_YFWD);
+    ZArgs<T> za = z_args<T>(h, h->spec_nxt, h->P_prev, h->P_scr, it);
+    tstart(h, RVE_K_ZGREEN);
+    RVE_CUDA(h, launch_zgreen<T>(za, dim3(zgrid_x, h->ny), h->zsmem, s));
+    tstop(h, RVE_K_ZGREEN);
+    tstart(h, RVE_K_YINV);
+    RVE_CUDA(h, launch_line<T>(ya, +1, dim3(ygrid_x, 6 * h->nz), h->ysmem, s));
+    tstop(h, RVE_K_YINV);
+    RVE_CUDA(h, cudaMemcpyAsync(h->st_host, h->st, sizeof(IterStatus), cudaMemcpyDeviceToHost, s));
+    RVE_CUDA(h, cudaStreamSynchronize(s));
+    tcollect(h);
+    const IterStatus& st = *h->st_host;
+    h->res_e.push_back(st.e_eq);
+    h->res_c.push_back(st.cF);
+    if (st.nan_flag) {
+      RVE_CUDA(h, launch_shift<T>((C2<T>*)h->spec_cur, (C2<T>*)h->backup, h->NL, h->H, dE0, true, s));
+      RVE_CUDA(h, cudaStreamSynchronize(s));
+      return fail(h, RVE_ERR_NAN, std::string("NaN or Inf in the ") +
+                                      ((st.nan_flag & 1) ? "mean stress" : "equilibrium residual") + " at increment " +
+                                      std::to_string(h->increment + 1) + ", iteration " + std::to_string(it));
+    }
+    const bool conv = h->opt.fixed_iters > 0 ? (it + 1 >= h->opt.fixed_iters)
+                                             : (st.e_eq < h->opt.tol && st.cF < h->opt.tol);
+    if (conv) {
+      const double e_eq = st.e_eq, cF = st.cF;
+      double E[6];
+      for (int c = 0; c < 6; ++c) E[c] = st.E[it & 1][c];
+      XArgs<T> ca = x_args<T>(h, h->spec_cur, nullptr, it);
+      tstart(h, RVE_K_COMMIT);
+      RVE_CUDA(h, launch_xpass<T>(ca, true, h->xgrid, h->xsmem, s));
+      tstop(h, RVE_K_COMMIT);
+      RVE_CUDA(h, cudaMemcpyAsync(h->st_host, h->st, sizeof(IterStatus), cudaMemcpyDeviceToHost, s));
+      RVE_CUDA(h, cudaStreamSynchronize(s));
+      tcollect(h);
+      for (int c = 0; c < 6; ++c) {
+        h->E_prev[c] = h->E_n[c];
+        h->E_n[c] = E[c];
+      }
+      h->time += h->dt;
+      h->increment += 1;
+      rve_effective r;
+      std::memset(&r, 0, sizeof(r));
+      r.increment = h->increment;
+      r.iterations = it + 1;
+      r.time = h->time;
+      for (int c = 0; c < 6; ++c) {
+        r.E[c] = E[c];
+        r.S[c] = h->st_host->sig_mean[c];
+      }
+      r.S_eq_of_mean = vm_of(r.S);
+      r.mean_S_eq = h->st_host->eff[0];
+      r.mean_f = h->st_host->eff[1];
+      r.mean_v = h->st_host->eff[2];
+      r.residual = e_eq;
+      r.stress_residual = cF;
+      h->hist.push_back(r);
+      if (iters) *iters += it + 1;
+      if (h->st_host->nan_flag) return fail(h, RVE_ERR_NAN, "NaN or Inf in the committed fields");
+      return RVE_OK;
+    }
+    if (it + 1 >= max_iter) {
+      RVE_CUDA(h, launch_shift<T>((C2<T>*)h->spec_cur, (C2<T>*)h->backup, h->NL, h->H, dE0, true, s));
+      RVE_CUDA(h, cudaStreamSynchronize(s));
+      char buf[200];
+      std::snprintf(buf, sizeof(buf), "increment %d: no convergence in %d iterations (e=%.3e, cF=%.3e)",
+                    h->increment + 1, max_iter, st.e_eq, st.cF);
+      return fail(h, RVE_ERR_NOT_CONVERGED, buf);
+    }
+    std::swap(h->spec_cur, h->spec_nxt);
+    std::swap(h->P_prev, h->P_scr);
+  }
+}
+
+bool valid_len(int n) {
+  FftDim d;
+  return n >= 1 && factor_radices(n, &d);
+}
+
+bool valid_grid(int nx, int ny, int nz) {
+  return nx >= 2 && nx % 2 == 0 && valid_len(nx) && valid_len(ny) && valid_len(nz);
+}
+
+template <typename T>
+rve_status get_field_t(rve_s* h, int which, void* dst, size_t bytes, int on_dev) {
+  const void* src = nullptr;
+  int comps = 0;
+  switch (which) {
+    case RVE_FIELD_STRESS: src = h->sig_n; comps = 6; break;
+    case RVE_FIELD_STRAIN: src = h->eps_n; comps = 6; break;
+    case RVE_FIELD_EPS_P: src = h->ep; comps = 6; break;
+    case RVE_FIELD_V: src = h->v; comps = 16; break;
+    case RVE_FIELD_ALPHA: src = h->al; comps = 12; break;
+    case RVE_FIELD_VM: src = h->sig_n; comps = 1; break;
+    default: return fail(h, RVE_ERR_INVALID_ARG, "unknown field");
+  }
+  const size_t n = (size_t)comps * h->nvox;
+  if (!dst || bytes < n * sizeof(double)) return fail(h, RVE_ERR_INVALID_ARG, "destination too small");
+  double* out = (double*)dst;
+  void* tmp = nullptr;
+  if (!on_dev) {
+    rve_status s = dalloc(h, &tmp, n * sizeof(double));
+    if (s) return s;
+    out = (double*)tmp;
+  }
+  cudaError_t e = which == RVE_FIELD_VM ? launch_von_mises<T>((const T*)src, out, h->nvox, h->stream)
+                                        : launch_to_double<T>((const T*)src, out, (long long)n, h->stream);
+  if (e == cudaSuccess && !on_dev) e = cudaMemcpyAsync(dst, tmp, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (tmp) {
+    h->owned.pop_back();
+    if (h->opt.free) h->opt.free(tmp, h->opt.alloc_ctx);
+    else cudaFree(tmp);
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "get_fields");
+  return RVE_OK;
+}
+
+struct BlobHeader {
+  char magic[8];
+  int nx, ny, nz, precision, increment, pad;
+  double time, E_n[6], E_prev[6];
+  long long n_hist;
+};
+
+}  // namespace
+
+namespace rve {
+void set_global_error(const std::string& msg) { g_err = msg; }
+}  // namespace rve
+
+// ================================================================= C ABI ==============
+extern "C" {
+
+void rve_options_default(rve_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = RVE_FP64;
+  o->green = RVE_GREEN_WILLOT;
+  o->n_sub = 0;
+  o->max_iter = 1000;
+  o->fixed_iters = 0;
+  o->tol = 1e-6;
+}
+
+void rve_material_default(rve_material* m) {
+  if (!m) return;
+  m->C11 = 183000.0; m->C12 = 74000.0; m->C13 = 74000.0; m->C33 = 178000.0; m->C44 = 105000.0; m->C66 = 78000.0;
+  m->r0_ord = 90.0; m->r0_sup = 200.0; m->r0_twin = 110.0;
+  m->K = 10.0; m->n = 10.0; m->Kt = 10.0; m->nt = 10.0;
+  m->Q_s = 20.0; m->Q_b = 20.0; m->b_s = 5.0; m->b_b = 5.0;
+  m->h_diag = 1.0; m->h_off = 1.2;
+  m->c = 10000.0; m->d = 500.0;
+  m->Kc = 1.45; m->fm = 0.8; m->eta = 1.0e4;
+}
+
+rve_status rve_create(rve_t* out, int nx, int ny, int nz, const uint32_t* grain_id, int grain_id_on_device,
+                      int n_grains, const double* euler, const rve_options* opt) {
+  if (!out) return fail(nullptr, RVE_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!grain_id || !euler || n_grains < 1) return fail(nullptr, RVE_ERR_INVALID_ARG, "need grain_id, euler, n_grains >= 1");
+  if (!valid_grid(nx, ny, nz))
+    return fail(nullptr, RVE_ERR_UNSUPPORTED, "grid sizes must be 2^a 3^b 5^c, at most 512, nx even");
+  rve_options o;
+  rve_options_default(&o);
+  if (opt) o = *opt;
+  if (o.precision != RVE_FP64 && o.precision != RVE_FP32) return fail(nullptr, RVE_ERR_INVALID_ARG, "bad precision");
+  if (o.green != RVE_GREEN_WILLOT && o.green != RVE_GREEN_MS) return fail(nullptr, RVE_ERR_INVALID_ARG, "bad green");
+  if (o.n_sub < 0 || o.fixed_iters < 0 || o.max_iter < 0 || !(o.tol > 0)) return fail(nullptr, RVE_ERR_INVALID_ARG, "bad options");
+  if ((o.alloc == nullptr) != (o.free == nullptr)) return fail(nullptr, RVE_ERR_INVALID_ARG, "alloc and free go together");
+  for (long long i = 0; i < 3LL * n_grains; ++i)
+    if (!std::isfinite(euler[i])) return fail(nullptr, RVE_ERR_INVALID_ARG, "euler angle not finite");
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return fail(nullptr, RVE_ERR_CUDA, "no CUDA device available");
+  }
+  if (o.device < 0 || o.device >= ndev) return fail(nullptr, RVE_ERR_INVALID_ARG, "bad device ordinal");
+  e = cudaSetDevice(o.device);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaSetDevice");
+
+  rve_s* h = new rve_s();
+  h->opt = o;
+  rve_material_default(&h->mat);
+  h->nx = nx; h->ny = ny; h->nz = nz;
+  h->H = nx / 2 + 1;
+  h->NL = (long long)ny * nz;
+  h->nvox = (long long)nx * ny * nz;
+  h->n_grains = n_grains;
+  h->stream = o.stream ? (cudaStream_t)o.stream : cudaStreamPerThread;
+  h->tsize = o.precision == RVE_FP64 ? 8 : 4;
+  factor_radices(nx, &h->dx);
+  factor_radices(ny, &h->dy);
+  factor_radices(nz, &h->dz);
+  h->euler.assign(euler, euler + 3LL * n_grains);
+  reference_medium(h->mat, &h->lam0, &h->mu0);
+  rve_status s;
+  // grain map: validate on the host copy
+  std::vector<uint32_t> gid((size_t)h->nvox);
+  if (grain_id_on_device) {
+    e = cudaMemcpy(gid.data(), grain_id, gid.size() * 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) { s = cuda_fail(h, e, "grain_id copy"); rve_destroy(h); return s; }
+  } else {
+    std::memcpy(gid.data(), grain_id, gid.size() * 4);
+  }
+  for (uint32_t g : gid)
+    if (g >= (uint32_t)n_grains) { s = fail(h, RVE_ERR_INVALID_ARG, "grain id >= n_grains"); rve_destroy(h); return s; }
+  if ((s = dalloc(h, (void**)&h->grain, gid.size() * 4))) { rve_destroy(h); return s; }
+  e = cudaMemcpyAsync(h->grain, gid.data(), gid.size() * 4, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) { s = cuda_fail(h, e, "grain_id upload"); rve_destroy(h); return s; }
+  if (o.precision == RVE_FP64) {
+    if ((s = upload_tables<double>(h)) || (s = alloc_fields<double>(h))) { rve_destroy(h); return s; }
+  } else {
+    if ((s = upload_tables<float>(h)) || (s = alloc_fields<float>(h))) { rve_destroy(h); return s; }
+  }
+  if (o.timing)
+    for (int k = 0; k < RVE_K_COUNT; ++k) {
+      e = cudaEventCreate(&h->ev_a[k]);
+      if (e == cudaSuccess) e = cudaEventCreate(&h->ev_b[k]);
+      if (e != cudaSuccess) { s = cuda_fail(h, e, "cudaEventCreate"); rve_destroy(h); return s; }
+    }
+  e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) { s = cuda_fail(h, e, "create"); rve_destroy(h); return s; }
+  *out = h;
+  return RVE_OK;
+}
+
+rve_status rve_set_material(rve_t h, const rve_material* m) {
+  if (!h || !m) return fail(h, RVE_ERR_INVALID_ARG, "NULL argument");
+  if (h->increment > 0) return fail(h, RVE_ERR_STATE, "material is fixed once stepping started");
+  rve_status s = check_material(h, *m);
+  if (s) return s;
+  h->mat = *m;
+  reference_medium(h->mat, &h->lam0, &h->mu0);
+  return RVE_OK;
+}
+
+rve_status rve_set_mixed_load(rve_t h, const double Edot[6], const uint8_t ctrl[6], const double Sigma[6], double dt) {
+  if (!h || !Edot || !ctrl || !Sigma) return fail(h, RVE_ERR_INVALID_ARG, "NULL argument");
+  if (!(dt > 0) || !std::isfinite(dt)) return fail(h, RVE_ERR_INVALID_ARG, "dt must be > 0");
+  int nc = 0;
+  for (int c = 0; c < 6; ++c) {
+    if (!std::isfinite(Edot[c]) || !std::isfinite(Sigma[c])) return fail(h, RVE_ERR_INVALID_ARG, "load not finite");
+    nc += ctrl[c] ? 1 : 0;
+  }
+  if (nc == 0) return fail(h, RVE_ERR_INVALID_ARG, "at least one component must be strain-controlled");
+  for (int c = 0; c < 6; ++c) {
+    h->Edot[c] = Edot[c];
+    h->ctrl[c] = ctrl[c] ? 1 : 0;
+    h->Sigma[c] = Sigma[c];
+  }
+  h->dt = dt;
+  return RVE_OK;
+}
+
+rve_status rve_step(rve_t h, int n, long long* iters) {
+  if (!h) return fail(h, RVE_ERR_INVALID_ARG, "NULL handle");
+  if (n < 0) return fail(h, RVE_ERR_INVALID_ARG, "n_increments < 0");
+  if (iters) *iters = 0;
+  cudaError_t e = cudaSetDevice(h->opt.device);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+  for (int i = 0; i < n; ++i) {
+    rve_status s = h->opt.precision == RVE_FP64 ? step_one<double>(h, iters) : step_one<float>(h, iters);
+    if (s) return s;
+  }
+  return RVE_OK;
+}
+
+rve_status rve_get_effective(rve_t h, rve_effective* last, rve_effective* hist, int cap, int* n_hist) {
+  if (!h) return fail(h, RVE_ERR_INVALID_ARG, "NULL handle");
+  if (n_hist) *n_hist = (int)h->hist.size();
+  if (last) {
+    if (h->hist.empty()) std::memset(last, 0, sizeof(*last));
+    else *last = h->hist.back();
+  }
+  if (hist && cap > 0) {
+    const int m = std::min<int>(cap, (int)h->hist.size());
+    for (int i = 0; i < m; ++i) hist[i] = h->hist[i];
+  }
+  return RVE_OK;
+}
+
+rve_status rve_get_fields(rve_t h, int which, void* dst, size_t bytes, int on_dev) {
+  if (!h) return fail(h, RVE_ERR_INVALID_ARG, "NULL handle");
+  cudaError_t e = cudaSetDevice(h->opt.device);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+  return h->opt.precision == RVE_FP64 ? get_field_t<double>(h, which, dst, bytes, on_dev)
+                                      : get_field_t<float>(h, which, dst, bytes, on_dev);
+}
+
+rve_status rve_save_state(rve_t h, void* blob, size_t* bytes) {
+  if (!h || !bytes) return fail(h, RVE_ERR_INVALID_ARG, "NULL argument");
+  const size_t ts = h->tsize;
+  const size_t spec = (size_t)6 * h->NL * h->H * 2 * ts;
+  const size_t fld = (size_t)h->nvox * ts;
+  const size_t need = sizeof(BlobHeader) + h->hist.size() * sizeof(rve_effective) + 2 * spec + fld * (6 + 16 + 12 + 6 + 6);
+  if (!blob) {
+    *bytes = need;
+    return RVE_OK;
+  }
+  if (*bytes < need) return fail(h, RVE_ERR_INVALID_ARG, "blob too small");
+  BlobHeader hd;
+  std::memset(&hd, 0, sizeof(hd));
+  std::memcpy(hd.magic, "RVESTAT1", 8);
+  hd.nx = h->nx; hd.ny = h->ny; hd.nz = h->nz; hd.precision = h->opt.precision; hd.increment = h->increment;
+  hd.time = h->time;
+  std::memcpy(hd.E_n, h->E_n, sizeof(hd.E_n));
+  std::memcpy(hd.E_prev, h->E_prev, sizeof(hd.E_prev));
+  hd.n_hist = (long long)h->hist.size();
+  char* p = (char*)blob;
+  std::memcpy(p, &hd, sizeof(hd));
+  p += sizeof(hd);
+  if (!h->hist.empty()) std::memcpy(p, h->hist.data(), h->hist.size() * sizeof(rve_effective));
+  p += h->hist.size() * sizeof(rve_effective);
+  struct { const void* d; size_t n; } parts[] = {{h->spec_cur, spec}, {h->P_prev, spec}, {h->ep, 6 * fld},
+                                                 {h->v, 16 * fld},     {h->al, 12 * fld},   {h->eps_n, 6 * fld},
+                                                 {h->sig_n, 6 * fld}};
+  for (auto& q : parts) {
+    cudaError_t e = cudaMemcpyAsync(p, q.d, q.n, cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "save_state");
+    p += q.n;
+  }
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "save_state");
+  *bytes = need;
+  return RVE_OK;
+}
+
+rve_status rve_load_state(rve_t h, const void* blob, size_t bytes) {
+  if (!h || !blob) return fail(h, RVE_ERR_INVALID_ARG, "NULL argument");
+  if (bytes < sizeof(BlobHeader)) return fail(h, RVE_ERR_INVALID_ARG, "blob too small");
+  BlobHeader hd;
+  std::memcpy(&hd, blob, sizeof(hd));
+  if (std::memcmp(hd.magic, "RVESTAT1", 8) || hd.nx != h->nx || hd.ny != h->ny || hd.nz != h->nz ||
+      hd.precision != h->opt.precision || hd.n_hist < 0)
+    return fail(h, RVE_ERR_INVALID_ARG, "blob does not match this handle");
+  const size_t ts = h->tsize;
+  const size_t spec = (size_t)6 * h->NL * h->H * 2 * ts;
+  const size_t fld = (size_t)h->nvox * ts;
+  const size_t need = sizeof(BlobHeader) + (size_t)hd.n_hist * sizeof(rve_effective) + 2 * spec + fld * 46;
+  if (bytes < need) return fail(h, RVE_ERR_INVALID_ARG, "blob truncated");
+  const char* p = (const char*)blob + sizeof(hd);
+  h->hist.assign((const rve_effective*)p, (const rve_effective*)p + hd.n_hist);
+  p += (size_t)hd.n_hist * sizeof(rve_effective);
+  struct { void* d; size_t n; } parts[] = {{h->spec_cur, spec}, {h->P_prev, spec}, {h->ep, 6 * fld},
+                                           {h->v, 16 * fld},     {h->al, 12 * fld},   {h->eps_n, 6 * fld},
+                                           {h->sig_n, 6 * fld}};
+  for (auto& q : parts) {
+    cudaError_t e = cudaMemcpyAsync(q.d, p, q.n, cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "load_state");
+    p += q.n;
+  }
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "load_state");
+  h->increment = hd.increment;
+  h->time = hd.time;
+  std::memcpy(h->E_n, hd.E_n, sizeof(hd.E_n));
+  std::memcpy(h->E_prev, hd.E_prev, sizeof(hd.E_prev));
+  return RVE_OK;
+}
+
+rve_status rve_kernel_times(rve_t h, double* ms, long long* launches, int reset) {
+  if (!h) return fail(h, RVE_ERR_INVALID_ARG, "NULL handle");
+  if (!h->opt.timing) return fail(h, RVE_ERR_STATE, "handle created without timing");
+  for (int k = 0; k < RVE_K_COUNT; ++k) {
+    if (ms) ms[k] = h->k_ms[k];
+    if (launches) launches[k] = h->k_n[k];
+    if (reset) {
+      h->k_ms[k] = 0.0;
+      h->k_n[k] = 0;
+    }
+  }
+  return RVE_OK;
+}
+
+rve_status rve_get_residuals(rve_t h, double* e_eq, double* c_F, int cap, int* n) {
+  if (!h) return fail(h, RVE_ERR_INVALID_ARG, "NULL handle");
+  const int m = (int)h->res_e.size();
+  if (n) *n = m;
+  for (int i = 0; i < std::min(cap, m); ++i) {
+    if (e_eq) e_eq[i] = h->res_e[i];
+    if (c_F) c_F[i] = h->res_c[i];
+  }
+  return RVE_OK;
+}
+
+const char* rve_last_error(rve_t h) {
+  if (h) return h->err.c_str();
+  return g_err.c_str();
+}
+
+void rve_destroy(rve_t h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  release(h);
+  delete h;
+}
+
+rve_status rve_material_point(int precision, const rve_material* mat, long long nvox, const void* R, const void* eps_n,
+                              const void* eps, void* state, void* sigma, double dt, int n_sub, void* stream) {
+  if (!mat || nvox < 0 || (nvox > 0 && (!R || !eps_n || !eps || !state || !sigma)) || !(dt > 0) || n_sub < 1)
+    return fail(nullptr, RVE_ERR_INVALID_ARG, "bad material-point arguments");
+  rve_s tmp;
+  tmp.mat = *mat;
+  rve_status s = check_material(&tmp, *mat);
+  if (s) return fail(nullptr, s, tmp.err);
+  reference_medium(tmp.mat, &tmp.lam0, &tmp.mu0);
+  cudaStream_t st = stream ? (cudaStream_t)stream : cudaStreamPerThread;
+  cudaError_t e;
+  if (precision == RVE_FP64)
+    e = launch_material_point<double>(make_mat<double>(&tmp), nvox, (const double*)R, (const double*)eps_n,
+                                      (const double*)eps, (double*)state, (double*)sigma, dt, n_sub, st);
+  else if (precision == RVE_FP32)
+    e = launch_material_point<float>(make_mat<float>(&tmp), nvox, (const float*)R, (const float*)eps_n,
+                                     (const float*)eps, (float*)state, (float*)sigma, (float)dt, n_sub, st);
+  else
+    return fail(nullptr, RVE_ERR_INVALID_ARG, "bad precision");
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "material_point");
+  return RVE_OK;
+}
+
+}  // extern "C"
+
+template <typename T>
+static rve_status fft_t(int nx, int ny, int nz, int ncomp, const void* in, void* spec, void* out, int sign,
+                        cudaStream_t st) {
+  rve_s h;
+  h.nx = nx; h.ny = ny; h.nz = nz; h.H = nx / 2 + 1; h.NL = (long long)ny * nz;
+  factor_radices(nx, &h.dx);
+  factor_radices(ny, &h.dy);
+  factor_radices(nz, &h.dz);
+  h.stream = st;
+  rve_status s;
+  if ((s = upload_tables<T>(&h))) { release(&h); return fail(nullptr, s, h.err); }
+  const int L = std::max(1, x_threads() / nx);
+  XFftArgs<T> xa;
+  xa.nx = nx; xa.H = h.H; xa.L = L; xa.ncomp = ncomp; xa.NL = h.NL;
+  xa.dx = h.dx;
+  xa.tw = (const C2<T>*)h.tw_x;
+  xa.real = (const T*)in;
+  xa.spec = (C2<T>*)spec;
+  xa.real_out = (T*)out;
+  const size_t xsm = (size_t)(nx + 2 * L * nx) * 2 * sizeof(T);
+  const dim3 xg((unsigned)((h.NL + L - 1) / L), ncomp);
+  const size_t budget = 96 * 1024;
+  auto pass = [&](const FftDim& d, void* tw, long long stride, int n_o2, long long A, long long B, int n_outer) {
+    LineArgs<T> la;
+    la.d = d;
+    la.tw = (const C2<T>*)tw;
+    la.spec = (C2<T>*)spec;
+    la.H = h.H;
+    la.HC = (int)std::max<size_t>(1, std::min<size_t>(16, (budget / (4 * sizeof(T))) / d.n));
+    la.HC = std::min(la.HC, h.H);
+    la.n_o2 = n_o2;
+    la.stride = stride;
+    la.A = A;
+    la.B = B;
+    const size_t sm = (size_t)(d.n + 2 * la.HC * (d.n + 1)) * 2 * sizeof(T);
+    return launch_line<T>(la, sign, dim3((h.H + la.HC - 1) / la.HC, n_outer), sm, st);
+  };
+  const long long plane = (long long)nz * ny * h.H;
+  cudaError_t e = cudaSuccess;
+  if (sign < 0) {
+    e = launch_xfft<T>(xa, -1, xg, xsm, st);
+    if (e == cudaSuccess) e = pass(h.dy, h.tw_y, h.H, nz, plane, (long long)ny * h.H, ncomp * nz);
+    if (e == cudaSuccess) e = pass(h.dz, h.tw_z, (long long)ny * h.H, ny, plane, h.H, ncomp * ny);
+  } else {
+    e = pass(h.dz, h.tw_z, (long long)ny * h.H, ny, plane, h.H, ncomp * ny);
+    if (e == cudaSuccess) e = pass(h.dy, h.tw_y, h.H, nz, plane, (long long)ny * h.H, ncomp * nz);
+    if (e == cudaSuccess) e = launch_xfft<T>(xa, +1, xg, xsm, st);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  release(&h);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "fft");
+  return RVE_OK;
+}
+
+extern "C" {
+
+rve_status rve_fft_r2c(int precision, int nx, int ny, int nz, int ncomp, const void* in, void* out, void* stream) {
+  if (!valid_grid(nx, ny, nz)) return fail(nullptr, RVE_ERR_UNSUPPORTED, "bad size");
+  if (ncomp < 1 || !in || !out) return fail(nullptr, RVE_ERR_INVALID_ARG, "bad arguments");
+  cudaStream_t st = stream ? (cudaStream_t)stream : cudaStreamPerThread;
+  if (precision == RVE_FP64) return fft_t<double>(nx, ny, nz, ncomp, in, out, nullptr, -1, st);
+  if (precision == RVE_FP32) return fft_t<float>(nx, ny, nz, ncomp, in, out, nullptr, -1, st);
+  return fail(nullptr, RVE_ERR_INVALID_ARG, "bad precision");
+}
+
+rve_status rve_fft_c2r(int precision, int nx, int ny, int nz, int ncomp, void* in, void* out, void* stream) {
+  if (!valid_grid(nx, ny, nz)) return fail(nullptr, RVE_ERR_UNSUPPORTED, "bad size");
+  if (ncomp < 1 || !in || !out) return fail(nullptr, RVE_ERR_INVALID_ARG, "bad arguments");
+  cudaStream_t st = stream ? (cudaStream_t)stream : cudaStreamPerThread;
+  if (precision == RVE_FP64) return fft_t<double>(nx, ny, nz, ncomp, nullptr, in, out, +1, st);
+  if (precision == RVE_FP32) return fft_t<float>(nx, ny, nz, ncomp, nullptr, in, out, +1, st);
+  return fail(nullptr, RVE_ERR_INVALID_ARG, "bad precision");
+}
+
+}  // extern "C"

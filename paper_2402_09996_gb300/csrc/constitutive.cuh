@@ -1,0 +1,352 @@
+// Per-voxel Meric-Cailletaud crystal plasticity (arXiv 2402.09996, Sec. 3 and 4).
+//
+// State (crystal frame): plastic strain eps_p (6 tensor components, order 11 22 33 23
+// 13 12), accumulated slip v (12 slip systems then 4 twin systems; the twin volume
+// fraction is f = sqrt(2) v), kinematic variables alpha of the 12 slip systems.
+//
+// Rates at strain eps (Sec. 3):
+//   sigma   = C : (eps - eps_p)                                 (tetragonal C, c || z)
+//   tau     = sigma : m,  m = (n x l + l x n)/2                 (Table 1 systems)
+//   r       = r0 + Q sum_s' q_ss' (1 - exp(-b v_s'))            (q = h_diag / h_off)
+//   slip:   a = |tau - c alpha| - r,  gdot = sign(tau - c alpha) rho,
+//           rho = < (a - eta rho) / K >^n                       (Sec. 4, Eq. (regu))
+//           alpha_dot = gdot - d |gdot| alpha
+//   twin:   rho = (Kc/sqrt2) <fm - sum f> < (tau - r - eta rho) / Kt >^nt, gdot = rho
+//   eps_p_dot = (1 - sum f) sum_s gdot_s m_s + sum_b gdot_b m_b,  v_dot = |gdot|.
+// Integration: n_sub classical RK4 steps along the linear strain path of the
+// increment (Sec. 3, "explicit ... Runge-Kutta 4th order").
+#pragma once
+
+#include "rve_common.cuh"
+
+namespace rve {
+
+// Table 1 (system 9 read as (1 -1 1)[1 1 0]); crystal frame with c/a = 1.
+__host__ __device__ __forceinline__ constexpr int sys_n(int s, int c) {
+  constexpr int t[16][3] = {{1, 1, -1}, {1, 1, -1}, {1, 1, -1}, {-1, 1, 1}, {-1, 1, 1}, {-1, 1, 1},
+                            {1, -1, 1}, {1, -1, 1}, {1, -1, 1}, {1, 1, 1},  {1, 1, 1},  {1, 1, 1},
+                            {1, 1, -1}, {-1, 1, 1}, {1, -1, 1}, {1, 1, 1}};
+  return t[s][c];
+}
+__host__ __device__ __forceinline__ constexpr int sys_l(int s, int c) {
+  constexpr int t[16][3] = {{0, 1, 1},  {1, 0, 1},  {1, -1, 0},  {0, -1, 1}, {-1, 0, -1}, {-1, -1, 0},
+                            {0, 1, 1},  {1, 0, -1}, {1, 1, 0},   {0, 1, -1}, {1, 0, -1},  {1, -1, 0},
+                            {1, 1, 2},  {-1, 1, -2}, {1, -1, -2}, {1, 1, -2}};
+  return t[s][c];
+}
+
+// 1 / (|n| |l|): sqrt(3) sqrt(2) for slip, sqrt(3) sqrt(6) for twins.
+template <typename T>
+__device__ __forceinline__ T sys_scale(int s) {
+  return s < 12 ? T(0.40824829046386301637) : T(0.23570226039551584147);
+}
+
+template <typename T>
+struct MPState {
+  T ep[6];
+  T v[16];
+  T al[12];
+};
+
+template <typename T>
+__device__ __forceinline__ void hooke(const MatDev<T>& M, const T* e, T* s) {
+  s[0] = M.C11 * e[0] + M.C12 * e[1] + M.C13 * e[2];
+  s[1] = M.C12 * e[0] + M.C11 * e[1] + M.C13 * e[2];
+  s[2] = M.C13 * (e[0] + e[1]) + M.C33 * e[2];
+  s[3] = T(2) * M.C44 * e[3];
+  s[4] = T(2) * M.C44 * e[4];
+  s[5] = T(2) * M.C66 * e[5];
+}
+
+// tau = sigma : m_s = (n . sigma . l) / (|n||l|)
+template <typename T>
+__device__ __forceinline__ T resolved(int s, const T* g) {
+  const T n0 = T(sys_n(s, 0)), n1 = T(sys_n(s, 1)), n2 = T(sys_n(s, 2));
+  const T l0 = T(sys_l(s, 0)), l1 = T(sys_l(s, 1)), l2 = T(sys_l(s, 2));
+  const T a0 = g[0] * l0 + g[5] * l1 + g[4] * l2;
+  const T a1 = g[5] * l0 + g[1] * l1 + g[3] * l2;
+  const T a2 = g[4] * l0 + g[3] * l1 + g[2] * l2;
+  return sys_scale<T>(s) * (n0 * a0 + n1 * a1 + n2 * a2);
+}
+
+// acc += w * m_s
+template <typename T>
+__device__ __forceinline__ void add_schmid(int s, T w, T* acc) {
+  const T n0 = T(sys_n(s, 0)), n1 = T(sys_n(s, 1)), n2 = T(sys_n(s, 2));
+  const T l0 = T(sys_l(s, 0)), l1 = T(sys_l(s, 1)), l2 = T(sys_l(s, 2));
+  const T f = w * sys_scale<T>(s);
+  const T h = T(0.5) * f;
+  acc[0] += f * (n0 * l0);
+  acc[1] += f * (n1 * l1);
+  acc[2] += f * (n2 * l2);
+  acc[3] += h * (n1 * l2 + n2 * l1);
+  acc[4] += h * (n0 * l2 + n2 * l0);
+  acc[5] += h * (n0 * l1 + n1 * l0);
+}
+
+// z^n for a small positive integer n (binary powering over a fixed 6-bit loop).
+template <typename T>
+__device__ __forceinline__ T ipow(T z, int n) {
+  T r = T(1), b = z;
+#pragma unroll
+  for (int bit = 0; bit < 6; ++bit) {
+    if ((n >> bit) & 1) r *= b;
+    b *= b;
+  }
+  return r;
+}
+
+template <typename T>
+__device__ __forceinline__ T powT(T z, T n, int n_int) {
+  return n_int > 0 ? ipow<T>(z, n_int) : pow(z, n);
+}
+
+template <typename T> __device__ __forceinline__ T fast_log2(T x);
+template <> __device__ __forceinline__ float fast_log2<float>(float x) { return __log2f(x); }
+template <> __device__ __forceinline__ double fast_log2<double>(double x) { return log2(x); }
+template <typename T> __device__ __forceinline__ T fast_exp2(T x);
+template <> __device__ __forceinline__ float fast_exp2<float>(float x) { return exp2f(x); }
+template <> __device__ __forceinline__ double fast_exp2<double>(double x) { return exp2(x); }
+template <typename T> __device__ __forceinline__ T fast_div(T a, T b);
+template <> __device__ __forceinline__ float fast_div<float>(float a, float b) { return __fdividef(a, b); }
+template <> __device__ __forceinline__ double fast_div<double>(double a, double b) { return a / b; }
+
+// Newton iterations after the starting point (enough for round-off in either precision,
+// see reg_rate).
+template <typename T> struct NewtonSteps;
+template <> struct NewtonSteps<float> { static constexpr int value = 4; };
+template <> struct NewtonSteps<double> { static constexpr int value = 6; };
+
+// Non-negative rho with rho = P < (a - eta rho) / Kn >^n  (Sec. 4, regularised flow);
+// rho = 0 when a <= 0 or P <= 0.
+// With z = (a - eta rho)/Kn the root solves phi(z) = c z^n + Kn z - a = 0, c = eta P.
+// Scaling z = zB u with zB = (a/c)^(1/n) leaves u^n + beta u - 1 = 0, beta = Kn zB / a,
+// whose root is close (within 5% for n >= 1.5) to the smooth minimum
+// u0 = (1 + beta^m)^(-1/m) of its two asymptotes 1 and 1/beta, with m chosen so that u0
+// is exact at beta = 1.  A fixed number of Newton steps then reaches round-off
+// (4 in float, 6 in double for beta in [1e-8, 1e8]), so the solve has no data-dependent
+// loop.  Logarithms are base 2.
+template <typename T>
+__device__ __forceinline__ T reg_rate(T a, T P, T Kn, T n, int n_int, T inv_n, T m, T lg_Kn, T eta,
+                                      T lg_eta, T lg_P) {
+  if (!(a > T(0)) || !(P > T(0))) return T(0);
+  if (!(eta > T(0))) return P * powT<T>(a / Kn, n, n_int);
+  const T c = eta * P;
+  const T la = fast_log2<T>(a);
+  const T lzB = (la - lg_eta - lg_P) * inv_n;
+  const T lb = lg_Kn + lzB - la;
+  const T L = m * lb;
+  const T lu = L > T(0) ? -lb - fast_log2<T>(T(1) + fast_exp2<T>(-L)) / m
+                        : -fast_log2<T>(T(1) + fast_exp2<T>(L)) / m;
+  T z = fast_exp2<T>(lzB + lu);
+#pragma unroll
+  for (int it = 0; it < NewtonSteps<T>::value; ++it) {
+    const T zn1 = n_int > 0 ? ipow<T>(z, n_int - 1) : pow(z, n - T(1));
+    const T phi = c * zn1 * z + Kn * z - a;
+    z = z - fast_div<T>(phi, n * c * zn1 + Kn);
+  }
+  z = z > T(0) ? z : T(0);
+  return P * powT<T>(z, n, n_int);
+}
+
+// One RK4 stage: evaluates the rates at elastic strain e0 + s*de - yt.ep and state yt,
+// adds wacc * rates to acc and overwrites yt with y0 + cnext * rates.
+template <typename T>
+__device__ __forceinline__ void rk_stage(const MatDev<T>& M, const T* e0, const T* de, T s,
+                                         const MPState<T>& y0, MPState<T>& yt, MPState<T>& acc,
+                                         T wacc, T cnext) {
+  T e[6], sg[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) e[c] = e0[c] + s * de[c] - yt.ep[c];
+  hooke<T>(M, e, sg);
+  T g[16];
+  T Sslip = T(0), Stw = T(0), vtw = T(0);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    g[k] = T(1) - exp(-M.b_s * yt.v[k]);
+    Sslip += g[k];
+  }
+#pragma unroll
+  for (int k = 12; k < 16; ++k) {
+    g[k] = T(1) - exp(-M.b_b * yt.v[k]);
+    Stw += g[k];
+    vtw += yt.v[k];
+  }
+  const T ftot = T(1.41421356237309504880) * vtw;
+  const T wslip = T(1) - ftot;
+  T fm_left = M.fm - ftot;
+  fm_left = fm_left > T(0) ? fm_left : T(0);
+  const T Ptw = (M.Kc * T(0.70710678118654752440)) * fm_left;
+  const T lg_Ptw = Ptw > T(0) ? fast_log2<T>(Ptw) : T(0);
+  const T dq = M.h_diag - M.h_off;
+  T dep[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    const T te = resolved<T>(k, sg) - M.c * yt.al[k];
+    const T r = M.r0[k] + M.Q_s * (M.h_off * Sslip + dq * g[k]);
+    const T a = fabs(te) - r;
+    const T rho = reg_rate<T>(a, T(1), M.K, M.n, M.n_int, M.inv_n, M.sm, M.lg_K, M.eta, M.lg_eta, T(0));
+    const T gd = te < T(0) ? -rho : rho;
+    add_schmid<T>(k, gd * wslip, dep);
+    const T ald = gd - M.d * rho * yt.al[k];
+    acc.v[k] += wacc * rho;
+    yt.v[k] = y0.v[k] + cnext * rho;
+    acc.al[k] += wacc * ald;
+    yt.al[k] = y0.al[k] + cnext * ald;
+  }
+#pragma unroll
+  for (int k = 12; k < 16; ++k) {
+    const T a = resolved<T>(k, sg) - (M.r0[k] + M.Q_b * (M.h_off * Stw + dq * g[k]));
+    const T rho = reg_rate<T>(a, Ptw, M.Kt, M.nt, M.nt_int, M.inv_nt, M.smt, M.lg_Kt, M.eta, M.lg_eta, lg_Ptw);
+    add_schmid<T>(k, rho, dep);
+    acc.v[k] += wacc * rho;
+    yt.v[k] = y0.v[k] + cnext * rho;
+  }
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    acc.ep[c] += wacc * dep[c];
+    yt.ep[c] = y0.ep[c] + cnext * dep[c];
+  }
+}
+
+// True when no system can be active anywhere on the increment's strain path with the
+// state frozen at t_n: |tau - x| - r (slip) and tau - r (twin) are convex in the path
+// parameter, so checking both ends suffices; the exact solution is then "no flow".
+template <typename T>
+__device__ __forceinline__ bool elastic_increment(const MatDev<T>& M, const T* e0, const T* de,
+                                                  const MPState<T>& y) {
+  T ea[6], eb[6], sa[6], sb[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    ea[c] = e0[c] - y.ep[c];
+    eb[c] = e0[c] + de[c] - y.ep[c];
+  }
+  hooke<T>(M, ea, sa);
+  hooke<T>(M, eb, sb);
+  T g[16];
+  T Sslip = T(0), Stw = T(0), vtw = T(0);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    g[k] = T(1) - exp(-M.b_s * y.v[k]);
+    Sslip += g[k];
+  }
+#pragma unroll
+  for (int k = 12; k < 16; ++k) {
+    g[k] = T(1) - exp(-M.b_b * y.v[k]);
+    Stw += g[k];
+    vtw += y.v[k];
+  }
+  const T dq = M.h_diag - M.h_off;
+  bool quiet = true;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    const T x = M.c * y.al[k];
+    const T r = M.r0[k] + M.Q_s * (M.h_off * Sslip + dq * g[k]);
+    const T a0 = fabs(resolved<T>(k, sa) - x) - r;
+    const T a1 = fabs(resolved<T>(k, sb) - x) - r;
+    quiet = quiet && !(a0 > T(0)) && !(a1 > T(0));
+  }
+  const T ftot = T(1.41421356237309504880) * vtw;
+  if (M.fm - ftot > T(0)) {
+#pragma unroll
+    for (int k = 12; k < 16; ++k) {
+      const T r = M.r0[k] + M.Q_b * (M.h_off * Stw + dq * g[k]);
+      const T a0 = resolved<T>(k, sa) - r;
+      const T a1 = resolved<T>(k, sb) - r;
+      quiet = quiet && !(a0 > T(0)) && !(a1 > T(0));
+    }
+  }
+  return quiet;
+}
+
+// eps_c = R^T eps R for a symmetric tensor in 6-component storage; R row-major.
+template <typename T>
+__device__ __forceinline__ void to_crystal(const T* R, const T* e, T* out) {
+  const T E[3][3] = {{e[0], e[5], e[4]}, {e[5], e[1], e[3]}, {e[4], e[3], e[2]}};
+  T A[3][3];  // E R
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) A[i][j] = E[i][0] * R[0 * 3 + j] + E[i][1] * R[1 * 3 + j] + E[i][2] * R[2 * 3 + j];
+  // out_ij = sum_k R_ki A_kj
+  out[0] = R[0] * A[0][0] + R[3] * A[1][0] + R[6] * A[2][0];
+  out[1] = R[1] * A[0][1] + R[4] * A[1][1] + R[7] * A[2][1];
+  out[2] = R[2] * A[0][2] + R[5] * A[1][2] + R[8] * A[2][2];
+  out[3] = R[1] * A[0][2] + R[4] * A[1][2] + R[7] * A[2][2];
+  out[4] = R[0] * A[0][2] + R[3] * A[1][2] + R[6] * A[2][2];
+  out[5] = R[0] * A[0][1] + R[3] * A[1][1] + R[6] * A[2][1];
+}
+
+// sigma = R sigma_c R^T
+template <typename T>
+__device__ __forceinline__ void to_sample(const T* R, const T* s, T* out) {
+  const T S[3][3] = {{s[0], s[5], s[4]}, {s[5], s[1], s[3]}, {s[4], s[3], s[2]}};
+  T B[3][3];  // S R^T : B_ij = sum_k S_ik R_jk
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) B[i][j] = S[i][0] * R[j * 3 + 0] + S[i][1] * R[j * 3 + 1] + S[i][2] * R[j * 3 + 2];
+  // out_ij = sum_k R_ik B_kj
+  out[0] = R[0] * B[0][0] + R[1] * B[1][0] + R[2] * B[2][0];
+  out[1] = R[3] * B[0][1] + R[4] * B[1][1] + R[5] * B[2][1];
+  out[2] = R[6] * B[0][2] + R[7] * B[1][2] + R[8] * B[2][2];
+  out[3] = R[3] * B[0][2] + R[4] * B[1][2] + R[5] * B[2][2];
+  out[4] = R[0] * B[0][2] + R[1] * B[1][2] + R[2] * B[2][2];
+  out[5] = R[0] * B[0][1] + R[1] * B[1][1] + R[2] * B[2][1];
+}
+
+// Integrates one voxel over the increment [t_n, t_n + dt] (strain eps_n -> eps, sample
+// frame) and returns the sample-frame stress at t_n + dt; y is updated in place.
+template <typename T>
+__device__ __forceinline__ void mc_voxel(const MatDev<T>& M, const T* R, const T* eps_n, const T* eps,
+                                         MPState<T>& y, T dt, int nsub, T* sig) {
+  T e0[6], e1[6], de[6];
+  to_crystal<T>(R, eps_n, e0);
+  to_crystal<T>(R, eps, e1);
+#pragma unroll
+  for (int c = 0; c < 6; ++c) de[c] = e1[c] - e0[c];
+  if (!elastic_increment<T>(M, e0, de, y)) {
+    const T h = dt / T(nsub);
+    const T inv = T(1) / T(nsub);
+    for (int m = 0; m < nsub; ++m) {
+      const T s0 = T(m) * inv, sh = (T(m) + T(0.5)) * inv, s1 = (T(m) + T(1)) * inv;
+      MPState<T> yt = y, acc;
+#pragma unroll
+      for (int c = 0; c < 6; ++c) acc.ep[c] = T(0);
+#pragma unroll
+      for (int c = 0; c < 16; ++c) acc.v[c] = T(0);
+#pragma unroll
+      for (int c = 0; c < 12; ++c) acc.al[c] = T(0);
+      // classical RK4: stages at s0, sh, sh, s1 with weights 1, 2, 2, 1; one copy of
+      // the stage body (not unrolled) keeps the code compact
+#pragma unroll 1
+      for (int stg = 0; stg < 4; ++stg) {
+        const T s = stg == 0 ? s0 : (stg == 3 ? s1 : sh);
+        const T wacc = (stg == 0 || stg == 3) ? T(1) : T(2);
+        const T cnext = stg < 2 ? T(0.5) * h : (stg == 2 ? h : T(0));
+        rk_stage<T>(M, e0, de, s, y, yt, acc, wacc, cnext);
+      }
+      const T w = h / T(6);
+#pragma unroll
+      for (int c = 0; c < 6; ++c) y.ep[c] += w * acc.ep[c];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) y.v[c] += w * acc.v[c];
+#pragma unroll
+      for (int c = 0; c < 12; ++c) y.al[c] += w * acc.al[c];
+    }
+  }
+  T ee[6], sc[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) ee[c] = e1[c] - y.ep[c];
+  hooke<T>(M, ee, sc);
+  to_sample<T>(R, sc, sig);
+}
+
+template <typename T>
+__device__ __forceinline__ T von_mises6(const T* s) {
+  const T p = (s[0] + s[1] + s[2]) / T(3);
+  const T a = s[0] - p, b = s[1] - p, c = s[2] - p;
+  return sqrt(T(1.5) * (a * a + b * b + c * c + T(2) * (s[3] * s[3] + s[4] * s[4] + s[5] * s[5])));
+}
+
+}  // namespace rve

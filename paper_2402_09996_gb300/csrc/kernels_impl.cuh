@@ -1,0 +1,146 @@
+// Definitions of the launch wrappers; included once per precision by kernels_f32.cu
+// and kernels_f64.cu with RVE_T set to the field type.
+#pragma once
+
+#include "launch.h"
+#include "solver_kernels.cuh"
+
+namespace rve {
+
+template <typename T>
+static cudaError_t set_smem(const void* fn, size_t smem) {
+  if (smem <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+template <typename T>
+cudaError_t launch_xpass(const XArgs<T>& a, bool commit, int grid, size_t smem, cudaStream_t s) {
+  if (commit) {
+    cudaError_t e = set_smem<T>((const void*)k_xpass<T, true>, smem);
+    if (e != cudaSuccess) return e;
+    k_xpass<T, true><<<grid, kXThreads, smem, s>>>(a);
+  } else {
+    cudaError_t e = set_smem<T>((const void*)k_xpass<T, false>, smem);
+    if (e != cudaSuccess) return e;
+    k_xpass<T, false><<<grid, kXThreads, smem, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_line(const LineArgs<T>& a, int sign, dim3 grid, size_t smem, cudaStream_t s) {
+  if (sign < 0) {
+    cudaError_t e = set_smem<T>((const void*)k_line<T, -1>, smem);
+    if (e != cudaSuccess) return e;
+    k_line<T, -1><<<grid, kLineThreads, smem, s>>>(a);
+  } else {
+    cudaError_t e = set_smem<T>((const void*)k_line<T, +1>, smem);
+    if (e != cudaSuccess) return e;
+    k_line<T, +1><<<grid, kLineThreads, smem, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_zgreen(const ZArgs<T>& a, dim3 grid, size_t smem, cudaStream_t s) {
+  cudaError_t e = set_smem<T>((const void*)k_zgreen<T>, smem);
+  if (e != cudaSuccess) return e;
+  k_zgreen<T><<<grid, kZThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_shift_backup(C2<T>* spec, C2<T>* backup, long long NL, int H, double d0, double d1, double d2,
+                               double d3, double d4, double d5, int restore) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 6 * NL) return;
+  C2<T>* p = spec + (size_t)i * H;
+  if (restore) {
+    *p = backup[i];
+    return;
+  }
+  backup[i] = *p;
+  const int c = (int)(i / NL);
+  const double d = c == 0 ? d0 : c == 1 ? d1 : c == 2 ? d2 : c == 3 ? d3 : c == 4 ? d4 : d5;
+  p->x = (T)((double)p->x + d);
+}
+
+template <typename T>
+cudaError_t launch_shift(C2<T>* spec, C2<T>* backup, long long NL, int H, const double* dE, bool restore,
+                         cudaStream_t s) {
+  const long long n = 6 * NL;
+  const int thr = 256;
+  const long long grid = (n + thr - 1) / thr;
+  k_shift_backup<T><<<(unsigned)grid, thr, 0, s>>>(spec, backup, NL, H, dE[0], dE[1], dE[2], dE[3], dE[4], dE[5],
+                                                   restore ? 1 : 0);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_material_point(const MatDev<T>& M, long long nvox, const T* R, const T* eps_n, const T* eps,
+                                  T* state, T* sigma, T dt, int nsub, cudaStream_t s) {
+  if (nvox <= 0) return cudaSuccess;
+  const int thr = 128;
+  const long long grid = (nvox + thr - 1) / thr;
+  k_material_point<T><<<(unsigned)grid, thr, 0, s>>>(M, nvox, R, eps_n, eps, state, sigma, dt, nsub);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_xfft(const XFftArgs<T>& a, int sign, dim3 grid, size_t smem, cudaStream_t s) {
+  if (sign < 0) {
+    cudaError_t e = set_smem<T>((const void*)k_xfft<T, -1>, smem);
+    if (e != cudaSuccess) return e;
+    k_xfft<T, -1><<<grid, kXThreads, smem, s>>>(a);
+  } else {
+    cudaError_t e = set_smem<T>((const void*)k_xfft<T, +1>, smem);
+    if (e != cudaSuccess) return e;
+    k_xfft<T, +1><<<grid, kXThreads, smem, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_to_double(const T* __restrict__ src, double* __restrict__ dst, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = (double)src[i];
+}
+
+template <typename T>
+cudaError_t launch_to_double(const T* src, double* dst, long long n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int thr = 256;
+  k_to_double<T><<<(unsigned)((n + thr - 1) / thr), thr, 0, s>>>(src, dst, n);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_von_mises(const T* __restrict__ sig, double* __restrict__ dst, long long nvox) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nvox) return;
+  T s[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) s[c] = sig[c * (size_t)nvox + i];
+  dst[i] = (double)von_mises6<T>(s);
+}
+
+template <typename T>
+cudaError_t launch_von_mises(const T* sig6, double* dst, long long nvox, cudaStream_t s) {
+  if (nvox <= 0) return cudaSuccess;
+  const int thr = 256;
+  k_von_mises<T><<<(unsigned)((nvox + thr - 1) / thr), thr, 0, s>>>(sig6, dst, nvox);
+  return cudaGetLastError();
+}
+
+#define RVE_INSTANTIATE(T)                                                                                         \
+  template cudaError_t launch_xpass<T>(const XArgs<T>&, bool, int, size_t, cudaStream_t);                         \
+  template cudaError_t launch_line<T>(const LineArgs<T>&, int, dim3, size_t, cudaStream_t);                       \
+  template cudaError_t launch_zgreen<T>(const ZArgs<T>&, dim3, size_t, cudaStream_t);                             \
+  template cudaError_t launch_shift<T>(C2<T>*, C2<T>*, long long, int, const double*, bool, cudaStream_t);        \
+  template cudaError_t launch_material_point<T>(const MatDev<T>&, long long, const T*, const T*, const T*, T*, T*, \
+                                                T, int, cudaStream_t);                                            \
+  template cudaError_t launch_xfft<T>(const XFftArgs<T>&, int, dim3, size_t, cudaStream_t);                       \
+  template cudaError_t launch_to_double<T>(const T*, double*, long long, cudaStream_t);                           \
+  template cudaError_t launch_von_mises<T>(const T*, double*, long long, cudaStream_t);
+
+}  // namespace rve

@@ -1,0 +1,80 @@
+// Common device types for the RVE solver kernels (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rve {
+
+template <typename T> struct C2t;
+template <> struct C2t<float> { using type = float2; };
+template <> struct C2t<double> { using type = double2; };
+template <typename T> using C2 = typename C2t<T>::type;
+
+template <typename T>
+__device__ __forceinline__ C2<T> mk(T x, T y) { C2<T> r; r.x = x; r.y = y; return r; }
+template <typename T>
+__device__ __forceinline__ C2<T> cadd(C2<T> a, C2<T> b) { return mk<T>(a.x + b.x, a.y + b.y); }
+template <typename T>
+__device__ __forceinline__ C2<T> csub(C2<T> a, C2<T> b) { return mk<T>(a.x - b.x, a.y - b.y); }
+template <typename T>
+__device__ __forceinline__ C2<T> cmul(C2<T> a, C2<T> b) {
+  return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+template <typename T>
+__device__ __forceinline__ C2<T> cmulc(C2<T> a, C2<T> b) {
+  return mk<T>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+template <typename T>
+__device__ __forceinline__ C2<T> cscale(C2<T> a, T s) { return mk<T>(a.x * s, a.y * s); }
+
+// One FFT length factored into radix stages (radices 2, 3, 4, 5).
+struct FftDim {
+  int n;
+  int nst;
+  int radix[12];
+};
+
+// Material constants on the device (Sec. 3, Sec. 4), plus the reference medium.
+template <typename T>
+struct MatDev {
+  T C11, C12, C13, C33, C44, C66;
+  T r0[16];
+  T K, n, Kt, nt;
+  T Q_s, Q_b, b_s, b_b;
+  T h_diag, h_off;
+  T c, d;
+  T Kc, fm, eta;
+  int n_int, nt_int;  // > 0 when n (nt) is that small integer: powers by multiplication
+  T lam0, mu0;        // isotropic reference medium C0
+  // starting point of the regularised-rate root (see reg_rate in constitutive.cuh)
+  T inv_n, inv_nt;    // 1/n, 1/nt
+  T sm, smt;          // smooth-min exponents: 1 / log2(1/u1), u1^n + u1 = 1
+  T lg_K, lg_Kt;      // log2 K, log2 Kt
+  T lg_eta;           // log2 eta (eta > 0)
+};
+
+// Mixed-load controller data (always double).
+struct LoadDev {
+  double Minv[36];    // Mandel inverse of C0 restricted to the free components (zero elsewhere)
+  double Sigma_m[6];  // target mean stress, Mandel
+  int free_mask[6];   // 1 = stress-controlled
+  int any_free;
+};
+
+// Per-iteration device record, written by the last CTA of each reduction.
+struct IterStatus {
+  double E[2][6];       // E^(i) in slot i%2 (tensor components)
+  double sig_mean[6];   // <sigma>^(i)
+  double cF;            // stress-constraint error
+  double res_sum;       // sum_xi w |kappa . sigma_hat|^2
+  double e_eq;          // equilibrium error
+  double eff[4];        // commit: <sigma_eq>, <f_beta>, <v^s>, unused
+  int nan_flag;
+  int pad;
+};
+
+constexpr int kNumRed = 9;  // reduction slots per CTA
+
+}  // namespace rve

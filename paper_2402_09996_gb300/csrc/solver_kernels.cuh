@@ -1,0 +1,552 @@
+// Kernels of one fixed-point iteration of the Green-operator solver (Sec. 3, last
+// paragraph) and of the commit of a converged increment.
+//
+// Spectral layout: S[c][kz][ky][kx], c = 6 tensor components, kx in [0, nx/2]
+// (half spectrum of the real-to-complex transform along x), complex interleaved.
+// Between iterations S holds the strain with x still in Fourier space and y, z in
+// real space ("x-spectral" form).  One iteration:
+//   k_xpass   inverse x-FFT -> eps(x) -> per-voxel MC update -> sigma, tau = sigma - C0:eps
+//             -> forward x-FFT (out of place); FP64 block sums of sigma; the last CTA
+//             forms <sigma>, the stress-constraint error and the mixed-load update.
+//   k_line    forward y-FFT (in place)
+//   k_zgreen  forward z-FFT -> eps_hat = -Gamma0(kappa):tau_hat / N, eps_hat(0) = E,
+//             equilibrium residual (FP64) -> inverse z-FFT (in place)
+//   k_line    inverse y-FFT (in place)
+#pragma once
+
+#include "constitutive.cuh"
+#include "fft_smem.cuh"
+#include "rve_common.cuh"
+
+namespace rve {
+
+// ---------------------------------------------------------------- reductions --------
+template <int NV>
+__device__ __forceinline__ void warp_sum(double* v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], off);
+}
+
+// Fixed-order block sum; result valid in every lane of warp 0.  blockDim % 32 == 0.
+template <int NV>
+__device__ __forceinline__ void block_sum(double* v, double (*red)[kNumRed]) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  warp_sum<NV>(v);
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) red[wid][i] = v[i];
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] = lane < nw ? red[lane][i] : 0.0;
+    warp_sum<NV>(v);
+  }
+  __syncthreads();
+}
+
+// Linear CTA index and CTA count of a 1-D or 2-D grid.
+__device__ __forceinline__ unsigned int block_linear() { return blockIdx.x + gridDim.x * blockIdx.y; }
+__device__ __forceinline__ unsigned int block_count() { return gridDim.x * gridDim.y; }
+
+// Stores this CTA's sums and returns true (in all threads) in the CTA that finished last.
+template <int NV>
+__device__ __forceinline__ bool publish_partial(double* v, double* partial, unsigned int* counter,
+                                                double (*red)[kNumRed], int* s_last) {
+  block_sum<NV>(v, red);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) partial[(size_t)block_linear() * kNumRed + i] = v[i];
+    __threadfence();
+    const unsigned int prev = atomicAdd(counter, 1u);
+    *s_last = (prev == block_count() - 1) ? 1 : 0;
+  }
+  __syncthreads();
+  return *s_last != 0;
+}
+
+// Deterministic grand total of all CTAs' partials (fixed assignment and tree order).
+template <int NV>
+__device__ __forceinline__ void total_partials(const double* partial, double* v, double (*red)[kNumRed]) {
+  __threadfence();
+#pragma unroll
+  for (int i = 0; i < NV; ++i) v[i] = 0.0;
+  for (int b = threadIdx.x; b < (int)block_count(); b += blockDim.x)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] += __ldcg(&partial[(size_t)b * kNumRed + i]);
+  block_sum<NV>(v, red);
+}
+
+__device__ __forceinline__ double mandel_w(int a) { return a < 3 ? 1.0 : 1.41421356237309504880; }
+
+// ---------------------------------------------------------------- x pass -----------
+template <typename T>
+struct XArgs {
+  int nx, ny, nz, H, L;
+  long long nvox;
+  FftDim dx;
+  const C2<T>* tw;
+  const C2<T>* spec_in;
+  C2<T>* spec_out;
+  T* ep;
+  T* v;
+  T* al;
+  T* eps_n;
+  T* sig_n;
+  const uint32_t* grain;
+  const T* Rg;
+  MatDev<T> M;
+  LoadDev ld;
+  T dt;
+  int nsub;
+  double* partial;
+  unsigned int* counter;
+  IterStatus* st;
+  int it;
+};
+
+constexpr int kXThreads = 128;
+
+template <typename T, bool COMMIT>
+__global__ void __launch_bounds__(kXThreads) k_xpass(const XArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[32][kNumRed];
+  __shared__ int s_last;
+  C2<T>* tw = reinterpret_cast<C2<T>*>(smem_raw);
+  C2<T>* b0 = tw + a.nx;
+  C2<T>* b1 = b0 + 3 * a.L * a.nx;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int nx = a.nx, H = a.H, half = nx / 2;
+  const size_t NL = (size_t)a.ny * a.nz;
+  const int line0 = blockIdx.x * a.L;
+  const int nl = min(a.L, (int)(NL - line0));
+  const size_t nvox = (size_t)a.nvox;
+
+  for (int i = tid; i < nx; i += nthr) tw[i] = a.tw[i];
+  // pack component pairs (2p, 2p+1) of each line as one complex Hermitian-extended
+  // sequence Z = A + iB, so one complex inverse FFT yields both real lines
+  for (int w = tid; w < 3 * nl * H; w += nthr) {
+    const int xi = w % H;
+    const int q = w / H;  // q = p * nl + l
+    const int l = q % nl, p = q / nl;
+    const size_t line = (size_t)line0 + l;
+    C2<T> A = a.spec_in[((size_t)(2 * p) * NL + line) * H + xi];
+    C2<T> B = a.spec_in[((size_t)(2 * p + 1) * NL + line) * H + xi];
+    if (xi == 0 || xi == half) {
+      A.y = T(0);
+      B.y = T(0);
+    }
+    C2<T>* seq = b0 + (size_t)q * nx;
+    seq[xi] = mk<T>(A.x - B.y, A.y + B.x);
+    if (xi > 0 && xi < half) seq[nx - xi] = mk<T>(A.x + B.y, B.x - A.y);
+  }
+  __syncthreads();
+  C2<T>* res = smem_fft<T, +1>(b0, b1, a.dx, 3 * nl, nx, tw, tid, nthr);
+  C2<T>* oth = (res == b0) ? b1 : b0;
+
+  double acc[kNumRed];
+#pragma unroll
+  for (int i = 0; i < kNumRed; ++i) acc[i] = 0.0;
+  for (int t = tid; t < nl * nx; t += nthr) {
+    const int l = t / nx, x = t - l * nx;
+    const size_t vox = ((size_t)line0 + l) * nx + x;
+    T eps[6], epsn[6], sig[6], R[9];
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+      const C2<T> z = res[(size_t)(p * nl + l) * nx + x];
+      eps[2 * p] = z.x;
+      eps[2 * p + 1] = z.y;
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) epsn[c] = a.eps_n[c * nvox + vox];
+    MPState<T> y;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) y.ep[c] = a.ep[c * nvox + vox];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) y.v[c] = a.v[c * nvox + vox];
+#pragma unroll
+    for (int c = 0; c < 12; ++c) y.al[c] = a.al[c * nvox + vox];
+    const uint32_t g = a.grain[vox];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) R[i] = a.Rg[(size_t)g * 9 + i];
+    mc_voxel<T>(a.M, R, epsn, eps, y, a.dt, a.nsub, sig);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) acc[c] += (double)sig[c];
+    if (COMMIT) {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) a.ep[c * nvox + vox] = y.ep[c];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) a.v[c * nvox + vox] = y.v[c];
+#pragma unroll
+      for (int c = 0; c < 12; ++c) a.al[c * nvox + vox] = y.al[c];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        a.eps_n[c * nvox + vox] = eps[c];
+        a.sig_n[c * nvox + vox] = sig[c];
+      }
+      acc[6] += (double)von_mises6<T>(sig);
+      acc[7] += 1.41421356237309504880 * ((double)y.v[12] + (double)y.v[13] + (double)y.v[14] + (double)y.v[15]);
+      double vs = 0.0;
+#pragma unroll
+      for (int c = 0; c < 12; ++c) vs += (double)y.v[c];
+      acc[8] += vs;
+    } else {
+      const T tr = a.M.lam0 * (eps[0] + eps[1] + eps[2]);
+      const T m2 = T(2) * a.M.mu0;
+      T tau[6];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) tau[c] = sig[c] - m2 * eps[c] - (c < 3 ? tr : T(0));
+#pragma unroll
+      for (int p = 0; p < 3; ++p) res[(size_t)(p * nl + l) * nx + x] = mk<T>(tau[2 * p], tau[2 * p + 1]);
+    }
+  }
+  if (!COMMIT) {
+    __syncthreads();
+    C2<T>* out = smem_fft<T, -1>(res, oth, a.dx, 3 * nl, nx, tw, tid, nthr);
+    // unpack: A = (Z_k + conj Z_{n-k}) / 2, B = (Z_k - conj Z_{n-k}) / (2i)
+    for (int w = tid; w < 3 * nl * H; w += nthr) {
+      const int xi = w % H;
+      const int q = w / H;
+      const int l = q % nl, p = q / nl;
+      const size_t line = (size_t)line0 + l;
+      const C2<T> Z = out[(size_t)q * nx + xi];
+      const C2<T> Zm = out[(size_t)q * nx + (xi == 0 ? 0 : nx - xi)];
+      const C2<T> A = mk<T>(T(0.5) * (Z.x + Zm.x), T(0.5) * (Z.y - Zm.y));
+      const C2<T> B = mk<T>(T(0.5) * (Z.y + Zm.y), T(-0.5) * (Z.x - Zm.x));
+      a.spec_out[((size_t)(2 * p) * NL + line) * H + xi] = A;
+      a.spec_out[((size_t)(2 * p + 1) * NL + line) * H + xi] = B;
+    }
+  }
+  if (publish_partial<kNumRed>(acc, a.partial, a.counter, red, &s_last)) {
+    total_partials<kNumRed>(a.partial, acc, red);
+    if (tid == 0) {
+      IterStatus* st = a.st;
+      const double inv = 1.0 / (double)a.nvox;
+      double S[6];
+      int bad = 0;
+      for (int c = 0; c < 6; ++c) {
+        S[c] = acc[c] * inv;
+        st->sig_mean[c] = S[c];
+        bad |= !isfinite(S[c]);
+      }
+      if (COMMIT) {
+        st->eff[0] = acc[6] * inv;
+        st->eff[1] = acc[7] * inv * 0.25;
+        st->eff[2] = acc[8] * inv / 12.0;
+        bad |= !isfinite(acc[6]) | !isfinite(acc[7]) | !isfinite(acc[8]);
+      } else {
+        // mixed-load update of the free components (Mandel form)
+        const LoadDev& ld = a.ld;
+        double miss[6], nm = 0.0, ns = 0.0;
+        for (int c = 0; c < 6; ++c) {
+          const double sm = S[c] * mandel_w(c);
+          miss[c] = ld.free_mask[c] ? sm - ld.Sigma_m[c] : 0.0;
+          nm += miss[c] * miss[c];
+          ns += sm * sm;
+        }
+        st->cF = ld.any_free ? sqrt(nm) / sqrt(ns) : 0.0;
+        const double* Ec = st->E[a.it & 1];
+        double* En = st->E[(a.it + 1) & 1];
+        for (int c = 0; c < 6; ++c) {
+          double em = Ec[c] * mandel_w(c);
+          if (ld.free_mask[c]) {
+            double corr = 0.0;
+            for (int b = 0; b < 6; ++b) corr += ld.Minv[c * 6 + b] * miss[b];
+            em -= corr;
+          }
+          En[c] = em / mandel_w(c);
+        }
+      }
+      st->nan_flag |= bad ? (COMMIT ? 4 : 1) : 0;
+      *a.counter = 0u;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- line FFT pass -----
+// Transforms, in place, lines of length d.n along an axis with element stride `stride`
+// (complex units).  Line base offset: (o / n_o2) * A + (o % n_o2) * B + h, for
+// o = blockIdx.y and h in a chunk of HC consecutive kx values.
+template <typename T>
+struct LineArgs {
+  FftDim d;
+  const C2<T>* tw;
+  C2<T>* spec;
+  int H, HC, n_o2;
+  long long stride, A, B;
+};
+
+constexpr int kLineThreads = 256;
+
+template <typename T, int SIGN>
+__global__ void __launch_bounds__(kLineThreads) k_line(const LineArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2<T>* tw = reinterpret_cast<C2<T>*>(smem_raw);
+  const int n = a.d.n;
+  const int ps = n + 1;  // padded sequence stride
+  C2<T>* b0 = tw + n;
+  C2<T>* b1 = b0 + (size_t)a.HC * ps;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int h0 = blockIdx.x * a.HC;
+  const int hc = min(a.HC, a.H - h0);
+  const int o = blockIdx.y;
+  const size_t base = (size_t)(o / a.n_o2) * a.A + (size_t)(o % a.n_o2) * a.B + h0;
+  for (int i = tid; i < n; i += nthr) tw[i] = a.tw[i];
+  for (int w = tid; w < hc * n; w += nthr) {
+    const int hh = w % hc, j = w / hc;
+    b0[(size_t)hh * ps + j] = a.spec[base + (size_t)j * a.stride + hh];
+  }
+  __syncthreads();
+  C2<T>* res = smem_fft<T, SIGN>(b0, b1, a.d, hc, ps, tw, tid, nthr);
+  for (int w = tid; w < hc * n; w += nthr) {
+    const int hh = w % hc, j = w / hc;
+    a.spec[base + (size_t)j * a.stride + hh] = res[(size_t)hh * ps + j];
+  }
+}
+
+// ---------------------------------------------------------------- z pass + Green ----
+template <typename T>
+struct ZArgs {
+  int nx, ny, nz, H, HC;
+  long long nvox;
+  FftDim dz;
+  const C2<T>* tw;
+  C2<T>* spec;
+  const C2<T>* P_prev;
+  C2<T>* P_out;
+  const T* kx;  // per dimension, 2*N values: Willot (sin, cos) of pi xi/N, or MS (freq, 0)
+  const T* ky;
+  const T* kzt;
+  int scheme;   // 0 Willot, 1 Moulinec-Suquet
+  T lam0, mu0, invN;
+  double* partial;
+  unsigned int* counter;
+  IterStatus* st;
+  int it;
+};
+
+constexpr int kZThreads = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(kZThreads) k_zgreen(const ZArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[32][kNumRed];
+  __shared__ int s_last;
+  const int nz = a.nz;
+  C2<T>* tw = reinterpret_cast<C2<T>*>(smem_raw);
+  const int ps = nz + 1;  // padded sequence stride
+  C2<T>* b0 = tw + nz;
+  C2<T>* b1 = b0 + (size_t)6 * a.HC * ps;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int j = blockIdx.y;
+  const int h0 = blockIdx.x * a.HC;
+  const int hc = min(a.HC, a.H - h0);
+  const size_t H = a.H, ny = a.ny;
+  for (int i = tid; i < nz; i += nthr) tw[i] = a.tw[i];
+  for (int w = tid; w < 6 * hc * nz; w += nthr) {
+    const int hh = w % hc;
+    const int r = w / hc;
+    const int kz = r % nz, c = r / nz;
+    b0[(size_t)(c * hc + hh) * ps + kz] = a.spec[(((size_t)c * nz + kz) * ny + j) * H + h0 + hh];
+  }
+  __syncthreads();
+  C2<T>* res = smem_fft<T, -1>(b0, b1, a.dz, 6 * hc, ps, tw, tid, nthr);
+  C2<T>* oth = (res == b0) ? b1 : b0;
+
+  const double* En = a.st->E[(a.it + 1) & 1];
+  const T coef = (a.lam0 + a.mu0) / (a.mu0 * (a.lam0 + T(2) * a.mu0));
+  double rs = 0.0;
+  for (int w = tid; w < hc * nz; w += nthr) {
+    const int hh = w % hc, kz = w / hc;
+    const int h = h0 + hh;
+    T k0, k1, k2;
+    if (a.scheme == 0) {
+      const T sx = a.kx[2 * h], cx = a.kx[2 * h + 1];
+      const T sy = a.ky[2 * j], cy = a.ky[2 * j + 1];
+      const T sz = a.kzt[2 * kz], cz = a.kzt[2 * kz + 1];
+      k0 = sx * cy * cz;
+      k1 = cx * sy * cz;
+      k2 = cx * cy * sz;
+    } else {
+      k0 = a.kx[2 * h];
+      k1 = a.ky[2 * j];
+      k2 = a.kzt[2 * kz];
+    }
+    C2<T> t[6];
+    const size_t g0 = ((size_t)kz * ny + j) * H + h;
+    const size_t cstride = (size_t)nz * ny * H;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) t[c] = res[(size_t)(c * hc + hh) * ps + kz];
+    // equilibrium residual kappa . sigma_hat = kappa . (tau_hat - tau_hat_prev)
+    {
+      C2<T> d[6];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        const C2<T> p = a.P_prev[c * cstride + g0];
+        d[c] = csub<T>(t[c], p);
+        a.P_out[c * cstride + g0] = t[c];
+      }
+      // symmetric order (11,22,33,23,13,12): row i of d times kappa
+      const double r0x = (double)d[0].x * k0 + (double)d[5].x * k1 + (double)d[4].x * k2;
+      const double r0y = (double)d[0].y * k0 + (double)d[5].y * k1 + (double)d[4].y * k2;
+      const double r1x = (double)d[5].x * k0 + (double)d[1].x * k1 + (double)d[3].x * k2;
+      const double r1y = (double)d[5].y * k0 + (double)d[1].y * k1 + (double)d[3].y * k2;
+      const double r2x = (double)d[4].x * k0 + (double)d[3].x * k1 + (double)d[2].x * k2;
+      const double r2y = (double)d[4].y * k0 + (double)d[3].y * k1 + (double)d[2].y * k2;
+      const double wgt = (h == 0 || 2 * h == a.nx) ? 1.0 : 2.0;
+      rs += wgt * (r0x * r0x + r0y * r0y + r1x * r1x + r1y * r1y + r2x * r2x + r2y * r2y);
+    }
+    const T kk = k0 * k0 + k1 * k1 + k2 * k2;
+    C2<T> e[6];
+    if (h == 0 && j == 0 && kz == 0) {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) e[c] = mk<T>(T(En[c]), T(0));
+    } else if (!(kk > T(0))) {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) e[c] = mk<T>(T(0), T(0));
+    } else {
+      // Gamma0 is homogeneous of degree 0 in kappa: with the unit direction n = kappa/|kappa|,
+      // eps_hat = -[ (n_i u_j + n_j u_i) / (2 mu0) - coef n_i n_j (n.u) ] / N,  u = tau_hat n
+      const T inv_k = T(1) / sqrt(kk);
+      const T n0 = k0 * inv_k, n1 = k1 * inv_k, n2 = k2 * inv_k;
+      const C2<T> u0 = mk<T>(t[0].x * n0 + t[5].x * n1 + t[4].x * n2, t[0].y * n0 + t[5].y * n1 + t[4].y * n2);
+      const C2<T> u1 = mk<T>(t[5].x * n0 + t[1].x * n1 + t[3].x * n2, t[5].y * n0 + t[1].y * n1 + t[3].y * n2);
+      const C2<T> u2 = mk<T>(t[4].x * n0 + t[3].x * n1 + t[2].x * n2, t[4].y * n0 + t[3].y * n1 + t[2].y * n2);
+      const C2<T> nun = mk<T>(n0 * u0.x + n1 * u1.x + n2 * u2.x, n0 * u0.y + n1 * u1.y + n2 * u2.y);
+      const T ia = -a.invN / (T(2) * a.mu0);
+      const T ib = a.invN * coef;
+      const T nv[3] = {n0, n1, n2};
+      const C2<T> uv[3] = {u0, u1, u2};
+      const int ii[6] = {0, 1, 2, 1, 0, 0};
+      const int jj[6] = {0, 1, 2, 2, 2, 1};
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        const T ni = nv[ii[c]], nj = nv[jj[c]];
+        const C2<T> ui = uv[ii[c]], uj = uv[jj[c]];
+        const T nij = ni * nj;
+        e[c] = mk<T>(ia * (ni * uj.x + nj * ui.x) + ib * nij * nun.x, ia * (ni * uj.y + nj * ui.y) + ib * nij * nun.y);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) res[(size_t)(c * hc + hh) * ps + kz] = e[c];
+  }
+  __syncthreads();
+  C2<T>* out = smem_fft<T, +1>(res, oth, a.dz, 6 * hc, ps, tw, tid, nthr);
+  for (int w = tid; w < 6 * hc * nz; w += nthr) {
+    const int hh = w % hc;
+    const int r = w / hc;
+    const int kz = r % nz, c = r / nz;
+    a.spec[(((size_t)c * nz + kz) * ny + j) * H + h0 + hh] = out[(size_t)(c * hc + hh) * ps + kz];
+  }
+  double v[kNumRed];
+  v[0] = rs;
+#pragma unroll
+  for (int i = 1; i < kNumRed; ++i) v[i] = 0.0;
+  if (publish_partial<1>(v, a.partial, a.counter, red, &s_last)) {
+    total_partials<1>(a.partial, v, red);
+    if (tid == 0) {
+      IterStatus* st = a.st;
+      const double* S = st->sig_mean;
+      const double nrm = sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2] + 2.0 * (S[3] * S[3] + S[4] * S[4] + S[5] * S[5]));
+      st->res_sum = v[0];
+      st->e_eq = nrm > 0.0 ? sqrt(v[0]) / ((double)a.nvox * nrm) : 0.0;
+      st->nan_flag |= !isfinite(v[0]) ? 2 : 0;
+      *a.counter = 0u;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- small kernels -----
+// Uniform shift of the strain field held in x-spectral form: Re S[c][line][kx=0] += dE[c].
+template <typename T>
+__global__ void k_shift(C2<T>* spec, long long NL, int H, double d0, double d1, double d2, double d3,
+                        double d4, double d5) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 6 * NL) return;
+  const int c = (int)(i / NL);
+  const double d = c == 0 ? d0 : c == 1 ? d1 : c == 2 ? d2 : c == 3 ? d3 : c == 4 ? d4 : d5;
+  C2<T>* p = spec + (size_t)i * H;
+  p->x = (T)((double)p->x + d);
+}
+
+template <typename T>
+__global__ void k_material_point(const MatDev<T> M, long long nvox, const T* __restrict__ R,
+                                 const T* __restrict__ eps_n, const T* __restrict__ eps, T* state,
+                                 T* sigma, T dt, int nsub) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nvox) return;
+  const size_t n = (size_t)nvox;
+  T r[9], en[6], e[6], s[6];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) r[k] = R[(size_t)i * 9 + k];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    en[c] = eps_n[c * n + i];
+    e[c] = eps[c * n + i];
+  }
+  MPState<T> y;
+#pragma unroll
+  for (int c = 0; c < 6; ++c) y.ep[c] = state[c * n + i];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) y.v[c] = state[(6 + c) * n + i];
+#pragma unroll
+  for (int c = 0; c < 12; ++c) y.al[c] = state[(22 + c) * n + i];
+  mc_voxel<T>(M, r, en, e, y, dt, nsub, s);
+#pragma unroll
+  for (int c = 0; c < 6; ++c) state[c * n + i] = y.ep[c];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) state[(6 + c) * n + i] = y.v[c];
+#pragma unroll
+  for (int c = 0; c < 12; ++c) state[(22 + c) * n + i] = y.al[c];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) sigma[c * n + i] = s[c];
+}
+
+// Stand-alone x transforms of ncomp real lines (FFT entry points; same packing as k_xpass).
+template <typename T>
+struct XFftArgs {
+  int nx, H, L, ncomp;
+  long long NL;
+  FftDim dx;
+  const C2<T>* tw;
+  const T* real;
+  C2<T>* spec;
+  T* real_out;
+};
+
+template <typename T, int SIGN>
+__global__ void __launch_bounds__(kXThreads) k_xfft(const XFftArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2<T>* tw = reinterpret_cast<C2<T>*>(smem_raw);
+  C2<T>* b0 = tw + a.nx;
+  C2<T>* b1 = b0 + (size_t)a.L * a.nx;
+  const int tid = threadIdx.x, nthr = blockDim.x, nx = a.nx, H = a.H, half = nx / 2;
+  const long long line0 = (long long)blockIdx.x * a.L;
+  const int nl = (int)min((long long)a.L, a.NL - line0);
+  const int c = blockIdx.y;  // component
+  const size_t nvox = (size_t)a.NL * nx;
+  for (int i = tid; i < nx; i += nthr) tw[i] = a.tw[i];
+  if (SIGN < 0) {
+    for (int t = tid; t < nl * nx; t += nthr) b0[t] = mk<T>(a.real[c * nvox + (size_t)line0 * nx + t], T(0));
+    __syncthreads();
+    C2<T>* r = smem_fft<T, -1>(b0, b1, a.dx, nl, nx, tw, tid, nthr);
+    for (int w = tid; w < nl * H; w += nthr) {
+      const int l = w / H, xi = w - l * H;
+      a.spec[((size_t)c * a.NL + line0 + l) * H + xi] = r[(size_t)l * nx + xi];
+    }
+  } else {
+    for (int w = tid; w < nl * H; w += nthr) {
+      const int l = w / H, xi = w - l * H;
+      C2<T> A = a.spec[((size_t)c * a.NL + line0 + l) * H + xi];
+      if (xi == 0 || xi == half) A.y = T(0);
+      b0[(size_t)l * nx + xi] = A;
+      if (xi > 0 && xi < half) b0[(size_t)l * nx + nx - xi] = mk<T>(A.x, -A.y);
+    }
+    __syncthreads();
+    C2<T>* r = smem_fft<T, +1>(b0, b1, a.dx, nl, nx, tw, tid, nthr);
+    for (int t = tid; t < nl * nx; t += nthr) a.real_out[c * nvox + (size_t)line0 * nx + t] = r[t].x;
+  }
+}
+
+}  // namespace rve

@@ -1,0 +1,414 @@
+"""ctypes binding of librve.so (include/rve.h): argument marshalling only.
+
+Every step of the solve runs in the library's CUDA kernels; this module converts
+numpy arrays / torch tensors to pointers, passes torch's current CUDA stream and,
+optionally, torch's caching allocator, and turns status codes into exceptions.
+If librve.so cannot be loaded or no CUDA device is usable, calls raise: there is
+no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from pathlib import Path
+
+import numpy as np
+
+_PKG = Path(__file__).resolve().parent
+LIB_PATH = _PKG / "librve.so"
+
+FP64, FP32 = 0, 1
+GREEN_WILLOT, GREEN_MS = 0, 1
+FIELD_STRESS, FIELD_STRAIN, FIELD_EPS_P, FIELD_V, FIELD_ALPHA, FIELD_VM = range(6)
+FIELD_COMPONENTS = {FIELD_STRESS: 6, FIELD_STRAIN: 6, FIELD_EPS_P: 6, FIELD_V: 16, FIELD_ALPHA: 12, FIELD_VM: 1}
+KERNELS = ["xpass", "yfwd", "zgreen", "yinv", "commit", "shift"]
+STATUS = {
+    0: "RVE_OK",
+    1: "RVE_ERR_INVALID_ARG",
+    2: "RVE_ERR_CUDA",
+    3: "RVE_ERR_OOM",
+    4: "RVE_ERR_NOT_CONVERGED",
+    5: "RVE_ERR_NAN",
+    6: "RVE_ERR_STATE",
+    7: "RVE_ERR_UNSUPPORTED",
+}
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class Options(C.Structure):
+    _fields_ = [
+        ("precision", C.c_int),
+        ("green", C.c_int),
+        ("n_sub", C.c_int),
+        ("max_iter", C.c_int),
+        ("fixed_iters", C.c_int),
+        ("tol", C.c_double),
+        ("stream", C.c_void_p),
+        ("device", C.c_int),
+        ("alloc", ALLOC_FN),
+        ("free", FREE_FN),
+        ("alloc_ctx", C.c_void_p),
+        ("timing", C.c_int),
+    ]
+
+
+MATERIAL_FIELDS = [
+    "C11", "C12", "C13", "C33", "C44", "C66", "r0_ord", "r0_sup", "r0_twin", "K", "n", "Kt", "nt",
+    "Q_s", "Q_b", "b_s", "b_b", "h_diag", "h_off", "c", "d", "Kc", "fm", "eta",
+]
+
+
+class Material(C.Structure):
+    _fields_ = [(f, C.c_double) for f in MATERIAL_FIELDS]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f in MATERIAL_FIELDS}
+
+
+class Effective(C.Structure):
+    _fields_ = [
+        ("increment", C.c_int),
+        ("iterations", C.c_int),
+        ("time", C.c_double),
+        ("E", C.c_double * 6),
+        ("S", C.c_double * 6),
+        ("S_eq_of_mean", C.c_double),
+        ("mean_S_eq", C.c_double),
+        ("mean_f", C.c_double),
+        ("mean_v", C.c_double),
+        ("residual", C.c_double),
+        ("stress_residual", C.c_double),
+    ]
+
+    def as_dict(self):
+        return {
+            "increment": self.increment,
+            "iterations": self.iterations,
+            "time": self.time,
+            "E": np.array(self.E[:]),
+            "S": np.array(self.S[:]),
+            "S_eq_of_mean": self.S_eq_of_mean,
+            "mean_S_eq": self.mean_S_eq,
+            "mean_f": self.mean_f,
+            "mean_v": self.mean_v,
+            "residual": self.residual,
+            "stress_residual": self.stress_residual,
+        }
+
+
+class RVEError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+_lib = None
+
+EXPORTED = [
+    "rve_options_default", "rve_material_default", "rve_create", "rve_set_material",
+    "rve_set_mixed_load", "rve_step", "rve_get_effective", "rve_get_fields", "rve_save_state",
+    "rve_load_state", "rve_last_error", "rve_destroy", "rve_material_point", "rve_fft_r2c",
+    "rve_fft_c2r", "rve_label_voronoi", "rve_kernel_times", "rve_get_residuals",
+]
+
+
+def load_library(path: str | os.PathLike | None = None):
+    """Load librve.so (raises OSError when missing: build it with build_lib.build())."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = Path(path) if path else LIB_PATH
+    if not p.exists():
+        raise OSError(f"{p} not found; build it with paper_2402_09996_gb300.build_lib.build()")
+    lib = C.CDLL(str(p))
+    vp, i, d, sz = C.c_void_p, C.c_int, C.c_double, C.c_size_t
+    lib.rve_options_default.argtypes = [C.POINTER(Options)]
+    lib.rve_material_default.argtypes = [C.POINTER(Material)]
+    lib.rve_create.argtypes = [C.POINTER(vp), i, i, i, vp, i, i, vp, C.POINTER(Options)]
+    lib.rve_set_material.argtypes = [vp, C.POINTER(Material)]
+    lib.rve_set_mixed_load.argtypes = [vp, vp, vp, vp, d]
+    lib.rve_step.argtypes = [vp, i, C.POINTER(C.c_longlong)]
+    lib.rve_get_effective.argtypes = [vp, C.POINTER(Effective), C.POINTER(Effective), i, C.POINTER(i)]
+    lib.rve_get_fields.argtypes = [vp, i, vp, sz, i]
+    lib.rve_save_state.argtypes = [vp, vp, C.POINTER(sz)]
+    lib.rve_load_state.argtypes = [vp, vp, sz]
+    lib.rve_last_error.argtypes = [vp]
+    lib.rve_last_error.restype = C.c_char_p
+    lib.rve_destroy.argtypes = [vp]
+    lib.rve_destroy.restype = None
+    lib.rve_material_point.argtypes = [i, C.POINTER(Material), C.c_longlong, vp, vp, vp, vp, vp, d, i, vp]
+    lib.rve_fft_r2c.argtypes = [i, i, i, i, i, vp, vp, vp]
+    lib.rve_fft_c2r.argtypes = [i, i, i, i, i, vp, vp, vp]
+    lib.rve_label_voronoi.argtypes = [i, i, i, i, vp, vp, vp, vp, i, vp]
+    lib.rve_kernel_times.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong), i]
+    lib.rve_get_residuals.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double), i, C.POINTER(i)]
+    for name in EXPORTED:
+        getattr(lib, name).restype = C.c_int
+    lib.rve_options_default.restype = None
+    lib.rve_material_default.restype = None
+    lib.rve_last_error.restype = C.c_char_p
+    lib.rve_destroy.restype = None
+    _lib = lib
+    return lib
+
+
+def _check(status: int, handle=None):
+    if status != 0:
+        msg = _lib.rve_last_error(handle).decode(errors="replace")
+        raise RVEError(status, msg)
+
+
+def default_material() -> Material:
+    lib = load_library()
+    m = Material()
+    lib.rve_material_default(C.byref(m))
+    return m
+
+
+def default_options() -> Options:
+    lib = load_library()
+    o = Options()
+    lib.rve_options_default(C.byref(o))
+    return o
+
+
+def _torch_stream():
+    import torch
+
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class _TorchAllocator:
+    """Device allocations through torch's caching allocator on the current stream."""
+
+    def __init__(self, device: int):
+        import torch
+
+        self.torch = torch
+        self.device = device
+        self.stream = torch.cuda.current_stream(device)
+
+        def _alloc(nbytes, _ctx):
+            try:
+                return self.torch.cuda.caching_allocator_alloc(int(nbytes), self.device, self.stream)
+            except Exception:  # noqa: BLE001 - reported to the library as a NULL pointer
+                return None
+
+        def _free(ptr, _ctx):
+            if ptr:
+                self.torch.cuda.caching_allocator_delete(ptr)
+
+        self.alloc = ALLOC_FN(_alloc)
+        self.free = FREE_FN(_free)
+
+
+def _ptr(a) -> C.c_void_p:
+    """Device pointer of a torch tensor or host pointer of a C-contiguous numpy array."""
+    if a is None:
+        return C.c_void_p(None)
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return C.c_void_p(a.data_ptr())
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return C.c_void_p(a.ctypes.data)
+
+
+class RVE:
+    """One periodic voxel RVE solved on the GPU (wraps an rve_t handle).
+
+    grain_id: (nz, ny, nx) integer labels (x fastest), numpy (host) or torch CUDA tensor;
+    euler: (n_grains, 3) Bunge angles [rad].
+    """
+
+    def __init__(self, grain_id, euler, precision=FP64, green=GREEN_WILLOT, n_sub=0, tol=1e-6, max_iter=1000,
+                 fixed_iters=0, device=0, use_torch=True, timing=False):
+        self.lib = load_library()
+        euler = np.ascontiguousarray(np.asarray(euler, dtype=np.float64))
+        shape = tuple(grain_id.shape)
+        if len(shape) != 3:
+            raise ValueError("grain_id must have shape (nz, ny, nx)")
+        self.shape = shape
+        self.nvox = int(np.prod(shape))
+        opt = default_options()
+        opt.precision, opt.green, opt.n_sub = precision, green, n_sub
+        opt.tol, opt.max_iter, opt.fixed_iters, opt.device = tol, max_iter, fixed_iters, device
+        opt.timing = 1 if timing else 0
+        self._allocator = None
+        on_dev = 0
+        if use_torch:
+            import torch
+
+            with torch.cuda.device(device):
+                opt.stream = _torch_stream()
+                self._allocator = _TorchAllocator(device)
+            opt.alloc, opt.free = self._allocator.alloc, self._allocator.free
+        if hasattr(grain_id, "data_ptr"):
+            gid = grain_id.contiguous()
+            if str(gid.dtype) not in ("torch.int32", "torch.uint32"):
+                raise TypeError("device grain_id must be int32/uint32")
+            on_dev = 1 if gid.is_cuda else 0
+            if not gid.is_cuda:
+                gid = gid.numpy().astype(np.uint32)
+        else:
+            gid = np.ascontiguousarray(np.asarray(grain_id).astype(np.uint32))
+        self._gid_keepalive = gid
+        h = C.c_void_p()
+        nz, ny, nx = shape
+        st = self.lib.rve_create(C.byref(h), nx, ny, nz, _ptr(gid), on_dev, euler.shape[0], _ptr(euler), C.byref(opt))
+        _check(st, None)
+        self.h = h
+
+    # ---- configuration ------------------------------------------------------
+    def set_material(self, **kw):
+        m = default_material()
+        for k, v in kw.items():
+            if k not in MATERIAL_FIELDS:
+                raise KeyError(k)
+            setattr(m, k, float(v))
+        _check(self.lib.rve_set_material(self.h, C.byref(m)), self.h)
+
+    def set_mixed_load(self, Edot=(0, 0, 1e-3, 0, 0, 0), strain_ctrl=(0, 0, 1, 0, 0, 0), Sigma=(0,) * 6, dt=1.0):
+        e = np.ascontiguousarray(Edot, dtype=np.float64)
+        c = np.ascontiguousarray(strain_ctrl, dtype=np.uint8)
+        s = np.ascontiguousarray(Sigma, dtype=np.float64)
+        _check(self.lib.rve_set_mixed_load(self.h, _ptr(e), _ptr(c), _ptr(s), float(dt)), self.h)
+
+    # ---- solve ----------------------------------------------------------------
+    def step(self, n_increments=1) -> int:
+        it = C.c_longlong(0)
+        _check(self.lib.rve_step(self.h, int(n_increments), C.byref(it)), self.h)
+        return int(it.value)
+
+    def effective(self) -> dict:
+        e = Effective()
+        _check(self.lib.rve_get_effective(self.h, C.byref(e), None, 0, None), self.h)
+        return e.as_dict()
+
+    def history(self) -> list:
+        n = C.c_int(0)
+        _check(self.lib.rve_get_effective(self.h, None, None, 0, C.byref(n)), self.h)
+        arr = (Effective * max(1, n.value))()
+        _check(self.lib.rve_get_effective(self.h, None, arr, n.value, None), self.h)
+        return [arr[i].as_dict() for i in range(n.value)]
+
+    def field(self, which: int, out=None):
+        """Committed field as float64 (components, nz, ny, nx); `out` may be a CUDA tensor."""
+        comps = FIELD_COMPONENTS[which]
+        if out is None:
+            out = np.empty((comps,) + self.shape, dtype=np.float64)
+            dev = 0
+        else:
+            dev = 1 if getattr(out, "is_cuda", False) else 0
+        nbytes = comps * self.nvox * 8
+        _check(self.lib.rve_get_fields(self.h, which, _ptr(out), nbytes, dev), self.h)
+        return out
+
+    def residuals(self):
+        """(e_eq, c_F) arrays of every fixed-point iteration of the latest increment."""
+        n = C.c_int(0)
+        _check(self.lib.rve_get_residuals(self.h, None, None, 0, C.byref(n)), self.h)
+        e = (C.c_double * max(1, n.value))()
+        c = (C.c_double * max(1, n.value))()
+        _check(self.lib.rve_get_residuals(self.h, e, c, n.value, None), self.h)
+        return np.array(e[: n.value]), np.array(c[: n.value])
+
+    def kernel_times(self, reset=False) -> dict:
+        """{kernel: (milliseconds, launches)} accumulated with CUDA events (timing=True)."""
+        ms = (C.c_double * len(KERNELS))()
+        n = (C.c_longlong * len(KERNELS))()
+        _check(self.lib.rve_kernel_times(self.h, ms, n, 1 if reset else 0), self.h)
+        return {k: (ms[i], n[i]) for i, k in enumerate(KERNELS)}
+
+    def save_state(self) -> bytes:
+        n = C.c_size_t(0)
+        _check(self.lib.rve_save_state(self.h, None, C.byref(n)), self.h)
+        buf = C.create_string_buffer(n.value)
+        _check(self.lib.rve_save_state(self.h, buf, C.byref(n)), self.h)
+        return buf.raw
+
+    def load_state(self, blob: bytes):
+        _check(self.lib.rve_load_state(self.h, C.c_char_p(blob), len(blob)), self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.rve_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+# ---- kernel-level entry points ----------------------------------------------
+def material_point(R, eps_n, eps, state, dt, n_sub, precision=FP64, **material):
+    """One increment of the per-voxel constitutive update on CUDA tensors.
+
+    R (nvox, 9), eps_n/eps (6, nvox), state (34, nvox) updated in place; returns sigma (6, nvox).
+    """
+    import torch
+
+    lib = load_library()
+    m = default_material()
+    for k, v in material.items():
+        setattr(m, k, float(v))
+    sigma = torch.empty_like(eps)
+    nvox = eps.shape[1]
+    st = lib.rve_material_point(precision, C.byref(m), nvox, _ptr(R), _ptr(eps_n), _ptr(eps), _ptr(state),
+                                _ptr(sigma), float(dt), int(n_sub), _torch_stream())
+    _check(st, None)
+    return sigma
+
+
+def fft_r2c(real, precision=FP64):
+    """Forward 3-D R2C transform of (ncomp, nz, ny, nx) CUDA tensor -> (ncomp, nz, ny, nx//2+1) complex."""
+    import torch
+
+    lib = load_library()
+    ncomp, nz, ny, nx = real.shape
+    cdt = torch.complex128 if precision == FP64 else torch.complex64
+    out = torch.empty((ncomp, nz, ny, nx // 2 + 1), dtype=cdt, device=real.device)
+    _check(lib.rve_fft_r2c(precision, nx, ny, nz, ncomp, _ptr(real.contiguous()), _ptr(out), _torch_stream()))
+    return out
+
+
+def fft_c2r(spec, nx, precision=FP64):
+    """Unnormalised inverse of fft_r2c; `spec` is consumed (overwritten)."""
+    import torch
+
+    lib = load_library()
+    ncomp, nz, ny, _ = spec.shape
+    rdt = torch.float64 if precision == FP64 else torch.float32
+    out = torch.empty((ncomp, nz, ny, nx), dtype=rdt, device=spec.device)
+    _check(lib.rve_fft_c2r(precision, nx, ny, nz, ncomp, _ptr(spec), _ptr(out), _torch_stream()))
+    return out
+
+
+def label_voronoi(inputs, out=None):
+    """Grain-ID map of an inputs.RVEInputs, computed on the GPU; numpy (nz, ny, nx) uint32
+    unless `out` (a CUDA int32 tensor) is given."""
+    lib = load_library()
+    nz, ny, nx = inputs.shape
+    seeds = np.ascontiguousarray(inputs.seeds, dtype=np.float64)
+    tw = np.ascontiguousarray(inputs.twinned, dtype=np.uint8)
+    nrm = np.ascontiguousarray(inputs.twin_normal, dtype=np.float64)
+    if out is None:
+        res = np.empty((nz, ny, nx), dtype=np.uint32)
+        st = lib.rve_label_voronoi(nx, ny, nz, seeds.shape[0], _ptr(seeds), _ptr(tw), _ptr(nrm), _ptr(res), 0, None)
+    else:
+        res = out
+        st = lib.rve_label_voronoi(nx, ny, nz, seeds.shape[0], _ptr(seeds), _ptr(tw), _ptr(nrm), _ptr(res), 1,
+                                   _torch_stream())
+    _check(st, None)
+    return res

@@ -188,6 +188,7 @@ struct rve_s {
   void *ep = nullptr, *v = nullptr, *al = nullptr, *eps_n = nullptr, *sig_n = nullptr;
   uint32_t* grain = nullptr;
   void* Rg = nullptr;
+  void* root_tab = nullptr;  // 2 * kRootTab rate-root deviations (slip n, twin nt)
   void *tw_x = nullptr, *tw_y = nullptr, *tw_z = nullptr;
   void *kx = nullptr, *ky = nullptr, *kz = nullptr;
   double* partial = nullptr;
@@ -415,7 +416,7 @@ rve_status alloc_fields(rve_s* h) {
   // launch geometry
   h->L = std::max(1, x_threads() / h->nx);
   h->xgrid = (int)((h->NL + h->L - 1) / h->L);
-  h->xsmem = (size_t)(h->nx + 6 * h->L * h->nx) * 2 * sizeof(T);
+  h->xsmem = (size_t)(h->nx + 6 * h->L * h->nx) * 2 * sizeof(T) + 2 * kRootTab * sizeof(T);
   const size_t budget = 96 * 1024;
   h->yHC = (int)std::max<size_t>(1, std::min<size_t>(16, (budget / (2 * 2 * sizeof(T))) / h->ny));
   h->yHC = std::min(h->yHC, h->H);
@@ -434,6 +435,43 @@ rve_status alloc_fields(rve_s* h) {
   return RVE_OK;
 }
 
+// Deviation table of the regularised-rate root (constitutive.cuh, reg_rate_tab): on
+// kRootTab nodes lb in [-kRootSpan, kRootSpan], d = log2 u* - min(0, -lb) where u* in
+// (0, 1] solves u^n + 2^lb u = 1 (bisection to double precision).
+void root_table(double n, double* out) {
+  for (int k = 0; k < kRootTab; ++k) {
+    const double lb = -kRootSpan + 2.0 * kRootSpan * (double)k / (double)(kRootTab - 1);
+    const double beta = std::exp2(lb);
+    double lo = 0.0, hi = 1.0;
+    for (int i = 0; i < 200; ++i) {
+      const double mid = 0.5 * (lo + hi);
+      if (std::pow(mid, n) + beta * mid - 1.0 > 0.0) hi = mid;
+      else lo = mid;
+    }
+    out[k] = std::log2(0.5 * (lo + hi)) - std::min(0.0, -lb);
+  }
+}
+
+template <typename T>
+std::vector<T> root_tables(const rve_material& m) {
+  std::vector<double> d(2 * kRootTab);
+  root_table(m.n, d.data());
+  root_table(m.nt, d.data() + kRootTab);
+  return std::vector<T>(d.begin(), d.end());
+}
+
+template <typename T>
+rve_status upload_root_tab(rve_s* h) {
+  const std::vector<T> t = root_tables<T>(h->mat);
+  if (!h->root_tab) {
+    rve_status s = dalloc(h, &h->root_tab, t.size() * sizeof(T));
+    if (s) return s;
+  }
+  RVE_CUDA(h, cudaMemcpyAsync(h->root_tab, t.data(), t.size() * sizeof(T), cudaMemcpyHostToDevice, h->stream));
+  RVE_CUDA(h, cudaStreamSynchronize(h->stream));
+  return RVE_OK;
+}
+
 template <typename T>
 XArgs<T> x_args(rve_s* h, const void* in, void* out, int it) {
   XArgs<T> a;
@@ -446,6 +484,7 @@ XArgs<T> x_args(rve_s* h, const void* in, void* out, int it) {
   a.ep = (T*)h->ep; a.v = (T*)h->v; a.al = (T*)h->al; a.eps_n = (T*)h->eps_n; a.sig_n = (T*)h->sig_n;
   a.grain = h->grain;
   a.Rg = (const T*)h->Rg;
+  a.root_tab = (const T*)h->root_tab;
   a.M = make_mat<T>(h);
   // mixed load
   double M0[36];
@@ -553,6 +592,7 @@ void initial_increment(rve_s* h, double dE0[6]) {
 template <typename T>
 rve_status step_one(rve_s* h, long long* iters) {
   cudaStream_t s = h->stream;
+  const int np = rate_variant(h->mat.eta, is_small_int(h->mat.n), is_small_int(h->mat.nt));
   double dE0[6];
   initial_increment(h, dE0);
   // E^(0) into slot 0 of the device status record
@@ -571,7 +611,7 @@ rve_status step_one(rve_s* h, long long* iters) {
   for (int it = 0;; ++it) {
     XArgs<T> xa = x_args<T>(h, h->spec_cur, h->spec_nxt, it);
     tstart(h, RVE_K_XPASS);
-    RVE_CUDA(h, launch_xpass<T>(xa, false, h->xgrid, h->xsmem, s));
+    RVE_CUDA(h, launch_xpass<T>(xa, np, false, h->xgrid, h->xsmem, s));
     tstop(h, RVE_K_XPASS);
     LineArgs<T> ya = y_args<T>(h, h->spec_nxt);
     tstart(h, RVE_K_YFWD);
@@ -605,7 +645,7 @@ rve_status step_one(rve_s* h, long long* iters) {
       for (int c = 0; c < 6; ++c) E[c] = st.E[it & 1][c];
       XArgs<T> ca = x_args<T>(h, h->spec_cur, nullptr, it);
       tstart(h, RVE_K_COMMIT);
-      RVE_CUDA(h, launch_xpass<T>(ca, true, h->xgrid, h->xsmem, s));
+      RVE_CUDA(h, launch_xpass<T>(ca, np, true, h->xgrid, h->xsmem, s));
       tstop(h, RVE_K_COMMIT);
       RVE_CUDA(h, cudaMemcpyAsync(h->st_host, h->st, sizeof(IterStatus), cudaMemcpyDeviceToHost, s));
       RVE_CUDA(h, cudaStreamSynchronize(s));
@@ -788,9 +828,15 @@ rve_status rve_create(rve_t* out, int nx, int ny, int nz, const uint32_t* grain_
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) { s = cuda_fail(h, e, "grain_id upload"); rve_destroy(h); return s; }
   if (o.precision == RVE_FP64) {
-    if ((s = upload_tables<double>(h)) || (s = alloc_fields<double>(h))) { rve_destroy(h); return s; }
+    if ((s = upload_tables<double>(h)) || (s = alloc_fields<double>(h)) || (s = upload_root_tab<double>(h))) {
+      rve_destroy(h);
+      return s;
+    }
   } else {
-    if ((s = upload_tables<float>(h)) || (s = alloc_fields<float>(h))) { rve_destroy(h); return s; }
+    if ((s = upload_tables<float>(h)) || (s = alloc_fields<float>(h)) || (s = upload_root_tab<float>(h))) {
+      rve_destroy(h);
+      return s;
+    }
   }
   if (o.timing)
     for (int k = 0; k < RVE_K_COUNT; ++k) {
@@ -811,7 +857,7 @@ rve_status rve_set_material(rve_t h, const rve_material* m) {
   if (s) return s;
   h->mat = *m;
   reference_medium(h->mat, &h->lam0, &h->mu0);
-  return RVE_OK;
+  return h->opt.precision == RVE_FP64 ? upload_root_tab<double>(h) : upload_root_tab<float>(h);
 }
 
 rve_status rve_set_mixed_load(rve_t h, const double Edot[6], const uint8_t ctrl[6], const double Sigma[6], double dt) {
@@ -984,17 +1030,26 @@ rve_status rve_material_point(int precision, const rve_material* mat, long long 
   rve_status s = check_material(&tmp, *mat);
   if (s) return fail(nullptr, s, tmp.err);
   reference_medium(tmp.mat, &tmp.lam0, &tmp.mu0);
+  if (precision != RVE_FP64 && precision != RVE_FP32) return fail(nullptr, RVE_ERR_INVALID_ARG, "bad precision");
   cudaStream_t st = stream ? (cudaStream_t)stream : cudaStreamPerThread;
+  tmp.stream = st;
+  const int np = rate_variant(mat->eta, is_small_int(mat->n), is_small_int(mat->nt));
+  s = precision == RVE_FP64 ? upload_root_tab<double>(&tmp) : upload_root_tab<float>(&tmp);
+  if (s) {
+    release(&tmp);
+    return fail(nullptr, s, tmp.err);
+  }
   cudaError_t e;
   if (precision == RVE_FP64)
-    e = launch_material_point<double>(make_mat<double>(&tmp), nvox, (const double*)R, (const double*)eps_n,
-                                      (const double*)eps, (double*)state, (double*)sigma, dt, n_sub, st);
-  else if (precision == RVE_FP32)
-    e = launch_material_point<float>(make_mat<float>(&tmp), nvox, (const float*)R, (const float*)eps_n,
-                                     (const float*)eps, (float*)state, (float*)sigma, (float)dt, n_sub, st);
+    e = launch_material_point<double>(make_mat<double>(&tmp), np, nvox, (const double*)R, (const double*)eps_n,
+                                      (const double*)eps, (double*)state, (double*)sigma, dt, n_sub,
+                                      (const double*)tmp.root_tab, st);
   else
-    return fail(nullptr, RVE_ERR_INVALID_ARG, "bad precision");
+    e = launch_material_point<float>(make_mat<float>(&tmp), np, nvox, (const float*)R, (const float*)eps_n,
+                                     (const float*)eps, (float*)state, (float*)sigma, (float)dt, n_sub,
+                                     (const float*)tmp.root_tab, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  release(&tmp);
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "material_point");
   return RVE_OK;
 }

@@ -15,6 +15,11 @@
 //   eps_p_dot = (1 - sum f) sum_s gdot_s m_s + sum_b gdot_b m_b,  v_dot = |gdot|.
 // Integration: n_sub classical RK4 steps along the linear strain path of the
 // increment (Sec. 3, "explicit ... Runge-Kutta 4th order").
+//
+// Template parameter NP selects how the regularised rates are solved:
+//   NP > 0   eta > 0 and n = nt = NP (compile-time power): table start, branch-free;
+//   NP = -1  eta > 0 and integer n, nt (run-time powers):   table start, branch-free;
+//   NP = 0   anything else (eta = 0 or non-integer exponents): generic per-system solve.
 #pragma once
 
 #include "rve_common.cuh"
@@ -84,16 +89,49 @@ __device__ __forceinline__ void add_schmid(int s, T w, T* acc) {
   acc[5] += h * (n0 * l1 + n1 * l0);
 }
 
-// z^n for a small positive integer n (binary powering over a fixed 6-bit loop).
+// ---------------------------------------------------------------- powers -------------
+// z^n for a small positive integer known at run time (loop).
 template <typename T>
 __device__ __forceinline__ T ipow(T z, int n) {
   T r = T(1), b = z;
-#pragma unroll
-  for (int bit = 0; bit < 6; ++bit) {
-    if ((n >> bit) & 1) r *= b;
+  while (n) {
+    if (n & 1) r *= b;
     b *= b;
+    n >>= 1;
   }
   return r;
+}
+
+// z^n for an integer 1 <= n < 64 without branches (selects over a fixed 6-bit loop).
+template <typename T>
+__device__ __forceinline__ T ipow_sel(T z, int n) {
+  T r = T(1), b = z;
+#pragma unroll
+  for (int bit = 0; bit < 6; ++bit) {
+    const T rb = r * b;
+    r = ((n >> bit) & 1) ? rb : r;
+    b = b * b;
+  }
+  return r;
+}
+
+// z^N for a compile-time N >= 1 (binary powering unrolled by the compiler).
+template <int N, typename T>
+__device__ __forceinline__ T cpow(T z) {
+  if constexpr (N == 1) {
+    return z;
+  } else if constexpr (N % 2 == 0) {
+    const T h = cpow<N / 2, T>(z);
+    return h * h;
+  } else {
+    return z * cpow<N - 1, T>(z);
+  }
+}
+
+template <typename T, int NP>
+__device__ __forceinline__ T zpow(T z, int n_int) {
+  if constexpr (NP > 0) return cpow<NP, T>(z);
+  else return ipow_sel<T>(z, n_int);
 }
 
 template <typename T>
@@ -111,24 +149,61 @@ template <typename T> __device__ __forceinline__ T fast_div(T a, T b);
 template <> __device__ __forceinline__ float fast_div<float>(float a, float b) { return __fdividef(a, b); }
 template <> __device__ __forceinline__ double fast_div<double>(double a, double b) { return a / b; }
 
-// Newton iterations after the starting point (enough for round-off in either precision,
-// see reg_rate).
+// ---------------------------------------------------------------- rate roots ---------
+// The regularised rate rho >= 0 solves rho = P < (a - eta rho) / Kn >^n  (Sec. 4), and
+// rho = 0 when a <= 0 or P <= 0.  With z = (a - eta rho)/Kn the root solves
+// phi(z) = c z^n + Kn z - a = 0, c = eta P, and rho = P z^n.  Scaling z = zB u with
+// zB = (a/c)^(1/n) leaves u^n + beta u - 1 = 0, beta = Kn zB / a, whose root u*(beta)
+// depends on log2(beta) alone.  Its deviation d = log2 u* - min(0, -log2 beta) from the
+// two asymptotes is tabulated on kRootTab nodes over [-kRootSpan, kRootSpan] (one node
+// at 0, where the asymptotes cross); linear interpolation starts Newton within 0.15 %,
+// so a fixed number of Newton steps reaches round-off (2 in float, 4 in double) and the
+// solve has no data-dependent branch.  Logarithms are base 2.
+
+template <typename T> struct TabNewton;
+template <> struct TabNewton<float> { static constexpr int value = 2; };
+template <> struct TabNewton<double> { static constexpr int value = 4; };
+
+// Branch-free solve (eta > 0, integer exponent): inactive systems run the same arithmetic
+// on a dummy positive argument and return 0, so all systems of a stage form one basic
+// block the compiler can interleave.  tab: kRootTab deviations for this exponent.
+template <typename T, int NP>
+__device__ __forceinline__ T reg_rate_tab(T a, T P, T Kn, T n, int n_int, T inv_n, T lg_Kn, T eta, T lg_eta,
+                                          T lg_P, const T* tab) {
+  const bool on = (a > T(0)) && (P > T(0));
+  const T aa = on ? a : T(1);
+  const T c = eta * (on ? P : T(1));
+  const T la = fast_log2<T>(aa);
+  const T lzB = (la - lg_eta - (on ? lg_P : T(0))) * inv_n;
+  const T lb = lg_Kn + lzB - la;
+  T lbc = lb < T(-kRootSpan) ? T(-kRootSpan) : lb;
+  lbc = lbc > T(kRootSpan) ? T(kRootSpan) : lbc;
+  const T t = (lbc + T(kRootSpan)) * T((kRootTab - 1) / (2.0 * kRootSpan));
+  int i = (int)t;
+  i = i > kRootTab - 2 ? kRootTab - 2 : i;
+  const T f = t - T(i);
+  const T d = tab[i] + f * (tab[i + 1] - tab[i]);
+  T z = fast_exp2<T>(lzB + (lb > T(0) ? -lb : T(0)) + d);
+#pragma unroll
+  for (int it = 0; it < TabNewton<T>::value; ++it) {
+    const T zn1 = zpow<T, (NP > 0 ? NP - 1 : 0)>(z, n_int - 1);
+    const T phi = c * zn1 * z + Kn * z - aa;
+    z = z - fast_div<T>(phi, n * c * zn1 + Kn);
+  }
+  z = z > T(0) ? z : T(0);
+  return on ? P * zpow<T, NP>(z, n_int) : T(0);
+}
+
+// Generic solve (any eta >= 0 and exponent n >= 1): per-system branch, a smooth-minimum
+// start u0 = (1 + beta^m)^(-1/m) of the asymptotes (m makes it exact at beta = 1; within
+// 5 % for n >= 1.5) and a fixed Newton count (4 in float, 6 in double).
 template <typename T> struct NewtonSteps;
 template <> struct NewtonSteps<float> { static constexpr int value = 4; };
 template <> struct NewtonSteps<double> { static constexpr int value = 6; };
 
-// Non-negative rho with rho = P < (a - eta rho) / Kn >^n  (Sec. 4, regularised flow);
-// rho = 0 when a <= 0 or P <= 0.
-// With z = (a - eta rho)/Kn the root solves phi(z) = c z^n + Kn z - a = 0, c = eta P.
-// Scaling z = zB u with zB = (a/c)^(1/n) leaves u^n + beta u - 1 = 0, beta = Kn zB / a,
-// whose root is close (within 5% for n >= 1.5) to the smooth minimum
-// u0 = (1 + beta^m)^(-1/m) of its two asymptotes 1 and 1/beta, with m chosen so that u0
-// is exact at beta = 1.  A fixed number of Newton steps then reaches round-off
-// (4 in float, 6 in double for beta in [1e-8, 1e8]), so the solve has no data-dependent
-// loop.  Logarithms are base 2.
 template <typename T>
-__device__ __forceinline__ T reg_rate(T a, T P, T Kn, T n, int n_int, T inv_n, T m, T lg_Kn, T eta,
-                                      T lg_eta, T lg_P) {
+__device__ __forceinline__ T reg_rate(T a, T P, T Kn, T n, int n_int, T inv_n, T m, T lg_Kn, T eta, T lg_eta,
+                                      T lg_P) {
   if (!(a > T(0)) || !(P > T(0))) return T(0);
   if (!(eta > T(0))) return P * powT<T>(a / Kn, n, n_int);
   const T c = eta * P;
@@ -149,12 +224,14 @@ __device__ __forceinline__ T reg_rate(T a, T P, T Kn, T n, int n_int, T inv_n, T
   return P * powT<T>(z, n, n_int);
 }
 
-// One RK4 stage: evaluates the rates at elastic strain e0 + s*de - yt.ep and state yt,
-// adds wacc * rates to acc and overwrites yt with y0 + cnext * rates.
-template <typename T>
+// ---------------------------------------------------------------- RK4 stage ----------
+// Evaluates the rates at elastic strain e0 + s*de - yt.ep and state yt, adds
+// wacc * rates to acc and overwrites yt with y0 + cnext * rates.
+// tab: 2*kRootTab deviations (slip exponent n, then twin exponent nt), NP != 0 only.
+template <typename T, int NP>
 __device__ __forceinline__ void rk_stage(const MatDev<T>& M, const T* e0, const T* de, T s,
-                                         const MPState<T>& y0, MPState<T>& yt, MPState<T>& acc,
-                                         T wacc, T cnext) {
+                                         const MPState<T>& y0, MPState<T>& yt, MPState<T>& acc, T wacc,
+                                         T cnext, const T* tab) {
   T e[6], sg[6];
 #pragma unroll
   for (int c = 0; c < 6; ++c) e[c] = e0[c] + s * de[c] - yt.ep[c];
@@ -177,30 +254,43 @@ __device__ __forceinline__ void rk_stage(const MatDev<T>& M, const T* e0, const 
   T fm_left = M.fm - ftot;
   fm_left = fm_left > T(0) ? fm_left : T(0);
   const T Ptw = (M.Kc * T(0.70710678118654752440)) * fm_left;
-  const T lg_Ptw = Ptw > T(0) ? fast_log2<T>(Ptw) : T(0);
+  const T lg_Ptw = fast_log2<T>(Ptw > T(0) ? Ptw : T(1));
   const T dq = M.h_diag - M.h_off;
+  T te[12], rho[16];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    te[k] = resolved<T>(k, sg) - M.c * yt.al[k];
+    const T a = fabs(te[k]) - (M.r0[k] + M.Q_s * (M.h_off * Sslip + dq * g[k]));
+    if constexpr (NP != 0)
+      rho[k] = reg_rate_tab<T, NP>(a, T(1), M.K, M.n, M.n_int, M.inv_n, M.lg_K, M.eta, M.lg_eta, T(0), tab);
+    else
+      rho[k] = reg_rate<T>(a, T(1), M.K, M.n, M.n_int, M.inv_n, M.sm, M.lg_K, M.eta, M.lg_eta, T(0));
+  }
+#pragma unroll
+  for (int k = 12; k < 16; ++k) {
+    const T a = resolved<T>(k, sg) - (M.r0[k] + M.Q_b * (M.h_off * Stw + dq * g[k]));
+    if constexpr (NP != 0)
+      rho[k] = reg_rate_tab<T, NP>(a, Ptw, M.Kt, M.nt, M.nt_int, M.inv_nt, M.lg_Kt, M.eta, M.lg_eta, lg_Ptw,
+                                   tab + kRootTab);
+    else
+      rho[k] = reg_rate<T>(a, Ptw, M.Kt, M.nt, M.nt_int, M.inv_nt, M.smt, M.lg_Kt, M.eta, M.lg_eta, lg_Ptw);
+  }
   T dep[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
 #pragma unroll
   for (int k = 0; k < 12; ++k) {
-    const T te = resolved<T>(k, sg) - M.c * yt.al[k];
-    const T r = M.r0[k] + M.Q_s * (M.h_off * Sslip + dq * g[k]);
-    const T a = fabs(te) - r;
-    const T rho = reg_rate<T>(a, T(1), M.K, M.n, M.n_int, M.inv_n, M.sm, M.lg_K, M.eta, M.lg_eta, T(0));
-    const T gd = te < T(0) ? -rho : rho;
+    const T gd = te[k] < T(0) ? -rho[k] : rho[k];
     add_schmid<T>(k, gd * wslip, dep);
-    const T ald = gd - M.d * rho * yt.al[k];
-    acc.v[k] += wacc * rho;
-    yt.v[k] = y0.v[k] + cnext * rho;
+    const T ald = gd - M.d * rho[k] * yt.al[k];
+    acc.v[k] += wacc * rho[k];
+    yt.v[k] = y0.v[k] + cnext * rho[k];
     acc.al[k] += wacc * ald;
     yt.al[k] = y0.al[k] + cnext * ald;
   }
 #pragma unroll
   for (int k = 12; k < 16; ++k) {
-    const T a = resolved<T>(k, sg) - (M.r0[k] + M.Q_b * (M.h_off * Stw + dq * g[k]));
-    const T rho = reg_rate<T>(a, Ptw, M.Kt, M.nt, M.nt_int, M.inv_nt, M.smt, M.lg_Kt, M.eta, M.lg_eta, lg_Ptw);
-    add_schmid<T>(k, rho, dep);
-    acc.v[k] += wacc * rho;
-    yt.v[k] = y0.v[k] + cnext * rho;
+    add_schmid<T>(k, rho[k], dep);
+    acc.v[k] += wacc * rho[k];
+    yt.v[k] = y0.v[k] + cnext * rho[k];
   }
 #pragma unroll
   for (int c = 0; c < 6; ++c) {
@@ -297,9 +387,9 @@ __device__ __forceinline__ void to_sample(const T* R, const T* s, T* out) {
 
 // Integrates one voxel over the increment [t_n, t_n + dt] (strain eps_n -> eps, sample
 // frame) and returns the sample-frame stress at t_n + dt; y is updated in place.
-template <typename T>
+template <typename T, int NP>
 __device__ __forceinline__ void mc_voxel(const MatDev<T>& M, const T* R, const T* eps_n, const T* eps,
-                                         MPState<T>& y, T dt, int nsub, T* sig) {
+                                         MPState<T>& y, T dt, int nsub, T* sig, const T* tab) {
   T e0[6], e1[6], de[6];
   to_crystal<T>(R, eps_n, e0);
   to_crystal<T>(R, eps, e1);
@@ -324,7 +414,7 @@ __device__ __forceinline__ void mc_voxel(const MatDev<T>& M, const T* R, const T
         const T s = stg == 0 ? s0 : (stg == 3 ? s1 : sh);
         const T wacc = (stg == 0 || stg == 3) ? T(1) : T(2);
         const T cnext = stg < 2 ? T(0.5) * h : (stg == 2 ? h : T(0));
-        rk_stage<T>(M, e0, de, s, y, yt, acc, wacc, cnext);
+        rk_stage<T, NP>(M, e0, de, s, y, yt, acc, wacc, cnext, tab);
       }
       const T w = h / T(6);
 #pragma unroll

@@ -1,5 +1,6 @@
-// Definitions of the launch wrappers; included once per precision by kernels_f32.cu
-// and kernels_f64.cu with RVE_T set to the field type.
+// Definitions of the launch wrappers, explicitly instantiated by kernels_f32.cu /
+// kernels_f64.cu (FFT passes and helpers) and by xpass_<precision>_np<NP>.cu (the
+// constitutive kernels, one rate-solve variant per translation unit).
 #pragma once
 
 #include "launch.h"
@@ -13,19 +14,34 @@ static cudaError_t set_smem(const void* fn, size_t smem) {
   return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-template <typename T>
-cudaError_t launch_xpass(const XArgs<T>& a, bool commit, int grid, size_t smem, cudaStream_t s) {
+template <typename T, int NP>
+cudaError_t launch_xpass_np(const XArgs<T>& a, bool commit, int grid, size_t smem, cudaStream_t s) {
   if (commit) {
-    cudaError_t e = set_smem<T>((const void*)k_xpass<T, true>, smem);
+    cudaError_t e = set_smem<T>((const void*)k_xpass<T, true, NP>, smem);
     if (e != cudaSuccess) return e;
-    k_xpass<T, true><<<grid, kXThreads, smem, s>>>(a);
+    k_xpass<T, true, NP><<<grid, kXThreads, smem, s>>>(a);
   } else {
-    cudaError_t e = set_smem<T>((const void*)k_xpass<T, false>, smem);
+    cudaError_t e = set_smem<T>((const void*)k_xpass<T, false, NP>, smem);
     if (e != cudaSuccess) return e;
-    k_xpass<T, false><<<grid, kXThreads, smem, s>>>(a);
+    k_xpass<T, false, NP><<<grid, kXThreads, smem, s>>>(a);
   }
   return cudaGetLastError();
 }
+
+template <typename T, int NP>
+cudaError_t launch_material_point_np(const MatDev<T>& M, long long nvox, const T* R, const T* eps_n, const T* eps,
+                                     T* state, T* sigma, T dt, int nsub, const T* root_tab, cudaStream_t s) {
+  if (nvox <= 0) return cudaSuccess;
+  const int thr = 128;
+  const long long grid = (nvox + thr - 1) / thr;
+  k_material_point<T, NP><<<(unsigned)grid, thr, 0, s>>>(M, nvox, R, eps_n, eps, state, sigma, dt, nsub, root_tab);
+  return cudaGetLastError();
+}
+
+#define RVE_INSTANTIATE_X(T, NP)                                                                                \
+  template cudaError_t launch_xpass_np<T, NP>(const XArgs<T>&, bool, int, size_t, cudaStream_t);              \
+  template cudaError_t launch_material_point_np<T, NP>(const MatDev<T>&, long long, const T*, const T*, const T*, \
+                                                       T*, T*, T, int, const T*, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_line(const LineArgs<T>& a, int sign, dim3 grid, size_t smem, cudaStream_t s) {
@@ -77,16 +93,6 @@ cudaError_t launch_shift(C2<T>* spec, C2<T>* backup, long long NL, int H, const 
 }
 
 template <typename T>
-cudaError_t launch_material_point(const MatDev<T>& M, long long nvox, const T* R, const T* eps_n, const T* eps,
-                                  T* state, T* sigma, T dt, int nsub, cudaStream_t s) {
-  if (nvox <= 0) return cudaSuccess;
-  const int thr = 128;
-  const long long grid = (nvox + thr - 1) / thr;
-  k_material_point<T><<<(unsigned)grid, thr, 0, s>>>(M, nvox, R, eps_n, eps, state, sigma, dt, nsub);
-  return cudaGetLastError();
-}
-
-template <typename T>
 cudaError_t launch_xfft(const XFftArgs<T>& a, int sign, dim3 grid, size_t smem, cudaStream_t s) {
   if (sign < 0) {
     cudaError_t e = set_smem<T>((const void*)k_xfft<T, -1>, smem);
@@ -133,12 +139,9 @@ cudaError_t launch_von_mises(const T* sig6, double* dst, long long nvox, cudaStr
 }
 
 #define RVE_INSTANTIATE(T)                                                                                         \
-  template cudaError_t launch_xpass<T>(const XArgs<T>&, bool, int, size_t, cudaStream_t);                         \
   template cudaError_t launch_line<T>(const LineArgs<T>&, int, dim3, size_t, cudaStream_t);                       \
   template cudaError_t launch_zgreen<T>(const ZArgs<T>&, dim3, size_t, cudaStream_t);                             \
   template cudaError_t launch_shift<T>(C2<T>*, C2<T>*, long long, int, const double*, bool, cudaStream_t);        \
-  template cudaError_t launch_material_point<T>(const MatDev<T>&, long long, const T*, const T*, const T*, T*, T*, \
-                                                T, int, cudaStream_t);                                            \
   template cudaError_t launch_xfft<T>(const XFftArgs<T>&, int, dim3, size_t, cudaStream_t);                       \
   template cudaError_t launch_to_double<T>(const T*, double*, long long, cudaStream_t);                           \
   template cudaError_t launch_von_mises<T>(const T*, double*, long long, cudaStream_t);

@@ -12,8 +12,30 @@ template <typename T> struct LineArgs;
 template <typename T> struct ZArgs;
 template <typename T> struct XFftArgs;
 
+// Rate-solve variants of the constitutive kernels (see constitutive.cuh): NP = 10 for
+// eta > 0 and n = nt = 10, NP = 0 for anything else.
+inline int rate_variant(double eta, int n_int, int nt_int) {
+  return (eta > 0.0 && n_int == 10 && nt_int == 10) ? 10 : 0;
+}
+
+// Per-variant entry points (each instantiated in its own translation unit).
+template <typename T, int NP>
+cudaError_t launch_xpass_np(const XArgs<T>& a, bool commit, int grid, size_t smem, cudaStream_t s);
+template <typename T, int NP>
+cudaError_t launch_material_point_np(const MatDev<T>& M, long long nvox, const T* R, const T* eps_n, const T* eps,
+                                     T* state, T* sigma, T dt, int nsub, const T* root_tab, cudaStream_t s);
+
 template <typename T>
-cudaError_t launch_xpass(const XArgs<T>& a, bool commit, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_xpass(const XArgs<T>& a, int np, bool commit, int grid, size_t smem, cudaStream_t s) {
+  return np == 10 ? launch_xpass_np<T, 10>(a, commit, grid, smem, s) : launch_xpass_np<T, 0>(a, commit, grid, smem, s);
+}
+template <typename T>
+cudaError_t launch_material_point(const MatDev<T>& M, int np, long long nvox, const T* R, const T* eps_n, const T* eps,
+                                  T* state, T* sigma, T dt, int nsub, const T* root_tab, cudaStream_t s) {
+  return np == 10 ? launch_material_point_np<T, 10>(M, nvox, R, eps_n, eps, state, sigma, dt, nsub, root_tab, s)
+                  : launch_material_point_np<T, 0>(M, nvox, R, eps_n, eps, state, sigma, dt, nsub, root_tab, s);
+}
+
 template <typename T>
 cudaError_t launch_line(const LineArgs<T>& a, int sign, dim3 grid, size_t smem, cudaStream_t s);
 template <typename T>
@@ -21,9 +43,6 @@ cudaError_t launch_zgreen(const ZArgs<T>& a, dim3 grid, size_t smem, cudaStream_
 template <typename T>
 cudaError_t launch_shift(C2<T>* spec, C2<T>* backup, long long NL, int H, const double* dE, bool restore,
                          cudaStream_t s);
-template <typename T>
-cudaError_t launch_material_point(const MatDev<T>& M, long long nvox, const T* R, const T* eps_n, const T* eps,
-                                  T* state, T* sigma, T dt, int nsub, cudaStream_t s);
 template <typename T>
 cudaError_t launch_xfft(const XFftArgs<T>& a, int sign, dim3 grid, size_t smem, cudaStream_t s);
 template <typename T>

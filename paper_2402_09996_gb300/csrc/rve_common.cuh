@@ -77,4 +77,9 @@ struct IterStatus {
 
 constexpr int kNumRed = 9;  // reduction slots per CTA
 
+// Regularised-rate root table (constitutive.cuh): kRootTab nodes of log2(beta) over
+// [-kRootSpan, kRootSpan], one node at 0.
+constexpr int kRootTab = 257;
+constexpr double kRootSpan = 16.0;
+
 }  // namespace rve

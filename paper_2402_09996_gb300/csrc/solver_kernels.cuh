@@ -96,6 +96,7 @@ struct XArgs {
   T* sig_n;
   const uint32_t* grain;
   const T* Rg;
+  const T* root_tab;  // 2 * kRootTab rate-root deviations (slip, twin)
   MatDev<T> M;
   LoadDev ld;
   T dt;
@@ -107,15 +108,20 @@ struct XArgs {
 };
 
 constexpr int kXThreads = 128;
+// minimum resident x-pass CTAs per SM requested from the register allocator
+#ifndef RVE_X_MINB
+#define RVE_X_MINB 1
+#endif
 
-template <typename T, bool COMMIT>
-__global__ void __launch_bounds__(kXThreads) k_xpass(const XArgs<T> a) {
+template <typename T, bool COMMIT, int NP>
+__global__ void __launch_bounds__(kXThreads, RVE_X_MINB) k_xpass(const XArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[32][kNumRed];
   __shared__ int s_last;
   C2<T>* tw = reinterpret_cast<C2<T>*>(smem_raw);
   C2<T>* b0 = tw + a.nx;
   C2<T>* b1 = b0 + 3 * a.L * a.nx;
+  T* tab = reinterpret_cast<T*>(b1 + 3 * a.L * a.nx);  // 2 * kRootTab
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int nx = a.nx, H = a.H, half = nx / 2;
   const size_t NL = (size_t)a.ny * a.nz;
@@ -124,6 +130,8 @@ __global__ void __launch_bounds__(kXThreads) k_xpass(const XArgs<T> a) {
   const size_t nvox = (size_t)a.nvox;
 
   for (int i = tid; i < nx; i += nthr) tw[i] = a.tw[i];
+  if (NP != 0)
+    for (int i = tid; i < 2 * kRootTab; i += nthr) tab[i] = a.root_tab[i];
   // pack component pairs (2p, 2p+1) of each line as one complex Hermitian-extended
   // sequence Z = A + iB, so one complex inverse FFT yields both real lines
   for (int w = tid; w < 3 * nl * H; w += nthr) {
@@ -170,7 +178,7 @@ __global__ void __launch_bounds__(kXThreads) k_xpass(const XArgs<T> a) {
     const uint32_t g = a.grain[vox];
 #pragma unroll
     for (int i = 0; i < 9; ++i) R[i] = a.Rg[(size_t)g * 9 + i];
-    mc_voxel<T>(a.M, R, epsn, eps, y, a.dt, a.nsub, sig);
+    mc_voxel<T, NP>(a.M, R, epsn, eps, y, a.dt, a.nsub, sig, tab);
 #pragma unroll
     for (int c = 0; c < 6; ++c) acc[c] += (double)sig[c];
     if (COMMIT) {
@@ -470,10 +478,14 @@ __global__ void k_shift(C2<T>* spec, long long NL, int H, double d0, double d1, 
   p->x = (T)((double)p->x + d);
 }
 
-template <typename T>
+template <typename T, int NP>
 __global__ void k_material_point(const MatDev<T> M, long long nvox, const T* __restrict__ R,
                                  const T* __restrict__ eps_n, const T* __restrict__ eps, T* state,
-                                 T* sigma, T dt, int nsub) {
+                                 T* sigma, T dt, int nsub, const T* __restrict__ root_tab) {
+  __shared__ T tab[2 * kRootTab];
+  if (NP != 0)
+    for (int k = threadIdx.x; k < 2 * kRootTab; k += blockDim.x) tab[k] = root_tab[k];
+  __syncthreads();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nvox) return;
   const size_t n = (size_t)nvox;
@@ -492,7 +504,7 @@ __global__ void k_material_point(const MatDev<T> M, long long nvox, const T* __r
   for (int c = 0; c < 16; ++c) y.v[c] = state[(6 + c) * n + i];
 #pragma unroll
   for (int c = 0; c < 12; ++c) y.al[c] = state[(22 + c) * n + i];
-  mc_voxel<T>(M, r, en, e, y, dt, nsub, s);
+  mc_voxel<T, NP>(M, r, en, e, y, dt, nsub, s, tab);
 #pragma unroll
   for (int c = 0; c < 6; ++c) state[c * n + i] = y.ep[c];
 #pragma unroll

@@ -88,7 +88,9 @@ typedef enum {
   RVE_K_YINV = 3,   /* inverse y-FFT */
   RVE_K_COMMIT = 4, /* commit of the converged increment */
   RVE_K_SHIFT = 5,  /* uniform strain shift at the start of an increment */
-  RVE_K_COUNT = 6
+  RVE_K_IDLE = 6,   /* speculative iteration launches that returned at once because the
+                       increment had already converged (counted, time not accumulated) */
+  RVE_K_COUNT = 7
 } rve_kernel_kind;
 
 /* Constants of Sec. 3 and Sec. 4 (MPa, s).  rve_material_default() fills the

@@ -161,6 +161,13 @@ double smooth_min_exponent(double n) {
   return 1.0 / std::log2(1.0 / (0.5 * (lo + hi)));
 }
 
+// Iterations enqueued per host synchronisation (launches after convergence return at
+// once), and event slots for per-launch timing: 4 kernels per iteration + shift + commit.
+constexpr int kBatch = 8;
+constexpr int kTSlots = 4 * kBatch + 2;
+constexpr int kSlotShift = 4 * kBatch;
+constexpr int kSlotCommit = 4 * kBatch + 1;
+
 int default_nsub(double dt) {
   int n = 1;
   while (dt / n > 0.125 * (1.0 + 1e-12) && n < (1 << 20)) n *= 2;
@@ -184,7 +191,14 @@ struct rve_s {
   FftDim dx{}, dy{}, dz{};
   std::vector<double> euler;
   // device buffers
-  void *spec_cur = nullptr, *spec_nxt = nullptr, *P_prev = nullptr, *P_scr = nullptr, *backup = nullptr;
+  // Three strain spectra and three tau_hat spectra rotate during an increment; the
+  // committed pair (spec[sb]: strain at t_n, P[pb]: the tau_hat that produced it) is
+  // never written before the commit, so a failed increment leaves them intact.
+  void* spec[3] = {nullptr, nullptr, nullptr};
+  void* P[3] = {nullptr, nullptr, nullptr};
+  int sb = 0, pb = 0;
+  void* backup = nullptr;
+  double* dhist = nullptr;  // device (e_eq, c_F) history, 2 * max_iter
   void *ep = nullptr, *v = nullptr, *al = nullptr, *eps_n = nullptr, *sig_n = nullptr;
   uint32_t* grain = nullptr;
   void* Rg = nullptr;
@@ -208,8 +222,9 @@ struct rve_s {
   std::vector<rve_effective> hist;
   std::string err;
   // optional per-kernel event timing
-  cudaEvent_t ev_a[RVE_K_COUNT] = {}, ev_b[RVE_K_COUNT] = {};
-  bool ev_used[RVE_K_COUNT] = {};
+  cudaEvent_t ev_a[kTSlots] = {}, ev_b[kTSlots] = {};
+  int ev_kind[kTSlots] = {};
+  bool ev_used[kTSlots] = {};
   double k_ms[RVE_K_COUNT] = {};
   long long k_n[RVE_K_COUNT] = {};
   std::vector<double> res_e, res_c;  // convergence history of the latest increment
@@ -250,30 +265,39 @@ rve_status dalloc(rve_s* h, void** p, size_t bytes) {
   return RVE_OK;
 }
 
-void tstart(rve_s* h, int k) {
-  if (h->opt.timing) cudaEventRecord(h->ev_a[k], h->stream);
-}
-void tstop(rve_s* h, int k) {
+// Per-launch event timing (opt.timing): a launch records into an event slot; after the
+// next stream synchronisation tcollect folds the slots into per-kind totals.
+void tstart(rve_s* h, int slot, int kind) {
   if (!h->opt.timing) return;
-  cudaEventRecord(h->ev_b[k], h->stream);
-  h->ev_used[k] = true;
+  cudaEventRecord(h->ev_a[slot], h->stream);
+  h->ev_kind[slot] = kind;
 }
-// After a stream synchronisation: fold the recorded launches into the totals.
-void tcollect(rve_s* h) {
+void tstop(rve_s* h, int slot) {
   if (!h->opt.timing) return;
-  for (int k = 0; k < RVE_K_COUNT; ++k)
+  cudaEventRecord(h->ev_b[slot], h->stream);
+  h->ev_used[slot] = true;
+}
+// work_iters: iterations of the batch that did work; launches of later iterations returned
+// at once and are counted as RVE_K_IDLE.
+void tcollect(rve_s* h, int work_iters) {
+  if (!h->opt.timing) return;
+  for (int k = 0; k < kTSlots; ++k)
     if (h->ev_used[k]) {
-      float ms = 0.f;
-      if (cudaEventElapsedTime(&ms, h->ev_a[k], h->ev_b[k]) == cudaSuccess) {
-        h->k_ms[k] += ms;
-        h->k_n[k] += 1;
+      if (k < kSlotShift && k / 4 >= work_iters) {
+        h->k_n[RVE_K_IDLE] += 1;
+      } else {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, h->ev_a[k], h->ev_b[k]) == cudaSuccess) {
+          h->k_ms[h->ev_kind[k]] += ms;
+          h->k_n[h->ev_kind[k]] += 1;
+        }
       }
       h->ev_used[k] = false;
     }
 }
 
 void release(rve_s* h) {
-  for (int k = 0; k < RVE_K_COUNT; ++k) {
+  for (int k = 0; k < kTSlots; ++k) {
     if (h->ev_a[k]) cudaEventDestroy(h->ev_a[k]);
     if (h->ev_b[k]) cudaEventDestroy(h->ev_b[k]);
     h->ev_a[k] = h->ev_b[k] = nullptr;
@@ -399,7 +423,7 @@ rve_status alloc_fields(rve_s* h) {
   const size_t spec = (size_t)6 * h->NL * h->H * 2 * sizeof(T);
   const size_t fld = (size_t)h->nvox * sizeof(T);
   rve_status s;
-  void** bufs[] = {&h->spec_cur, &h->spec_nxt, &h->P_prev, &h->P_scr};
+  void** bufs[] = {&h->spec[0], &h->spec[1], &h->spec[2], &h->P[0], &h->P[1], &h->P[2]};
   for (void** b : bufs) {
     if ((s = dalloc(h, b, spec))) return s;
     RVE_CUDA(h, cudaMemsetAsync(*b, 0, spec, h->stream));
@@ -414,14 +438,26 @@ rve_status alloc_fields(rve_s* h) {
     RVE_CUDA(h, cudaMemsetAsync(*f.p, 0, fld * f.comps, h->stream));
   }
   // launch geometry
-  h->L = std::max(1, x_threads() / h->nx);
+  // x lines per CTA: enough to give every thread a voxel, up to 4 voxels per thread (a
+  // thread then integrates voxels of several lines, which evens out the elastic/plastic
+  // work between the CTA's warps) while keeping at least 2 CTAs per SM
+  {
+    const long long fill = (x_threads() + h->nx - 1) / h->nx;
+    const long long most = std::max<long long>(1, 4LL * x_threads() / h->nx);
+    const long long keep = std::max<long long>(1, h->NL / (2 * 152));
+    h->L = (int)std::max(fill, std::min(most, keep));
+  }
   h->xgrid = (int)((h->NL + h->L - 1) / h->L);
   h->xsmem = (size_t)(h->nx + 6 * h->L * h->nx) * 2 * sizeof(T) + 2 * kRootTab * sizeof(T);
   const size_t budget = 96 * 1024;
-  h->yHC = (int)std::max<size_t>(1, std::min<size_t>(16, (budget / (2 * 2 * sizeof(T))) / h->ny));
+  // y and z passes: tiles of HC kx values x 6 components (two buffers of padded lines);
+  // about 50 KB per CTA so that four CTAs share an SM
+  const size_t tile_budget = 50 * 1024;
+  (void)budget;
+  h->yHC = (int)std::max<size_t>(1, std::min<size_t>(16, tile_budget / (2 * 6 * 2 * sizeof(T) * (h->ny + 1))));
   h->yHC = std::min(h->yHC, h->H);
-  h->ysmem = (size_t)(h->ny + 2 * h->yHC * (h->ny + 1)) * 2 * sizeof(T);
-  h->zHC = (int)std::max<size_t>(1, std::min<size_t>(16, (budget / (2 * 2 * sizeof(T) * 6)) / h->nz));
+  h->ysmem = (size_t)(h->ny + 12 * h->yHC * (h->ny + 1)) * 2 * sizeof(T);
+  h->zHC = (int)std::max<size_t>(1, std::min<size_t>(16, tile_budget / (2 * 6 * 2 * sizeof(T) * (h->nz + 1))));
   h->zHC = std::min(h->zHC, h->H);
   h->zsmem = (size_t)(h->nz + 12 * h->zHC * (h->nz + 1)) * 2 * sizeof(T);
   const int zgrid = ((h->H + h->zHC - 1) / h->zHC) * h->ny;
@@ -432,6 +468,8 @@ rve_status alloc_fields(rve_s* h) {
   if ((s = dalloc(h, (void**)&h->st, sizeof(IterStatus)))) return s;
   RVE_CUDA(h, cudaMemsetAsync(h->st, 0, sizeof(IterStatus), h->stream));
   RVE_CUDA(h, cudaMallocHost((void**)&h->st_host, sizeof(IterStatus)));
+  const int max_iter = h->opt.max_iter > 0 ? h->opt.max_iter : 1000;
+  if ((s = dalloc(h, (void**)&h->dhist, (size_t)2 * max_iter * sizeof(double)))) return s;
   return RVE_OK;
 }
 
@@ -474,7 +512,7 @@ rve_status upload_root_tab(rve_s* h) {
 
 template <typename T>
 XArgs<T> x_args(rve_s* h, const void* in, void* out, int it) {
-  XArgs<T> a;
+  XArgs<T> a{};
   a.nx = h->nx; a.ny = h->ny; a.nz = h->nz; a.H = h->H; a.L = h->L;
   a.nvox = h->nvox;
   a.dx = h->dx;
@@ -511,27 +549,32 @@ XArgs<T> x_args(rve_s* h, const void* in, void* out, int it) {
   a.counter = h->counter;
   a.st = h->st;
   a.it = it;
+  a.done = out ? &h->st->done : nullptr;  // the commit (no output spectrum) always runs
   return a;
 }
 
 template <typename T>
 LineArgs<T> y_args(rve_s* h, void* spec) {
-  LineArgs<T> a;
+  LineArgs<T> a{};
   a.d = h->dy;
   a.tw = (const C2<T>*)h->tw_y;
   a.spec = (C2<T>*)spec;
   a.H = h->H;
   a.HC = h->yHC;
-  a.n_o2 = h->nz;
-  a.stride = h->H;
-  a.A = (long long)h->nz * h->ny * h->H;
-  a.B = (long long)h->ny * h->H;
+  // component-interleaved spectra: CTA (kx chunk, kz) transforms all 6 components
+  a.NC = 6;
+  a.hstride = 6;
+  a.n_o2 = 1;
+  a.stride = (long long)h->H * 6;
+  a.A = (long long)h->ny * h->H * 6;
+  a.B = 0;
+  a.done = &h->st->done;
   return a;
 }
 
 template <typename T>
 ZArgs<T> z_args(rve_s* h, void* spec, const void* Pp, void* Po, int it) {
-  ZArgs<T> a;
+  ZArgs<T> a{};
   a.nx = h->nx; a.ny = h->ny; a.nz = h->nz; a.H = h->H; a.HC = h->zHC;
   a.nvox = h->nvox;
   a.dz = h->dz;
@@ -546,6 +589,11 @@ ZArgs<T> z_args(rve_s* h, void* spec, const void* Pp, void* Po, int it) {
   a.lam0 = (T)h->lam0;
   a.mu0 = (T)h->mu0;
   a.invN = (T)(1.0 / (double)h->nvox);
+  a.conv.tol = h->opt.tol;
+  a.conv.fixed_iters = h->opt.fixed_iters;
+  a.conv.max_iter = h->opt.max_iter > 0 ? h->opt.max_iter : 1000;
+  a.conv.hist = h->dhist;
+  a.done = &h->st->done;
   a.partial = h->partial;
   a.counter = h->counter;
   a.st = h->st;
@@ -595,98 +643,121 @@ rve_status step_one(rve_s* h, long long* iters) {
   const int np = rate_variant(h->mat.eta, is_small_int(h->mat.n), is_small_int(h->mat.nt));
   double dE0[6];
   initial_increment(h, dE0);
-  // E^(0) into slot 0 of the device status record
+  // E^(0) into slot 0 of the device status record; clear the NaN flag and the decision
   for (int c = 0; c < 6; ++c) h->st_host->E[0][c] = h->E_n[c] + dE0[c];
-  h->st_host->nan_flag = 0;
   RVE_CUDA(h, cudaMemcpyAsync(h->st->E[0], h->st_host->E[0], 6 * sizeof(double), cudaMemcpyHostToDevice, s));
-  RVE_CUDA(h, cudaMemsetAsync(&h->st->nan_flag, 0, sizeof(int), s));
-  tstart(h, RVE_K_SHIFT);
-  RVE_CUDA(h, launch_shift<T>((C2<T>*)h->spec_cur, (C2<T>*)h->backup, h->NL, h->H, dE0, false, s));
-  tstop(h, RVE_K_SHIFT);
-  h->res_e.clear();
-  h->res_c.clear();
+  RVE_CUDA(h, cudaMemsetAsync(&h->st->nan_flag, 0, 3 * sizeof(int), s));
+  // Buffer rotation: iteration it reads strain spectrum S_in(it) and writes S_out(it)
+  // (then transformed in place); S_in(0) is the committed spectrum, S_out alternates
+  // between the two others, and S_in(it) = S_out(it - 1).  The tau_hat spectra rotate
+  // the same way.  The committed pair is only read, so a failed increment keeps it.
+  const int s0 = h->sb, s1 = (h->sb + 1) % 3, s2 = (h->sb + 2) % 3;
+  const int p0 = h->pb, p1 = (h->pb + 1) % 3, p2 = (h->pb + 2) % 3;
+  auto s_out = [&](int it) { return (it % 2 == 0) ? s1 : s2; };
+  auto s_in = [&](int it) { return it == 0 ? s0 : s_out(it - 1); };
+  auto p_out = [&](int it) { return (it % 2 == 0) ? p1 : p2; };
+  auto p_in = [&](int it) { return it == 0 ? p0 : p_out(it - 1); };
+  tstart(h, kSlotShift, RVE_K_SHIFT);
+  RVE_CUDA(h, launch_shift<T>((C2<T>*)h->spec[s0], (C2<T>*)h->backup, h->NL, h->H, dE0, false, s));
+  tstop(h, kSlotShift);
   const int zgrid_x = (h->H + h->zHC - 1) / h->zHC;
   const int ygrid_x = (h->H + h->yHC - 1) / h->yHC;
   const int max_iter = h->opt.max_iter > 0 ? h->opt.max_iter : 1000;
-  for (int it = 0;; ++it) {
-    XArgs<T> xa = x_args<T>(h, h->spec_cur, h->spec_nxt, it);
-    tstart(h, RVE_K_XPASS);
-    RVE_CUDA(h, launch_xpass<T>(xa, np, false, h->xgrid, h->xsmem, s));
-    tstop(h, RVE_K_XPASS);
-    LineArgs<T> ya = y_args<T>(h, h->spec_nxt);
-    tstart(h, RVE_K_YFWD);
-    RVE_CUDA(h, launch_line<T>(ya, -1, dim3(ygrid_x, 6 * h->nz), h->ysmem, s));
-    tstop(h, RVE_K_YFWD);
-    ZArgs<T> za = z_args<T>(h, h->spec_nxt, h->P_prev, h->P_scr, it);
-    tstart(h, RVE_K_ZGREEN);
-    RVE_CUDA(h, launch_zgreen<T>(za, dim3(zgrid_x, h->ny), h->zsmem, s));
-    tstop(h, RVE_K_ZGREEN);
-    tstart(h, RVE_K_YINV);
-    RVE_CUDA(h, launch_line<T>(ya, +1, dim3(ygrid_x, 6 * h->nz), h->ysmem, s));
-    tstop(h, RVE_K_YINV);
+  // Iterations are enqueued kBatch at a time; the residual kernel decides convergence on
+  // the device and later launches of the batch return at once.
+  int it0 = 0;
+  for (;;) {
+    const int nb = std::min(kBatch, max_iter - it0);
+    for (int b = 0; b < nb; ++b) {
+      const int it = it0 + b;
+      XArgs<T> xa = x_args<T>(h, h->spec[s_in(it)], h->spec[s_out(it)], it);
+      tstart(h, 4 * b + 0, RVE_K_XPASS);
+      RVE_CUDA(h, launch_xpass<T>(xa, np, false, h->xgrid, h->xsmem, s));
+      tstop(h, 4 * b + 0);
+      LineArgs<T> ya = y_args<T>(h, h->spec[s_out(it)]);
+      tstart(h, 4 * b + 1, RVE_K_YFWD);
+      RVE_CUDA(h, launch_line<T>(ya, -1, dim3(ygrid_x, h->nz), h->ysmem, s));
+      tstop(h, 4 * b + 1);
+      ZArgs<T> za = z_args<T>(h, h->spec[s_out(it)], h->P[p_in(it)], h->P[p_out(it)], it);
+      tstart(h, 4 * b + 2, RVE_K_ZGREEN);
+      RVE_CUDA(h, launch_zgreen<T>(za, dim3(zgrid_x, h->ny), h->zsmem, s));
+      tstop(h, 4 * b + 2);
+      tstart(h, 4 * b + 3, RVE_K_YINV);
+      RVE_CUDA(h, launch_line<T>(ya, +1, dim3(ygrid_x, h->nz), h->ysmem, s));
+      tstop(h, 4 * b + 3);
+    }
     RVE_CUDA(h, cudaMemcpyAsync(h->st_host, h->st, sizeof(IterStatus), cudaMemcpyDeviceToHost, s));
     RVE_CUDA(h, cudaStreamSynchronize(s));
-    tcollect(h);
-    const IterStatus& st = *h->st_host;
-    h->res_e.push_back(st.e_eq);
-    h->res_c.push_back(st.cF);
-    if (st.nan_flag) {
-      RVE_CUDA(h, launch_shift<T>((C2<T>*)h->spec_cur, (C2<T>*)h->backup, h->NL, h->H, dE0, true, s));
-      RVE_CUDA(h, cudaStreamSynchronize(s));
+    const int done = h->st_host->done;
+    tcollect(h, done ? h->st_host->done_it - it0 + 1 : nb);
+    if (done || it0 + nb >= max_iter) break;
+    it0 += nb;
+  }
+  const IterStatus st = *h->st_host;
+  const int last = st.done ? st.done_it : max_iter - 1;
+  {
+    std::vector<double> hh(2 * (size_t)(last + 1));
+    RVE_CUDA(h, cudaMemcpyAsync(hh.data(), h->dhist, hh.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    RVE_CUDA(h, cudaStreamSynchronize(s));
+    h->res_e.resize(last + 1);
+    h->res_c.resize(last + 1);
+    for (int i = 0; i <= last; ++i) {
+      h->res_e[i] = hh[2 * i];
+      h->res_c[i] = hh[2 * i + 1];
+    }
+  }
+  if (st.done != 1) {
+    // roll back: undo the start-of-increment shift of the committed spectrum
+    RVE_CUDA(h, launch_shift<T>((C2<T>*)h->spec[s0], (C2<T>*)h->backup, h->NL, h->H, dE0, true, s));
+    RVE_CUDA(h, cudaStreamSynchronize(s));
+    if (st.done == 2)
       return fail(h, RVE_ERR_NAN, std::string("NaN or Inf in the ") +
                                       ((st.nan_flag & 1) ? "mean stress" : "equilibrium residual") + " at increment " +
-                                      std::to_string(h->increment + 1) + ", iteration " + std::to_string(it));
-    }
-    const bool conv = h->opt.fixed_iters > 0 ? (it + 1 >= h->opt.fixed_iters)
-                                             : (st.e_eq < h->opt.tol && st.cF < h->opt.tol);
-    if (conv) {
-      const double e_eq = st.e_eq, cF = st.cF;
-      double E[6];
-      for (int c = 0; c < 6; ++c) E[c] = st.E[it & 1][c];
-      XArgs<T> ca = x_args<T>(h, h->spec_cur, nullptr, it);
-      tstart(h, RVE_K_COMMIT);
-      RVE_CUDA(h, launch_xpass<T>(ca, np, true, h->xgrid, h->xsmem, s));
-      tstop(h, RVE_K_COMMIT);
-      RVE_CUDA(h, cudaMemcpyAsync(h->st_host, h->st, sizeof(IterStatus), cudaMemcpyDeviceToHost, s));
-      RVE_CUDA(h, cudaStreamSynchronize(s));
-      tcollect(h);
-      for (int c = 0; c < 6; ++c) {
-        h->E_prev[c] = h->E_n[c];
-        h->E_n[c] = E[c];
-      }
-      h->time += h->dt;
-      h->increment += 1;
-      rve_effective r;
-      std::memset(&r, 0, sizeof(r));
-      r.increment = h->increment;
-      r.iterations = it + 1;
-      r.time = h->time;
-      for (int c = 0; c < 6; ++c) {
-        r.E[c] = E[c];
-        r.S[c] = h->st_host->sig_mean[c];
-      }
-      r.S_eq_of_mean = vm_of(r.S);
-      r.mean_S_eq = h->st_host->eff[0];
-      r.mean_f = h->st_host->eff[1];
-      r.mean_v = h->st_host->eff[2];
-      r.residual = e_eq;
-      r.stress_residual = cF;
-      h->hist.push_back(r);
-      if (iters) *iters += it + 1;
-      if (h->st_host->nan_flag) return fail(h, RVE_ERR_NAN, "NaN or Inf in the committed fields");
-      return RVE_OK;
-    }
-    if (it + 1 >= max_iter) {
-      RVE_CUDA(h, launch_shift<T>((C2<T>*)h->spec_cur, (C2<T>*)h->backup, h->NL, h->H, dE0, true, s));
-      RVE_CUDA(h, cudaStreamSynchronize(s));
-      char buf[200];
-      std::snprintf(buf, sizeof(buf), "increment %d: no convergence in %d iterations (e=%.3e, cF=%.3e)",
-                    h->increment + 1, max_iter, st.e_eq, st.cF);
-      return fail(h, RVE_ERR_NOT_CONVERGED, buf);
-    }
-    std::swap(h->spec_cur, h->spec_nxt);
-    std::swap(h->P_prev, h->P_scr);
+                                      std::to_string(h->increment + 1) + ", iteration " + std::to_string(last));
+    char buf[200];
+    std::snprintf(buf, sizeof(buf), "increment %d: no convergence in %d iterations (e=%.3e, cF=%.3e)",
+                  h->increment + 1, max_iter, st.e_eq, st.cF);
+    return fail(h, RVE_ERR_NOT_CONVERGED, buf);
   }
+  // a8: commit the converged iterate
+  const int it = st.done_it;
+  const double e_eq = st.e_eq, cF = st.cF;
+  double E[6];
+  for (int c = 0; c < 6; ++c) E[c] = st.E[it & 1][c];
+  XArgs<T> ca = x_args<T>(h, h->spec[s_in(it)], nullptr, it);
+  tstart(h, kSlotCommit, RVE_K_COMMIT);
+  RVE_CUDA(h, launch_xpass<T>(ca, np, true, h->xgrid, h->xsmem, s));
+  tstop(h, kSlotCommit);
+  RVE_CUDA(h, cudaMemcpyAsync(h->st_host, h->st, sizeof(IterStatus), cudaMemcpyDeviceToHost, s));
+  RVE_CUDA(h, cudaStreamSynchronize(s));
+  tcollect(h, 0);
+  h->sb = s_in(it);
+  h->pb = p_in(it);
+  for (int c = 0; c < 6; ++c) {
+    h->E_prev[c] = h->E_n[c];
+    h->E_n[c] = E[c];
+  }
+  h->time += h->dt;
+  h->increment += 1;
+  rve_effective r;
+  std::memset(&r, 0, sizeof(r));
+  r.increment = h->increment;
+  r.iterations = it + 1;
+  r.time = h->time;
+  for (int c = 0; c < 6; ++c) {
+    r.E[c] = E[c];
+    r.S[c] = h->st_host->sig_mean[c];
+  }
+  r.S_eq_of_mean = vm_of(r.S);
+  r.mean_S_eq = h->st_host->eff[0];
+  r.mean_f = h->st_host->eff[1];
+  r.mean_v = h->st_host->eff[2];
+  r.residual = e_eq;
+  r.stress_residual = cF;
+  h->hist.push_back(r);
+  if (iters) *iters += it + 1;
+  if (h->st_host->nan_flag) return fail(h, RVE_ERR_NAN, "NaN or Inf in the committed fields");
+  return RVE_OK;
 }
 
 bool valid_len(int n) {
@@ -839,7 +910,7 @@ rve_status rve_create(rve_t* out, int nx, int ny, int nz, const uint32_t* grain_
     }
   }
   if (o.timing)
-    for (int k = 0; k < RVE_K_COUNT; ++k) {
+    for (int k = 0; k < kTSlots; ++k) {
       e = cudaEventCreate(&h->ev_a[k]);
       if (e == cudaSuccess) e = cudaEventCreate(&h->ev_b[k]);
       if (e != cudaSuccess) { s = cuda_fail(h, e, "cudaEventCreate"); rve_destroy(h); return s; }
@@ -937,7 +1008,7 @@ rve_status rve_save_state(rve_t h, void* blob, size_t* bytes) {
   p += sizeof(hd);
   if (!h->hist.empty()) std::memcpy(p, h->hist.data(), h->hist.size() * sizeof(rve_effective));
   p += h->hist.size() * sizeof(rve_effective);
-  struct { const void* d; size_t n; } parts[] = {{h->spec_cur, spec}, {h->P_prev, spec}, {h->ep, 6 * fld},
+  struct { const void* d; size_t n; } parts[] = {{h->spec[h->sb], spec}, {h->P[h->pb], spec}, {h->ep, 6 * fld},
                                                  {h->v, 16 * fld},     {h->al, 12 * fld},   {h->eps_n, 6 * fld},
                                                  {h->sig_n, 6 * fld}};
   for (auto& q : parts) {
@@ -967,7 +1038,7 @@ rve_status rve_load_state(rve_t h, const void* blob, size_t bytes) {
   const char* p = (const char*)blob + sizeof(hd);
   h->hist.assign((const rve_effective*)p, (const rve_effective*)p + hd.n_hist);
   p += (size_t)hd.n_hist * sizeof(rve_effective);
-  struct { void* d; size_t n; } parts[] = {{h->spec_cur, spec}, {h->P_prev, spec}, {h->ep, 6 * fld},
+  struct { void* d; size_t n; } parts[] = {{h->spec[h->sb], spec}, {h->P[h->pb], spec}, {h->ep, 6 * fld},
                                            {h->v, 16 * fld},     {h->al, 12 * fld},   {h->eps_n, 6 * fld},
                                            {h->sig_n, 6 * fld}};
   for (auto& q : parts) {
@@ -1068,7 +1139,7 @@ static rve_status fft_t(int nx, int ny, int nz, int ncomp, const void* in, void*
   rve_status s;
   if ((s = upload_tables<T>(&h))) { release(&h); return fail(nullptr, s, h.err); }
   const int L = std::max(1, x_threads() / nx);
-  XFftArgs<T> xa;
+  XFftArgs<T> xa{};
   xa.nx = nx; xa.H = h.H; xa.L = L; xa.ncomp = ncomp; xa.NL = h.NL;
   xa.dx = h.dx;
   xa.tw = (const C2<T>*)h.tw_x;
@@ -1079,7 +1150,8 @@ static rve_status fft_t(int nx, int ny, int nz, int ncomp, const void* in, void*
   const dim3 xg((unsigned)((h.NL + L - 1) / L), ncomp);
   const size_t budget = 96 * 1024;
   auto pass = [&](const FftDim& d, void* tw, long long stride, int n_o2, long long A, long long B, int n_outer) {
-    LineArgs<T> la;
+    LineArgs<T> la{};
+    la.done = nullptr;  // stand-alone transform: always runs
     la.d = d;
     la.tw = (const C2<T>*)tw;
     la.spec = (C2<T>*)spec;
@@ -1087,6 +1159,8 @@ static rve_status fft_t(int nx, int ny, int nz, int ncomp, const void* in, void*
     la.HC = (int)std::max<size_t>(1, std::min<size_t>(16, (budget / (4 * sizeof(T))) / d.n));
     la.HC = std::min(la.HC, h.H);
     la.n_o2 = n_o2;
+    la.NC = 1;
+    la.hstride = 1;
     la.stride = stride;
     la.A = A;
     la.B = B;

@@ -145,6 +145,11 @@ template <> __device__ __forceinline__ double fast_log2<double>(double x) { retu
 template <typename T> __device__ __forceinline__ T fast_exp2(T x);
 template <> __device__ __forceinline__ float fast_exp2<float>(float x) { return exp2f(x); }
 template <> __device__ __forceinline__ double fast_exp2<double>(double x) { return exp2(x); }
+// e^x for the hardening terms (x = -b v in [-b v_max, 0]): the float intrinsic is within
+// a few ulp there.
+template <typename T> __device__ __forceinline__ T fast_exp(T x);
+template <> __device__ __forceinline__ float fast_exp<float>(float x) { return __expf(x); }
+template <> __device__ __forceinline__ double fast_exp<double>(double x) { return exp(x); }
 template <typename T> __device__ __forceinline__ T fast_div(T a, T b);
 template <> __device__ __forceinline__ float fast_div<float>(float a, float b) { return __fdividef(a, b); }
 template <> __device__ __forceinline__ double fast_div<double>(double a, double b) { return a / b; }
@@ -156,13 +161,13 @@ template <> __device__ __forceinline__ double fast_div<double>(double a, double 
 // zB = (a/c)^(1/n) leaves u^n + beta u - 1 = 0, beta = Kn zB / a, whose root u*(beta)
 // depends on log2(beta) alone.  Its deviation d = log2 u* - min(0, -log2 beta) from the
 // two asymptotes is tabulated on kRootTab nodes over [-kRootSpan, kRootSpan] (one node
-// at 0, where the asymptotes cross); linear interpolation starts Newton within 0.15 %,
-// so a fixed number of Newton steps reaches round-off (2 in float, 4 in double) and the
+// at 0, where the asymptotes cross); linear interpolation starts Newton within 3e-5,
+// so a fixed number of Newton steps reaches round-off (1 in float, 3 in double) and the
 // solve has no data-dependent branch.  Logarithms are base 2.
 
 template <typename T> struct TabNewton;
-template <> struct TabNewton<float> { static constexpr int value = 2; };
-template <> struct TabNewton<double> { static constexpr int value = 4; };
+template <> struct TabNewton<float> { static constexpr int value = 1; };
+template <> struct TabNewton<double> { static constexpr int value = 3; };
 
 // Branch-free solve (eta > 0, integer exponent): inactive systems run the same arithmetic
 // on a dummy positive argument and return 0, so all systems of a stage form one basic
@@ -240,12 +245,12 @@ __device__ __forceinline__ void rk_stage(const MatDev<T>& M, const T* e0, const 
   T Sslip = T(0), Stw = T(0), vtw = T(0);
 #pragma unroll
   for (int k = 0; k < 12; ++k) {
-    g[k] = T(1) - exp(-M.b_s * yt.v[k]);
+    g[k] = T(1) - fast_exp<T>(-M.b_s * yt.v[k]);
     Sslip += g[k];
   }
 #pragma unroll
   for (int k = 12; k < 16; ++k) {
-    g[k] = T(1) - exp(-M.b_b * yt.v[k]);
+    g[k] = T(1) - fast_exp<T>(-M.b_b * yt.v[k]);
     Stw += g[k];
     vtw += yt.v[k];
   }
@@ -256,24 +261,32 @@ __device__ __forceinline__ void rk_stage(const MatDev<T>& M, const T* e0, const 
   const T Ptw = (M.Kc * T(0.70710678118654752440)) * fm_left;
   const T lg_Ptw = fast_log2<T>(Ptw > T(0) ? Ptw : T(1));
   const T dq = M.h_diag - M.h_off;
-  T te[12], rho[16];
+  T te[12], av[16], rho[16];
 #pragma unroll
   for (int k = 0; k < 12; ++k) {
     te[k] = resolved<T>(k, sg) - M.c * yt.al[k];
-    const T a = fabs(te[k]) - (M.r0[k] + M.Q_s * (M.h_off * Sslip + dq * g[k]));
-    if constexpr (NP != 0)
-      rho[k] = reg_rate_tab<T, NP>(a, T(1), M.K, M.n, M.n_int, M.inv_n, M.lg_K, M.eta, M.lg_eta, T(0), tab);
-    else
-      rho[k] = reg_rate<T>(a, T(1), M.K, M.n, M.n_int, M.inv_n, M.sm, M.lg_K, M.eta, M.lg_eta, T(0));
+    av[k] = fabs(te[k]) - (M.r0[k] + M.Q_s * (M.h_off * Sslip + dq * g[k]));
   }
 #pragma unroll
-  for (int k = 12; k < 16; ++k) {
-    const T a = resolved<T>(k, sg) - (M.r0[k] + M.Q_b * (M.h_off * Stw + dq * g[k]));
-    if constexpr (NP != 0)
-      rho[k] = reg_rate_tab<T, NP>(a, Ptw, M.Kt, M.nt, M.nt_int, M.inv_nt, M.lg_Kt, M.eta, M.lg_eta, lg_Ptw,
+  for (int k = 12; k < 16; ++k) av[k] = resolved<T>(k, sg) - (M.r0[k] + M.Q_b * (M.h_off * Stw + dq * g[k]));
+  if constexpr (NP != 0) {
+    // all 16 solves as one straight-line block (in the developed plastic regime nearly
+    // every system is needed by some lane of a warp, and interleaving the independent
+    // solves hides their latency)
+#pragma unroll
+    for (int k = 0; k < 12; ++k)
+      rho[k] = reg_rate_tab<T, NP>(av[k], T(1), M.K, M.n, M.n_int, M.inv_n, M.lg_K, M.eta, M.lg_eta, T(0), tab);
+#pragma unroll
+    for (int k = 12; k < 16; ++k)
+      rho[k] = reg_rate_tab<T, NP>(av[k], Ptw, M.Kt, M.nt, M.nt_int, M.inv_nt, M.lg_Kt, M.eta, M.lg_eta, lg_Ptw,
                                    tab + kRootTab);
-    else
-      rho[k] = reg_rate<T>(a, Ptw, M.Kt, M.nt, M.nt_int, M.inv_nt, M.smt, M.lg_Kt, M.eta, M.lg_eta, lg_Ptw);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 12; ++k)
+      rho[k] = reg_rate<T>(av[k], T(1), M.K, M.n, M.n_int, M.inv_n, M.sm, M.lg_K, M.eta, M.lg_eta, T(0));
+#pragma unroll
+    for (int k = 12; k < 16; ++k)
+      rho[k] = reg_rate<T>(av[k], Ptw, M.Kt, M.nt, M.nt_int, M.inv_nt, M.smt, M.lg_Kt, M.eta, M.lg_eta, lg_Ptw);
   }
   T dep[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
 #pragma unroll
@@ -317,12 +330,12 @@ __device__ __forceinline__ bool elastic_increment(const MatDev<T>& M, const T* e
   T Sslip = T(0), Stw = T(0), vtw = T(0);
 #pragma unroll
   for (int k = 0; k < 12; ++k) {
-    g[k] = T(1) - exp(-M.b_s * y.v[k]);
+    g[k] = T(1) - fast_exp<T>(-M.b_s * y.v[k]);
     Sslip += g[k];
   }
 #pragma unroll
   for (int k = 12; k < 16; ++k) {
-    g[k] = T(1) - exp(-M.b_b * y.v[k]);
+    g[k] = T(1) - fast_exp<T>(-M.b_b * y.v[k]);
     Stw += g[k];
     vtw += y.v[k];
   }

@@ -34,7 +34,11 @@ cudaError_t launch_material_point_np(const MatDev<T>& M, long long nvox, const T
   if (nvox <= 0) return cudaSuccess;
   const int thr = 128;
   const long long grid = (nvox + thr - 1) / thr;
-  k_material_point<T, NP><<<(unsigned)grid, thr, 0, s>>>(M, nvox, R, eps_n, eps, state, sigma, dt, nsub, root_tab);
+  const size_t smem = (size_t)(2 * kRootTab) * sizeof(T);
+  cudaError_t e = set_smem<T>((const void*)k_material_point<T, NP>, smem);
+  if (e != cudaSuccess) return e;
+  k_material_point<T, NP><<<(unsigned)grid, thr, smem, s>>>(M, nvox, R, eps_n, eps, state, sigma, dt, nsub,
+                                                            root_tab);
   return cudaGetLastError();
 }
 
@@ -68,15 +72,16 @@ cudaError_t launch_zgreen(const ZArgs<T>& a, dim3 grid, size_t smem, cudaStream_
 template <typename T>
 __global__ void k_shift_backup(C2<T>* spec, C2<T>* backup, long long NL, int H, double d0, double d1, double d2,
                                double d3, double d4, double d5, int restore) {
+  // i = line * 6 + c; the kx = 0 entry of (line, c) is at line * H * 6 + c
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= 6 * NL) return;
-  C2<T>* p = spec + (size_t)i * H;
+  const int c = (int)(i % 6);
+  C2<T>* p = spec + (size_t)(i / 6) * H * 6 + c;
   if (restore) {
     *p = backup[i];
     return;
   }
   backup[i] = *p;
-  const int c = (int)(i / NL);
   const double d = c == 0 ? d0 : c == 1 ? d1 : c == 2 ? d2 : c == 3 ? d3 : c == 4 ? d4 : d5;
   p->x = (T)((double)p->x + d);
 }

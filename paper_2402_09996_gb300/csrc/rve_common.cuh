@@ -72,14 +72,24 @@ struct IterStatus {
   double e_eq;          // equilibrium error
   double eff[4];        // commit: <sigma_eq>, <f_beta>, <v^s>, unused
   int nan_flag;
+  int done;             // 0 iterating; 1 converged; 2 NaN/Inf; 3 iteration cap reached
+  int done_it;          // iteration at which `done` was set
   int pad;
+};
+
+// Convergence rule evaluated on the device after each iteration's residual.
+struct ConvDev {
+  double tol;
+  int fixed_iters;  // > 0: stop after exactly this many iterations
+  int max_iter;
+  double* hist;     // 2 * max_iter: (e_eq, c_F) of every iteration of the increment
 };
 
 constexpr int kNumRed = 9;  // reduction slots per CTA
 
 // Regularised-rate root table (constitutive.cuh): kRootTab nodes of log2(beta) over
 // [-kRootSpan, kRootSpan], one node at 0.
-constexpr int kRootTab = 257;
+constexpr int kRootTab = 2049;
 constexpr double kRootSpan = 16.0;
 
 }  // namespace rve

@@ -99,6 +99,7 @@ struct XArgs {
   const T* root_tab;  // 2 * kRootTab rate-root deviations (slip, twin)
   MatDev<T> M;
   LoadDev ld;
+  const int* done;  // iteration launches return at once when *done != 0 (NULL: always run)
   T dt;
   int nsub;
   double* partial;
@@ -127,6 +128,7 @@ __global__ void __launch_bounds__(kXThreads, RVE_X_MINB) k_xpass(const XArgs<T> 
   const size_t NL = (size_t)a.ny * a.nz;
   const int line0 = blockIdx.x * a.L;
   const int nl = min(a.L, (int)(NL - line0));
+  if (a.done && *a.done) return;  // increment already decided: speculative launch
   const size_t nvox = (size_t)a.nvox;
 
   for (int i = tid; i < nx; i += nthr) tw[i] = a.tw[i];
@@ -134,13 +136,16 @@ __global__ void __launch_bounds__(kXThreads, RVE_X_MINB) k_xpass(const XArgs<T> 
     for (int i = tid; i < 2 * kRootTab; i += nthr) tab[i] = a.root_tab[i];
   // pack component pairs (2p, 2p+1) of each line as one complex Hermitian-extended
   // sequence Z = A + iB, so one complex inverse FFT yields both real lines
+  // (spectra are component-interleaved: entry (line, kx, c) at (line * H + kx) * 6 + c,
+  // so consecutive threads read consecutive component pairs of the CTA's lines)
   for (int w = tid; w < 3 * nl * H; w += nthr) {
-    const int xi = w % H;
-    const int q = w / H;  // q = p * nl + l
-    const int l = q % nl, p = q / nl;
-    const size_t line = (size_t)line0 + l;
-    C2<T> A = a.spec_in[((size_t)(2 * p) * NL + line) * H + xi];
-    C2<T> B = a.spec_in[((size_t)(2 * p + 1) * NL + line) * H + xi];
+    const int p = w % 3;
+    const int r = w / 3;
+    const int xi = r % H, l = r / H;
+    const int q = p * nl + l;
+    const size_t e0 = (((size_t)line0 + l) * H + xi) * 6 + 2 * p;
+    C2<T> A = a.spec_in[e0];
+    C2<T> B = a.spec_in[e0 + 1];
     if (xi == 0 || xi == half) {
       A.y = T(0);
       B.y = T(0);
@@ -214,16 +219,17 @@ __global__ void __launch_bounds__(kXThreads, RVE_X_MINB) k_xpass(const XArgs<T> 
     C2<T>* out = smem_fft<T, -1>(res, oth, a.dx, 3 * nl, nx, tw, tid, nthr);
     // unpack: A = (Z_k + conj Z_{n-k}) / 2, B = (Z_k - conj Z_{n-k}) / (2i)
     for (int w = tid; w < 3 * nl * H; w += nthr) {
-      const int xi = w % H;
-      const int q = w / H;
-      const int l = q % nl, p = q / nl;
-      const size_t line = (size_t)line0 + l;
+      const int p = w % 3;
+      const int r = w / 3;
+      const int xi = r % H, l = r / H;
+      const int q = p * nl + l;
       const C2<T> Z = out[(size_t)q * nx + xi];
       const C2<T> Zm = out[(size_t)q * nx + (xi == 0 ? 0 : nx - xi)];
       const C2<T> A = mk<T>(T(0.5) * (Z.x + Zm.x), T(0.5) * (Z.y - Zm.y));
       const C2<T> B = mk<T>(T(0.5) * (Z.y + Zm.y), T(-0.5) * (Z.x - Zm.x));
-      a.spec_out[((size_t)(2 * p) * NL + line) * H + xi] = A;
-      a.spec_out[((size_t)(2 * p + 1) * NL + line) * H + xi] = B;
+      const size_t e0 = (((size_t)line0 + l) * H + xi) * 6 + 2 * p;
+      a.spec_out[e0] = A;
+      a.spec_out[e0 + 1] = B;
     }
   }
   if (publish_partial<kNumRed>(acc, a.partial, a.counter, red, &s_last)) {
@@ -274,14 +280,19 @@ __global__ void __launch_bounds__(kXThreads, RVE_X_MINB) k_xpass(const XArgs<T> 
 
 // ---------------------------------------------------------------- line FFT pass -----
 // Transforms, in place, lines of length d.n along an axis with element stride `stride`
-// (complex units).  Line base offset: (o / n_o2) * A + (o % n_o2) * B + h, for
-// o = blockIdx.y and h in a chunk of HC consecutive kx values.
+// (complex units), for NC components at once.  Element (line j, kx offset hh, component
+// c) of CTA (blockIdx.x, o = blockIdx.y) sits at
+//   (o / n_o2) * A + (o % n_o2) * B + (h0 + hh) * hstride + c + j * stride,
+// h0 = blockIdx.x * HC.  The solver's spectra are component-interleaved (NC = 6,
+// hstride = 6: each (j, kx chunk) row is HC * 6 contiguous values); the stand-alone FFT
+// entry points use component-major spectra (NC = 1, hstride = 1).
 template <typename T>
 struct LineArgs {
   FftDim d;
   const C2<T>* tw;
   C2<T>* spec;
-  int H, HC, n_o2;
+  int H, HC, n_o2, NC, hstride;
+  const int* done;  // as in XArgs
   long long stride, A, B;
 };
 
@@ -293,23 +304,28 @@ __global__ void __launch_bounds__(kLineThreads) k_line(const LineArgs<T> a) {
   C2<T>* tw = reinterpret_cast<C2<T>*>(smem_raw);
   const int n = a.d.n;
   const int ps = n + 1;  // padded sequence stride
+  const int NC = a.NC;
   C2<T>* b0 = tw + n;
-  C2<T>* b1 = b0 + (size_t)a.HC * ps;
+  C2<T>* b1 = b0 + (size_t)NC * a.HC * ps;
   const int tid = threadIdx.x, nthr = blockDim.x;
+  if (a.done && *a.done) return;
   const int h0 = blockIdx.x * a.HC;
   const int hc = min(a.HC, a.H - h0);
   const int o = blockIdx.y;
-  const size_t base = (size_t)(o / a.n_o2) * a.A + (size_t)(o % a.n_o2) * a.B + h0;
+  const size_t base = (size_t)(o / a.n_o2) * a.A + (size_t)(o % a.n_o2) * a.B + (size_t)h0 * a.hstride;
+  const int row = hc * NC;  // values per line position, contiguous when hstride == NC
   for (int i = tid; i < n; i += nthr) tw[i] = a.tw[i];
-  for (int w = tid; w < hc * n; w += nthr) {
-    const int hh = w % hc, j = w / hc;
-    b0[(size_t)hh * ps + j] = a.spec[base + (size_t)j * a.stride + hh];
+  for (int w = tid; w < row * n; w += nthr) {
+    const int rc = w % row, j = w / row;
+    const int c = rc % NC, hh = rc / NC;
+    b0[(size_t)(c * hc + hh) * ps + j] = a.spec[base + (size_t)j * a.stride + (size_t)hh * a.hstride + c];
   }
   __syncthreads();
-  C2<T>* res = smem_fft<T, SIGN>(b0, b1, a.d, hc, ps, tw, tid, nthr);
-  for (int w = tid; w < hc * n; w += nthr) {
-    const int hh = w % hc, j = w / hc;
-    a.spec[base + (size_t)j * a.stride + hh] = res[(size_t)hh * ps + j];
+  C2<T>* res = smem_fft<T, SIGN>(b0, b1, a.d, row, ps, tw, tid, nthr);
+  for (int w = tid; w < row * n; w += nthr) {
+    const int rc = w % row, j = w / row;
+    const int c = rc % NC, hh = rc / NC;
+    a.spec[base + (size_t)j * a.stride + (size_t)hh * a.hstride + c] = res[(size_t)(c * hc + hh) * ps + j];
   }
 }
 
@@ -327,6 +343,8 @@ struct ZArgs {
   const T* ky;
   const T* kzt;
   int scheme;   // 0 Willot, 1 Moulinec-Suquet
+  ConvDev conv;
+  const int* done;
   T lam0, mu0, invN;
   double* partial;
   unsigned int* counter;
@@ -347,16 +365,17 @@ __global__ void __launch_bounds__(kZThreads) k_zgreen(const ZArgs<T> a) {
   C2<T>* b0 = tw + nz;
   C2<T>* b1 = b0 + (size_t)6 * a.HC * ps;
   const int tid = threadIdx.x, nthr = blockDim.x;
+  if (a.done && *a.done) return;
   const int j = blockIdx.y;
   const int h0 = blockIdx.x * a.HC;
   const int hc = min(a.HC, a.H - h0);
   const size_t H = a.H, ny = a.ny;
   for (int i = tid; i < nz; i += nthr) tw[i] = a.tw[i];
+  // component-interleaved spectra: for each kz the CTA's hc * 6 values are contiguous
   for (int w = tid; w < 6 * hc * nz; w += nthr) {
-    const int hh = w % hc;
-    const int r = w / hc;
-    const int kz = r % nz, c = r / nz;
-    b0[(size_t)(c * hc + hh) * ps + kz] = a.spec[(((size_t)c * nz + kz) * ny + j) * H + h0 + hh];
+    const int rc = w % (6 * hc), kz = w / (6 * hc);
+    const int c = rc % 6, hh = rc / 6;
+    b0[(size_t)(c * hc + hh) * ps + kz] = a.spec[(((size_t)kz * ny + j) * H + h0 + hh) * 6 + c];
   }
   __syncthreads();
   C2<T>* res = smem_fft<T, -1>(b0, b1, a.dz, 6 * hc, ps, tw, tid, nthr);
@@ -382,8 +401,7 @@ __global__ void __launch_bounds__(kZThreads) k_zgreen(const ZArgs<T> a) {
       k2 = a.kzt[2 * kz];
     }
     C2<T> t[6];
-    const size_t g0 = ((size_t)kz * ny + j) * H + h;
-    const size_t cstride = (size_t)nz * ny * H;
+    const size_t g0 = (((size_t)kz * ny + j) * H + h) * 6;
 #pragma unroll
     for (int c = 0; c < 6; ++c) t[c] = res[(size_t)(c * hc + hh) * ps + kz];
     // equilibrium residual kappa . sigma_hat = kappa . (tau_hat - tau_hat_prev)
@@ -391,9 +409,9 @@ __global__ void __launch_bounds__(kZThreads) k_zgreen(const ZArgs<T> a) {
       C2<T> d[6];
 #pragma unroll
       for (int c = 0; c < 6; ++c) {
-        const C2<T> p = a.P_prev[c * cstride + g0];
+        const C2<T> p = a.P_prev[g0 + c];
         d[c] = csub<T>(t[c], p);
-        a.P_out[c * cstride + g0] = t[c];
+        a.P_out[g0 + c] = t[c];
       }
       // symmetric order (11,22,33,23,13,12): row i of d times kappa
       const double r0x = (double)d[0].x * k0 + (double)d[5].x * k1 + (double)d[4].x * k2;
@@ -442,10 +460,9 @@ __global__ void __launch_bounds__(kZThreads) k_zgreen(const ZArgs<T> a) {
   __syncthreads();
   C2<T>* out = smem_fft<T, +1>(res, oth, a.dz, 6 * hc, ps, tw, tid, nthr);
   for (int w = tid; w < 6 * hc * nz; w += nthr) {
-    const int hh = w % hc;
-    const int r = w / hc;
-    const int kz = r % nz, c = r / nz;
-    a.spec[(((size_t)c * nz + kz) * ny + j) * H + h0 + hh] = out[(size_t)(c * hc + hh) * ps + kz];
+    const int rc = w % (6 * hc), kz = w / (6 * hc);
+    const int c = rc % 6, hh = rc / 6;
+    a.spec[(((size_t)kz * ny + j) * H + h0 + hh) * 6 + c] = out[(size_t)(c * hc + hh) * ps + kz];
   }
   double v[kNumRed];
   v[0] = rs;
@@ -460,29 +477,30 @@ __global__ void __launch_bounds__(kZThreads) k_zgreen(const ZArgs<T> a) {
       st->res_sum = v[0];
       st->e_eq = nrm > 0.0 ? sqrt(v[0]) / ((double)a.nvox * nrm) : 0.0;
       st->nan_flag |= !isfinite(v[0]) ? 2 : 0;
+      // convergence decision (equilibrium and stress-constraint errors of iteration it)
+      const ConvDev& cv = a.conv;
+      cv.hist[2 * a.it] = st->e_eq;
+      cv.hist[2 * a.it + 1] = st->cF;
+      int code = 0;
+      if (st->nan_flag) code = 2;
+      else if (cv.fixed_iters > 0 ? a.it + 1 >= cv.fixed_iters : (st->e_eq < cv.tol && st->cF < cv.tol)) code = 1;
+      else if (a.it + 1 >= cv.max_iter) code = 3;
+      if (code) {
+        st->done_it = a.it;
+        st->done = code;
+      }
       *a.counter = 0u;
     }
   }
 }
 
 // ---------------------------------------------------------------- small kernels -----
-// Uniform shift of the strain field held in x-spectral form: Re S[c][line][kx=0] += dE[c].
-template <typename T>
-__global__ void k_shift(C2<T>* spec, long long NL, int H, double d0, double d1, double d2, double d3,
-                        double d4, double d5) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= 6 * NL) return;
-  const int c = (int)(i / NL);
-  const double d = c == 0 ? d0 : c == 1 ? d1 : c == 2 ? d2 : c == 3 ? d3 : c == 4 ? d4 : d5;
-  C2<T>* p = spec + (size_t)i * H;
-  p->x = (T)((double)p->x + d);
-}
-
 template <typename T, int NP>
 __global__ void k_material_point(const MatDev<T> M, long long nvox, const T* __restrict__ R,
                                  const T* __restrict__ eps_n, const T* __restrict__ eps, T* state,
                                  T* sigma, T dt, int nsub, const T* __restrict__ root_tab) {
-  __shared__ T tab[2 * kRootTab];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* tab = reinterpret_cast<T*>(smem_raw);  // 2 * kRootTab
   if (NP != 0)
     for (int k = threadIdx.x; k < 2 * kRootTab; k += blockDim.x) tab[k] = root_tab[k];
   __syncthreads();

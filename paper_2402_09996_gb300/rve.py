@@ -21,7 +21,7 @@ FP64, FP32 = 0, 1
 GREEN_WILLOT, GREEN_MS = 0, 1
 FIELD_STRESS, FIELD_STRAIN, FIELD_EPS_P, FIELD_V, FIELD_ALPHA, FIELD_VM = range(6)
 FIELD_COMPONENTS = {FIELD_STRESS: 6, FIELD_STRAIN: 6, FIELD_EPS_P: 6, FIELD_V: 16, FIELD_ALPHA: 12, FIELD_VM: 1}
-KERNELS = ["xpass", "yfwd", "zgreen", "yinv", "commit", "shift"]
+KERNELS = ["xpass", "yfwd", "zgreen", "yinv", "commit", "shift", "idle"]
 STATUS = {
     0: "RVE_OK",
     1: "RVE_ERR_INVALID_ARG",

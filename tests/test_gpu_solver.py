@@ -65,9 +65,11 @@ def test_ragged_voronoi_tolerance_mode(lib, cuda, prec):
             e_ref = np.array([r[0] for r in rec["residuals"]])
             c_ref = np.array([r[1] for r in rec["residuals"]])
             m = min(len(e_got), len(e_ref))
-            rtol = 1e-7 if p == rve.FP64 else 1e-1
-            assert np.allclose(e_got[:m], e_ref[:m], rtol=rtol, atol=0), (rec["increment"], e_got[:m], e_ref[:m])
-            assert np.allclose(c_got[:m], c_ref[:m], rtol=rtol, atol=1e-12), (rec["increment"], c_got[:m], c_ref[:m])
+            # FP32: the mean stress carries float rounding of ~1e-7 relative, a floor for
+            # both errors well below the 1e-6 tolerance
+            rtol, atol = (1e-7, 1e-12) if p == rve.FP64 else (1e-1, 3e-7)
+            assert np.allclose(e_got[:m], e_ref[:m], rtol=rtol, atol=atol), (rec["increment"], e_got[:m], e_ref[:m])
+            assert np.allclose(c_got[:m], c_ref[:m], rtol=rtol, atol=atol), (rec["increment"], c_got[:m], c_ref[:m])
         got = s.history()
         sig = s.field(rve.FIELD_STRESS)
         eps = s.field(rve.FIELD_STRAIN)
@@ -110,19 +112,22 @@ def test_not_converged_keeps_state(lib, cuda):
     gid = np.zeros((8, 8, 8), dtype=np.uint32)
     gid[:4] = 1
     euler = np.array([[0.3, 0.9, 1.7], [2.1, 1.2, 0.4]])
-    with _rve(gid, euler, max_iter=3) as s:
-        s.set_mixed_load(dt=1.0)
+    # an oversized increment fails on the iteration cap; the same handle then solves a
+    # normal increment from the untouched committed state, exactly like the oracle
+    with _rve(gid, euler, max_iter=25) as s:
+        s.set_mixed_load(dt=20.0)
         with pytest.raises(rve.RVEError) as ei:
             s.step(1)
         assert ei.value.status == 4
         assert s.history() == []
-    # same handle semantics after a failure: a fresh solve with a loose cap still matches
-    with _rve(gid, euler, fixed_iters=4) as s:
-        s.step(1)
-        h = s.history()[0]
-    ref = _oracle(gid, euler, fixed_iters=4)
-    ref.run(1)
-    assert rel_err(h["S"], ref.history[0]["S"]) < 1e-9
+        assert len(s.residuals()[0]) == 25
+        s.set_mixed_load(dt=0.5)
+        s.step(2)
+        got = s.history()
+    ref = _oracle(gid, euler, max_iter=25)
+    ref.set_load(orc.Load(dt=0.5))
+    ref.run(2)
+    _compare_histories(got, ref.history, 1e-9)
 
 
 def test_save_load_roundtrip(lib, cuda):

@@ -296,6 +296,27 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_profile_case(args):
+    """A small case for `ncu --profile-from-start off`: the kernels of --steps increments in
+    the plastic regime, on inputs of a few hundred MB, after --warmup untimed increments."""
+    import torch
+
+    from paper_2402_09996_gb300 import inputs, rve
+
+    n = args.profile_case
+    inp = inputs.make_inputs((n, n, n), 60, 0.5, seed=11)
+    solver = rve.RVE(rve.label_voronoi(inp), inp.euler, precision=rve.FP32)
+    solver.set_mixed_load(dt=0.5)
+    solver.step(args.warmup)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    solver.step(args.steps)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    print(f"profile case {n}^3: {solver.effective()['iterations']} iterations in the last increment")
+    solver.close()
+
+
 def main_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -304,6 +325,10 @@ def main_args(argv=None):
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", type=int, default=0, metavar="N",
+                    help="profiling case: an N^3 twinned RVE (60 grains, p=0.5, seed 11), "
+                         "--warmup increments, then --steps increments between "
+                         "cudaProfilerStart/Stop; prints no JSON line")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -314,6 +339,8 @@ def main():
     args = main_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.profile_case:
+        run_profile_case(args)
     else:
         run_gpu(args)
 

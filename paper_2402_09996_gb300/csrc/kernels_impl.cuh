@@ -8,9 +8,11 @@
 
 namespace rve {
 
+// Opt in to the dynamic shared memory a launch needs (static shared memory counts
+// towards the default 48 KB limit too, so any sizeable request sets the attribute).
 template <typename T>
 static cudaError_t set_smem(const void* fn, size_t smem) {
-  if (smem <= 48 * 1024) return cudaSuccess;
+  if (smem <= 16 * 1024) return cudaSuccess;
   return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 

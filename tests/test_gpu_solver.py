@@ -88,6 +88,29 @@ def test_ragged_voronoi_tolerance_mode(lib, cuda, prec):
     assert np.max(np.abs(eps.reshape(6, -1).mean(axis=1) - E)) < (1e-12 if p == rve.FP64 else 1e-6) * abs(E[2]) + 1e-15
 
 
+@pytest.mark.parametrize("shape,prec", [((96, 96, 96), "fp32"), ((32, 160, 64), "fp32"), ((40, 24, 30), "fp64"),
+                                        ((128, 128, 128), "fp32"), ((1, 64, 64), "fp32")])
+def test_launch_geometries_keep_invariants(lib, cuda, shape, prec):
+    """Grids whose tile sizes and launch shapes differ from the parity cases: two
+    increments converge, the mean strain equals the prescribed macroscopic strain and
+    the free mean stresses vanish to the tolerance."""
+    from paper_2402_09996_gb300 import inputs, rve
+
+    inp = inputs.make_inputs(shape, 12, 0.5, seed=sum(shape))
+    gid = rve.label_voronoi(inp)
+    p = rve.FP64 if prec == "fp64" else rve.FP32
+    with _rve(gid, inp.euler, precision=p) as s:
+        s.set_mixed_load(dt=0.5)
+        s.step(2)
+        h = s.history()[-1]
+        eps = s.field(rve.FIELD_STRAIN)
+    assert h["residual"] < 1e-6 and h["stress_residual"] < 1e-6
+    assert abs(h["E"][2] - 1e-3) < 1e-15
+    assert abs(eps[2].mean() - h["E"][2]) < (1e-12 if p == rve.FP64 else 1e-7)
+    S = h["S"]
+    assert np.max(np.abs(np.delete(S, 2))) < 1e-5 * abs(S[2])
+
+
 def test_homogeneous_one_iteration_under_strain_control(lib, cuda):
     """One grain, all six components prescribed: equilibrium holds at iteration 0."""
     gid = np.zeros((4, 6, 8), dtype=np.uint32)

@@ -234,6 +234,26 @@ rve_status rve_label_voronoi(int nx, int ny, int nz, int n_parent, const double*
                              const uint8_t* twinned, const double* twin_normal,
                              uint32_t* grain_id_out, int out_on_device, void* stream);
 
+/* rve_label_voronoi without any device allocation (the paper has no counterpart: this is
+ * a service for callers that must not allocate).  Some callers cannot call cudaMalloc or
+ * cudaFree: code that owns all device memory through its own pool, code that must not
+ * trigger the implicit device-wide synchronisation of those calls (latency-critical
+ * loops, other work in flight on the device), and library code embedded where
+ * allocation is forbidden.  This variant keeps its scratch (seeds, normals, centroid sums
+ * of up to RVE_NOALLOC_MAX_PARENTS parents, about 470 KB) in one static device array that
+ * every GPU loading this library holds until the process exits.
+ *   Inputs and output as rve_label_voronoi, except that grain_id_out must be a device
+ *   pointer (nx*ny*nz labels).  n_parent > RVE_NOALLOC_MAX_PARENTS -> RVE_ERR_INVALID_ARG.
+ *   The first call on a device looks up the array's device address (once per device,
+ *   with that device current); make that first call before any stream capture.
+ *   All calls share the one array: calls whose work overlaps on the GPU (other streams,
+ *   other host threads) race and must be serialised by the caller.  The call returns
+ *   after its work on `stream` has finished. */
+#define RVE_NOALLOC_MAX_PARENTS 4096
+rve_status rve_label_voronoi_noalloc(int nx, int ny, int nz, int n_parent, const double* seeds,
+                                     const uint8_t* twinned, const double* twin_normal,
+                                     uint32_t* grain_id_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -16,6 +16,7 @@
 
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -201,6 +202,126 @@ extern "C" rve_status rve_label_voronoi(int nx, int ny, int nz, int n_parent, co
     LBL_CUDA(cudaGetLastError());
   }
   if (!out_on_device) LBL_CUDA(cudaMemcpyAsync(out, lab, sizeof(uint32_t) * nvox, cudaMemcpyDeviceToHost, st));
+  LBL_CUDA(cudaStreamSynchronize(st));
+  return RVE_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// Labelling without device allocation.
+//
+// For callers that may not allocate device memory (a caller-owned memory pool, loops
+// that cannot afford the device-wide synchronisation of cudaMalloc/cudaFree, embedding
+// where allocation is forbidden), the scratch of the labelling lives in one static
+// device array of fixed size; only the caller's output buffer is written besides it.
+namespace {
+
+constexpr int kNoAllocMax = RVE_NOALLOC_MAX_PARENTS;
+
+struct NoAllocScratch {
+  double seeds[3 * kNoAllocMax];
+  double cent[3 * kNoAllocMax];
+  double normal[3 * kNoAllocMax];
+  unsigned long long sums[4 * kNoAllocMax];
+  int seed_vox[3 * kNoAllocMax];
+  uint8_t twinned[kNoAllocMax];
+};
+
+// Held by every GPU that loads this library until the process exits.  In host code the
+// name is only a stand-in: kernels receive the device address looked up below.
+static __device__ __align__(256) NoAllocScratch g_noalloc;
+
+// Device address of g_noalloc per device ordinal, looked up once per device.
+std::mutex g_noalloc_mu;
+NoAllocScratch* g_noalloc_ptr[64] = {nullptr};
+
+// Seed voxel indices: min(trunc(s * n), n - 1) per axis, as the host path computes them.
+__global__ void k_seed_vox(int n_parent, int nx, int ny, int nz, NoAllocScratch* sc) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n_parent) return;
+  const int n[3] = {nx, ny, nz};
+  for (int a = 0; a < 3; ++a) {
+    const int v = (int)__dmul_rn(sc->seeds[3 * p + a], (double)n[a]);
+    sc->seed_vox[3 * p + a] = v < n[a] - 1 ? v : n[a] - 1;
+  }
+}
+
+// Centroid of each twinned parent: (seed voxel centre) + (integer offset sum) / count,
+// the same rounded operations as the host path.
+__global__ void k_centroids(int n_parent, NoAllocScratch* sc) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n_parent) return;
+  const long long cnt = (long long)sc->sums[4 * p + 3];
+  for (int a = 0; a < 3; ++a) {
+    const double base = __dadd_rn((double)sc->seed_vox[3 * p + a], 0.5);
+    sc->cent[3 * p + a] =
+        cnt > 0 ? __dadd_rn(base, __ddiv_rn((double)(long long)sc->sums[4 * p + a], (double)cnt)) : base;
+  }
+}
+
+}  // namespace
+
+extern "C" rve_status rve_label_voronoi_noalloc(int nx, int ny, int nz, int n_parent, const double* seeds,
+                                                const uint8_t* twinned, const double* twin_normal,
+                                                uint32_t* out, void* stream) {
+  if (nx < 1 || ny < 1 || nz < 1 || n_parent < 1 || !seeds || !out) {
+    rve::set_global_error("rve_label_voronoi_noalloc: bad sizes or NULL pointer");
+    return RVE_ERR_INVALID_ARG;
+  }
+  if (n_parent > kNoAllocMax) {
+    rve::set_global_error("rve_label_voronoi_noalloc: n_parent " + std::to_string(n_parent) +
+                          " exceeds the no-allocation maximum of " + std::to_string(kNoAllocMax));
+    return RVE_ERR_INVALID_ARG;
+  }
+  for (long long s = 0; s < 3LL * n_parent; ++s)
+    if (!(seeds[s] >= 0.0 && seeds[s] < 1.0)) {
+      rve::set_global_error("rve_label_voronoi_noalloc: seeds must lie in [0, 1)");
+      return RVE_ERR_INVALID_ARG;
+    }
+  bool any_twin = false;
+  if (twinned)
+    for (int p = 0; p < n_parent; ++p) any_twin |= twinned[p] != 0;
+  if (any_twin && !twin_normal) {
+    rve::set_global_error("rve_label_voronoi_noalloc: twin_normal is NULL");
+    return RVE_ERR_INVALID_ARG;
+  }
+  int dev = 0;
+  LBL_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) {
+    rve::set_global_error("rve_label_voronoi_noalloc: device ordinal out of range");
+    return RVE_ERR_INVALID_ARG;
+  }
+  NoAllocScratch* sc = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      void* p = nullptr;
+      LBL_CUDA(cudaGetSymbolAddress(&p, g_noalloc));
+      g_noalloc_ptr[dev] = static_cast<NoAllocScratch*>(p);
+    }
+    sc = g_noalloc_ptr[dev];
+  }
+  const long long nvox = (long long)nx * ny * nz;
+  cudaStream_t st = stream ? (cudaStream_t)stream : cudaStreamPerThread;
+  LBL_CUDA(cudaMemcpyAsync(sc->seeds, seeds, 3 * sizeof(double) * n_parent, cudaMemcpyHostToDevice, st));
+  const int thr = 256;
+  const unsigned grid = (unsigned)((nvox + thr - 1) / thr);
+  k_voronoi<<<grid, thr, 0, st>>>(nx, ny, nz, n_parent, sc->seeds, out);
+  LBL_CUDA(cudaGetLastError());
+  if (any_twin) {
+    const unsigned pg = (unsigned)((n_parent + 127) / 128);
+    LBL_CUDA(cudaMemcpyAsync(sc->twinned, twinned, n_parent, cudaMemcpyHostToDevice, st));
+    LBL_CUDA(cudaMemcpyAsync(sc->normal, twin_normal, 3 * sizeof(double) * n_parent, cudaMemcpyHostToDevice, st));
+    // the array keeps the previous call's contents: the sums must start at zero
+    LBL_CUDA(cudaMemsetAsync(sc->sums, 0, 4 * sizeof(unsigned long long) * n_parent, st));
+    k_seed_vox<<<pg, 128, 0, st>>>(n_parent, nx, ny, nz, sc);
+    LBL_CUDA(cudaGetLastError());
+    k_centroid_sums<<<grid, thr, 0, st>>>(nx, ny, nz, out, sc->twinned, sc->seed_vox, sc->sums);
+    LBL_CUDA(cudaGetLastError());
+    k_centroids<<<pg, 128, 0, st>>>(n_parent, sc);
+    LBL_CUDA(cudaGetLastError());
+    k_twin_split<<<grid, thr, 0, st>>>(nx, ny, nz, n_parent, out, sc->twinned, sc->cent, sc->normal);
+    LBL_CUDA(cudaGetLastError());
+  }
   LBL_CUDA(cudaStreamSynchronize(st));
   return RVE_OK;
 }

@@ -110,8 +110,9 @@ EXPORTED = [
     "rve_options_default", "rve_material_default", "rve_create", "rve_set_material",
     "rve_set_mixed_load", "rve_step", "rve_get_effective", "rve_get_fields", "rve_save_state",
     "rve_load_state", "rve_last_error", "rve_destroy", "rve_material_point", "rve_fft_r2c",
-    "rve_fft_c2r", "rve_label_voronoi", "rve_kernel_times", "rve_get_residuals",
+    "rve_fft_c2r", "rve_label_voronoi", "rve_kernel_times", "rve_get_residuals", "rve_label_voronoi_noalloc",
 ]
+NOALLOC_MAX_PARENTS = 4096  # RVE_NOALLOC_MAX_PARENTS of include/rve.h
 
 
 def load_library(path: str | os.PathLike | None = None):
@@ -144,6 +145,7 @@ def load_library(path: str | os.PathLike | None = None):
     lib.rve_label_voronoi.argtypes = [i, i, i, i, vp, vp, vp, vp, i, vp]
     lib.rve_kernel_times.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong), i]
     lib.rve_get_residuals.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double), i, C.POINTER(i)]
+    lib.rve_label_voronoi_noalloc.argtypes = [i, i, i, i, vp, vp, vp, vp, vp]
     for name in EXPORTED:
         getattr(lib, name).restype = C.c_int
     lib.rve_options_default.restype = None
@@ -412,3 +414,20 @@ def label_voronoi(inputs, out=None):
                                    _torch_stream())
     _check(st, None)
     return res
+
+
+def label_voronoi_noalloc(inputs, out):
+    """Grain-ID map of an inputs.RVEInputs written into `out`, a CUDA int32 tensor
+    (nz, ny, nx), by the entry point that allocates no device memory (its scratch is a
+    fixed static array: at most NOALLOC_MAX_PARENTS parents)."""
+    lib = load_library()
+    nz, ny, nx = inputs.shape
+    seeds = np.ascontiguousarray(inputs.seeds, dtype=np.float64)
+    tw = np.ascontiguousarray(inputs.twinned, dtype=np.uint8)
+    nrm = np.ascontiguousarray(inputs.twin_normal, dtype=np.float64)
+    if not getattr(out, "is_cuda", False) or tuple(out.shape) != (nz, ny, nx):
+        raise ValueError("out must be a CUDA tensor of shape (nz, ny, nx)")
+    st = lib.rve_label_voronoi_noalloc(nx, ny, nz, seeds.shape[0], _ptr(seeds), _ptr(tw), _ptr(nrm), _ptr(out),
+                                       _torch_stream())
+    _check(st, None)
+    return out

@@ -38,6 +38,10 @@ WORKLOAD = "twinned RVE 128^3, 200 Voronoi grains (p_twin 0.5), FP32 fields + FP
 BYTES_PER_VOXIT_FP32 = 260          # state + strain/stress traffic of the fused iteration
 FLOPS_RHS = 1100                    # one evaluation of the constitutive right-hand side
 FP32_LANES_PER_SM, N_SM = 128, 152  # GB300
+# DRAM bytes (read + write) of one trial x-pass launch on the 128^3 FP32 workload, from ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum, mean of two launches); valid for the x-pass
+# source as profiled, to be re-taken whenever that kernel changes
+XPASS_DRAM_BYTES_128 = 435_919_488
 
 
 def flops_per_voxit(n_sub):
@@ -217,7 +221,8 @@ def run_gpu(args):
                    "l2": "inputs larger than L2 (per-iteration state ~390 MB)",
                    "parallelism": f"replicas x{ws}"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": None, "kernel": "k_xpass", "avg_launch_ms": avg,
+                     "traffic": XPASS_DRAM_BYTES_128 if nvox == 128 ** 3 else None,
+                     "traffic_unit": "bytes per launch", "kernel": "k_xpass", "avg_launch_ms": avg,
                      "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz"},
         "kernel_share": {k: round(m / total_k_ms, 4) for k, (m, _) in ktimes.items() if total_k_ms > 0},
         "kernel_avg_ms": {k: (m / n if n else None) for k, (m, n) in ktimes.items()},

@@ -165,6 +165,23 @@ rve_status rve_set_mixed_load(rve_t h, const double Edot[6], const uint8_t strai
  * total fixed-point iterations run by this call, committed increments only. */
 rve_status rve_step(rve_t h, int n_increments, long long* iterations_out);
 
+/* Run n_increments load increments on each of n independent solvers at once (an
+ * ensemble of RVE realizations of any sizes and precisions, each with its own material
+ * and load; Sec. 5 averages over such realizations).  Each handle works on a private
+ * stream created for the call, ordered after the work already enqueued on its own
+ * stream and before any work enqueued there afterwards, so the RVEs' kernels run
+ * concurrently and a small RVE does not leave the GPU idle.  The host resumes each
+ * handle as soon as its enqueued iterations finish.  Results are identical to calling
+ * rve_step on each handle in turn.
+ *   hs             n distinct handles on one device (host array, not retained);
+ *   iterations_out total committed fixed-point iterations over all handles (may be NULL);
+ *   failed_out     index of the first handle that returned an error, or -1 (may be NULL).
+ * A handle that fails (RVE_ERR_NOT_CONVERGED, RVE_ERR_NAN, ...) keeps its last committed
+ * increment and stops; the others run all n_increments.  The first error is returned and
+ * rve_last_error(NULL) names its handle.  With opt.timing the kernel times of a handle
+ * include the time its kernels shared the GPU with the other handles'. */
+rve_status rve_step_batch(rve_t* hs, int n, int n_increments, long long* iterations_out, int* failed_out);
+
 /* Effective results.  last (may be NULL) receives the most recent record;
  * hist (may be NULL) receives up to cap records, oldest first; n_hist (may be
  * NULL) receives the number of records held. */

@@ -12,6 +12,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/rve.h"
@@ -228,6 +229,14 @@ struct rve_s {
   double k_ms[RVE_K_COUNT] = {};
   long long k_n[RVE_K_COUNT] = {};
   std::vector<double> res_e, res_c;  // convergence history of the latest increment
+  // resumable increment (shared by rve_step and rve_step_batch): the host enqueues a
+  // phase of work, records ev_sync after the status copy, and resumes when it completes
+  cudaEvent_t ev_sync = nullptr;
+  int inc_phase = 0;  // 0 idle, 1 fixed-point iterations in flight, 2 commit in flight
+  int inc_it0 = 0, inc_nb = 0, inc_last = 0;
+  double inc_dE0[6] = {0, 0, 0, 0, 0, 0};
+  double inc_E[6] = {0, 0, 0, 0, 0, 0};
+  double inc_e = 0.0, inc_c = 0.0;
 };
 
 namespace {
@@ -297,6 +306,8 @@ void tcollect(rve_s* h, int work_iters) {
 }
 
 void release(rve_s* h) {
+  if (h->ev_sync) cudaEventDestroy(h->ev_sync);
+  h->ev_sync = nullptr;
   for (int k = 0; k < kTSlots; ++k) {
     if (h->ev_a[k]) cudaEventDestroy(h->ev_a[k]);
     if (h->ev_b[k]) cudaEventDestroy(h->ev_b[k]);
@@ -637,127 +648,202 @@ void initial_increment(rve_s* h, double dE0[6]) {
   }
 }
 
+// Buffer rotation: iteration it reads strain spectrum S_in(it) and writes S_out(it)
+// (then transformed in place); S_in(0) is the committed spectrum, S_out alternates
+// between the two others, and S_in(it) = S_out(it - 1).  The tau_hat spectra rotate
+// the same way.  The committed pair is only read, so a failed increment keeps it.
+struct Rotation {
+  int s0, s1, s2, p0, p1, p2;
+  explicit Rotation(const rve_s* h)
+      : s0(h->sb), s1((h->sb + 1) % 3), s2((h->sb + 2) % 3), p0(h->pb), p1((h->pb + 1) % 3), p2((h->pb + 2) % 3) {}
+  int s_out(int it) const { return (it % 2 == 0) ? s1 : s2; }
+  int s_in(int it) const { return it == 0 ? s0 : s_out(it - 1); }
+  int p_out(int it) const { return (it % 2 == 0) ? p1 : p2; }
+  int p_in(int it) const { return it == 0 ? p0 : p_out(it - 1); }
+};
+
+int max_iter_of(const rve_s* h) { return h->opt.max_iter > 0 ? h->opt.max_iter : 1000; }
+
+int np_of(const rve_s* h) { return rate_variant(h->mat.eta, is_small_int(h->mat.n), is_small_int(h->mat.nt)); }
+
+// Enqueues iterations inc_it0 .. inc_it0 + inc_nb - 1, then the status copy and ev_sync.
+// The residual kernel decides convergence on the device; later launches of the batch
+// return at once.
 template <typename T>
-rve_status step_one(rve_s* h, long long* iters) {
+rve_status enqueue_iterations(rve_s* h) {
   cudaStream_t s = h->stream;
-  const int np = rate_variant(h->mat.eta, is_small_int(h->mat.n), is_small_int(h->mat.nt));
-  double dE0[6];
-  initial_increment(h, dE0);
-  // E^(0) into slot 0 of the device status record; clear the NaN flag and the decision
-  for (int c = 0; c < 6; ++c) h->st_host->E[0][c] = h->E_n[c] + dE0[c];
-  RVE_CUDA(h, cudaMemcpyAsync(h->st->E[0], h->st_host->E[0], 6 * sizeof(double), cudaMemcpyHostToDevice, s));
-  RVE_CUDA(h, cudaMemsetAsync(&h->st->nan_flag, 0, 3 * sizeof(int), s));
-  // Buffer rotation: iteration it reads strain spectrum S_in(it) and writes S_out(it)
-  // (then transformed in place); S_in(0) is the committed spectrum, S_out alternates
-  // between the two others, and S_in(it) = S_out(it - 1).  The tau_hat spectra rotate
-  // the same way.  The committed pair is only read, so a failed increment keeps it.
-  const int s0 = h->sb, s1 = (h->sb + 1) % 3, s2 = (h->sb + 2) % 3;
-  const int p0 = h->pb, p1 = (h->pb + 1) % 3, p2 = (h->pb + 2) % 3;
-  auto s_out = [&](int it) { return (it % 2 == 0) ? s1 : s2; };
-  auto s_in = [&](int it) { return it == 0 ? s0 : s_out(it - 1); };
-  auto p_out = [&](int it) { return (it % 2 == 0) ? p1 : p2; };
-  auto p_in = [&](int it) { return it == 0 ? p0 : p_out(it - 1); };
-  tstart(h, kSlotShift, RVE_K_SHIFT);
-  RVE_CUDA(h, launch_shift<T>((C2<T>*)h->spec[s0], (C2<T>*)h->backup, h->NL, h->H, dE0, false, s));
-  tstop(h, kSlotShift);
+  const Rotation r(h);
+  const int np = np_of(h);
   const int zgrid_x = (h->H + h->zHC - 1) / h->zHC;
   const int ygrid_x = (h->H + h->yHC - 1) / h->yHC;
-  const int max_iter = h->opt.max_iter > 0 ? h->opt.max_iter : 1000;
-  // Iterations are enqueued kBatch at a time; the residual kernel decides convergence on
-  // the device and later launches of the batch return at once.
-  int it0 = 0;
-  for (;;) {
-    const int nb = std::min(kBatch, max_iter - it0);
-    for (int b = 0; b < nb; ++b) {
-      const int it = it0 + b;
-      XArgs<T> xa = x_args<T>(h, h->spec[s_in(it)], h->spec[s_out(it)], it);
-      tstart(h, 4 * b + 0, RVE_K_XPASS);
-      RVE_CUDA(h, launch_xpass<T>(xa, np, false, h->xgrid, h->xsmem, s));
-      tstop(h, 4 * b + 0);
-      LineArgs<T> ya = y_args<T>(h, h->spec[s_out(it)]);
-      tstart(h, 4 * b + 1, RVE_K_YFWD);
-      RVE_CUDA(h, launch_line<T>(ya, -1, dim3(ygrid_x, h->nz), h->ysmem, s));
-      tstop(h, 4 * b + 1);
-      ZArgs<T> za = z_args<T>(h, h->spec[s_out(it)], h->P[p_in(it)], h->P[p_out(it)], it);
-      tstart(h, 4 * b + 2, RVE_K_ZGREEN);
-      RVE_CUDA(h, launch_zgreen<T>(za, dim3(zgrid_x, h->ny), h->zsmem, s));
-      tstop(h, 4 * b + 2);
-      tstart(h, 4 * b + 3, RVE_K_YINV);
-      RVE_CUDA(h, launch_line<T>(ya, +1, dim3(ygrid_x, h->nz), h->ysmem, s));
-      tstop(h, 4 * b + 3);
-    }
-    RVE_CUDA(h, cudaMemcpyAsync(h->st_host, h->st, sizeof(IterStatus), cudaMemcpyDeviceToHost, s));
-    RVE_CUDA(h, cudaStreamSynchronize(s));
-    const int done = h->st_host->done;
-    tcollect(h, done ? h->st_host->done_it - it0 + 1 : nb);
-    if (done || it0 + nb >= max_iter) break;
-    it0 += nb;
+  h->inc_nb = std::min(kBatch, max_iter_of(h) - h->inc_it0);
+  for (int b = 0; b < h->inc_nb; ++b) {
+    const int it = h->inc_it0 + b;
+    XArgs<T> xa = x_args<T>(h, h->spec[r.s_in(it)], h->spec[r.s_out(it)], it);
+    tstart(h, 4 * b + 0, RVE_K_XPASS);
+    RVE_CUDA(h, launch_xpass<T>(xa, np, false, h->xgrid, h->xsmem, s));
+    tstop(h, 4 * b + 0);
+    LineArgs<T> ya = y_args<T>(h, h->spec[r.s_out(it)]);
+    tstart(h, 4 * b + 1, RVE_K_YFWD);
+    RVE_CUDA(h, launch_line<T>(ya, -1, dim3(ygrid_x, h->nz), h->ysmem, s));
+    tstop(h, 4 * b + 1);
+    ZArgs<T> za = z_args<T>(h, h->spec[r.s_out(it)], h->P[r.p_in(it)], h->P[r.p_out(it)], it);
+    tstart(h, 4 * b + 2, RVE_K_ZGREEN);
+    RVE_CUDA(h, launch_zgreen<T>(za, dim3(zgrid_x, h->ny), h->zsmem, s));
+    tstop(h, 4 * b + 2);
+    tstart(h, 4 * b + 3, RVE_K_YINV);
+    RVE_CUDA(h, launch_line<T>(ya, +1, dim3(ygrid_x, h->nz), h->ysmem, s));
+    tstop(h, 4 * b + 3);
   }
-  const IterStatus st = *h->st_host;
-  const int last = st.done ? st.done_it : max_iter - 1;
-  {
-    std::vector<double> hh(2 * (size_t)(last + 1));
-    RVE_CUDA(h, cudaMemcpyAsync(hh.data(), h->dhist, hh.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
-    RVE_CUDA(h, cudaStreamSynchronize(s));
-    h->res_e.resize(last + 1);
-    h->res_c.resize(last + 1);
-    for (int i = 0; i <= last; ++i) {
-      h->res_e[i] = hh[2 * i];
-      h->res_c[i] = hh[2 * i + 1];
-    }
-  }
-  if (st.done != 1) {
-    // roll back: undo the start-of-increment shift of the committed spectrum
-    RVE_CUDA(h, launch_shift<T>((C2<T>*)h->spec[s0], (C2<T>*)h->backup, h->NL, h->H, dE0, true, s));
-    RVE_CUDA(h, cudaStreamSynchronize(s));
-    if (st.done == 2)
-      return fail(h, RVE_ERR_NAN, std::string("NaN or Inf in the ") +
-                                      ((st.nan_flag & 1) ? "mean stress" : "equilibrium residual") + " at increment " +
-                                      std::to_string(h->increment + 1) + ", iteration " + std::to_string(last));
-    char buf[200];
-    std::snprintf(buf, sizeof(buf), "increment %d: no convergence in %d iterations (e=%.3e, cF=%.3e)",
-                  h->increment + 1, max_iter, st.e_eq, st.cF);
-    return fail(h, RVE_ERR_NOT_CONVERGED, buf);
-  }
-  // a8: commit the converged iterate
-  const int it = st.done_it;
-  const double e_eq = st.e_eq, cF = st.cF;
-  double E[6];
-  for (int c = 0; c < 6; ++c) E[c] = st.E[it & 1][c];
-  XArgs<T> ca = x_args<T>(h, h->spec[s_in(it)], nullptr, it);
-  tstart(h, kSlotCommit, RVE_K_COMMIT);
-  RVE_CUDA(h, launch_xpass<T>(ca, np, true, h->xgrid, h->xsmem, s));
-  tstop(h, kSlotCommit);
   RVE_CUDA(h, cudaMemcpyAsync(h->st_host, h->st, sizeof(IterStatus), cudaMemcpyDeviceToHost, s));
-  RVE_CUDA(h, cudaStreamSynchronize(s));
+  RVE_CUDA(h, cudaEventRecord(h->ev_sync, s));
+  return RVE_OK;
+}
+
+// Starts increment n -> n+1: macroscopic step and initial guess (a1), then the first
+// batch of iterations.
+template <typename T>
+rve_status inc_begin(rve_s* h) {
+  cudaStream_t s = h->stream;
+  initial_increment(h, h->inc_dE0);
+  // E^(0) into slot 0 of the device status record; clear the NaN flag and the decision
+  for (int c = 0; c < 6; ++c) h->st_host->E[0][c] = h->E_n[c] + h->inc_dE0[c];
+  RVE_CUDA(h, cudaMemcpyAsync(h->st->E[0], h->st_host->E[0], 6 * sizeof(double), cudaMemcpyHostToDevice, s));
+  RVE_CUDA(h, cudaMemsetAsync(&h->st->nan_flag, 0, 3 * sizeof(int), s));
+  const Rotation r(h);
+  tstart(h, kSlotShift, RVE_K_SHIFT);
+  RVE_CUDA(h, launch_shift<T>((C2<T>*)h->spec[r.s0], (C2<T>*)h->backup, h->NL, h->H, h->inc_dE0, false, s));
+  tstop(h, kSlotShift);
+  h->inc_it0 = 0;
+  h->inc_phase = 1;
+  rve_status st = enqueue_iterations<T>(h);
+  if (st) h->inc_phase = 0;
+  return st;
+}
+
+// Resumes after ev_sync completed.  Sets *finished when the increment is committed (or
+// has failed and been rolled back; the status says which).
+template <typename T>
+rve_status inc_advance(rve_s* h, bool* finished, long long* iters) {
+  cudaStream_t s = h->stream;
+  const Rotation r(h);
+  *finished = false;
+  if (h->inc_phase == 1) {
+    const int done = h->st_host->done;
+    const int it0 = h->inc_it0, nb = h->inc_nb;
+    tcollect(h, done ? h->st_host->done_it - it0 + 1 : nb);
+    const int max_iter = max_iter_of(h);
+    if (!done && it0 + nb < max_iter) {
+      h->inc_it0 += nb;
+      rve_status st = enqueue_iterations<T>(h);
+      if (st) { h->inc_phase = 0; *finished = true; }
+      return st;
+    }
+    const IterStatus stat = *h->st_host;
+    const int last = stat.done ? stat.done_it : max_iter - 1;
+    {
+      std::vector<double> hh(2 * (size_t)(last + 1));
+      h->inc_phase = 0;
+      *finished = true;  // unless the commit below is enqueued
+      RVE_CUDA(h, cudaMemcpyAsync(hh.data(), h->dhist, hh.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+      RVE_CUDA(h, cudaStreamSynchronize(s));
+      h->res_e.resize(last + 1);
+      h->res_c.resize(last + 1);
+      for (int i = 0; i <= last; ++i) {
+        h->res_e[i] = hh[2 * i];
+        h->res_c[i] = hh[2 * i + 1];
+      }
+    }
+    if (stat.done != 1) {
+      // roll back: undo the start-of-increment shift of the committed spectrum
+      RVE_CUDA(h, launch_shift<T>((C2<T>*)h->spec[r.s0], (C2<T>*)h->backup, h->NL, h->H, h->inc_dE0, true, s));
+      RVE_CUDA(h, cudaStreamSynchronize(s));
+      if (stat.done == 2)
+        return fail(h, RVE_ERR_NAN, std::string("NaN or Inf in the ") +
+                                        ((stat.nan_flag & 1) ? "mean stress" : "equilibrium residual") +
+                                        " at increment " + std::to_string(h->increment + 1) + ", iteration " +
+                                        std::to_string(last));
+      char buf[200];
+      std::snprintf(buf, sizeof(buf), "increment %d: no convergence in %d iterations (e=%.3e, cF=%.3e)",
+                    h->increment + 1, max_iter, stat.e_eq, stat.cF);
+      return fail(h, RVE_ERR_NOT_CONVERGED, buf);
+    }
+    // a8: commit the converged iterate
+    const int it = stat.done_it;
+    h->inc_last = it;
+    h->inc_e = stat.e_eq;
+    h->inc_c = stat.cF;
+    for (int c = 0; c < 6; ++c) h->inc_E[c] = stat.E[it & 1][c];
+    XArgs<T> ca = x_args<T>(h, h->spec[r.s_in(it)], nullptr, it);
+    tstart(h, kSlotCommit, RVE_K_COMMIT);
+    RVE_CUDA(h, launch_xpass<T>(ca, np_of(h), true, h->xgrid, h->xsmem, s));
+    tstop(h, kSlotCommit);
+    RVE_CUDA(h, cudaMemcpyAsync(h->st_host, h->st, sizeof(IterStatus), cudaMemcpyDeviceToHost, s));
+    RVE_CUDA(h, cudaEventRecord(h->ev_sync, s));
+    h->inc_phase = 2;
+    *finished = false;
+    return RVE_OK;
+  }
+  if (h->inc_phase != 2) {
+    *finished = true;
+    return fail(h, RVE_ERR_STATE, "no increment in progress");
+  }
+  // the commit completed: advance the host state
+  *finished = true;
+  h->inc_phase = 0;
   tcollect(h, 0);
-  h->sb = s_in(it);
-  h->pb = p_in(it);
+  const int it = h->inc_last;
+  h->sb = r.s_in(it);
+  h->pb = r.p_in(it);
   for (int c = 0; c < 6; ++c) {
     h->E_prev[c] = h->E_n[c];
-    h->E_n[c] = E[c];
+    h->E_n[c] = h->inc_E[c];
   }
   h->time += h->dt;
   h->increment += 1;
-  rve_effective r;
-  std::memset(&r, 0, sizeof(r));
-  r.increment = h->increment;
-  r.iterations = it + 1;
-  r.time = h->time;
+  rve_effective rec;
+  std::memset(&rec, 0, sizeof(rec));
+  rec.increment = h->increment;
+  rec.iterations = it + 1;
+  rec.time = h->time;
   for (int c = 0; c < 6; ++c) {
-    r.E[c] = E[c];
-    r.S[c] = h->st_host->sig_mean[c];
+    rec.E[c] = h->inc_E[c];
+    rec.S[c] = h->st_host->sig_mean[c];
   }
-  r.S_eq_of_mean = vm_of(r.S);
-  r.mean_S_eq = h->st_host->eff[0];
-  r.mean_f = h->st_host->eff[1];
-  r.mean_v = h->st_host->eff[2];
-  r.residual = e_eq;
-  r.stress_residual = cF;
-  h->hist.push_back(r);
+  rec.S_eq_of_mean = vm_of(rec.S);
+  rec.mean_S_eq = h->st_host->eff[0];
+  rec.mean_f = h->st_host->eff[1];
+  rec.mean_v = h->st_host->eff[2];
+  rec.residual = h->inc_e;
+  rec.stress_residual = h->inc_c;
+  h->hist.push_back(rec);
   if (iters) *iters += it + 1;
   if (h->st_host->nan_flag) return fail(h, RVE_ERR_NAN, "NaN or Inf in the committed fields");
   return RVE_OK;
+}
+
+rve_status inc_begin_any(rve_s* h) {
+  return h->opt.precision == RVE_FP64 ? inc_begin<double>(h) : inc_begin<float>(h);
+}
+
+rve_status inc_advance_any(rve_s* h, bool* finished, long long* iters) {
+  return h->opt.precision == RVE_FP64 ? inc_advance<double>(h, finished, iters)
+                                      : inc_advance<float>(h, finished, iters);
+}
+
+// One increment on the handle's stream, waiting for each phase.
+rve_status step_one(rve_s* h, long long* iters) {
+  rve_status st = inc_begin_any(h);
+  bool finished = st != RVE_OK;
+  while (!finished) {
+    cudaError_t e = cudaEventSynchronize(h->ev_sync);
+    if (e != cudaSuccess) {
+      h->inc_phase = 0;
+      return cuda_fail(h, e, "cudaEventSynchronize");
+    }
+    st = inc_advance_any(h, &finished, iters);
+  }
+  return st;
 }
 
 bool valid_len(int n) {
@@ -909,6 +995,8 @@ rve_status rve_create(rve_t* out, int nx, int ny, int nz, const uint32_t* grain_
       return s;
     }
   }
+  e = cudaEventCreateWithFlags(&h->ev_sync, cudaEventDisableTiming);
+  if (e != cudaSuccess) { s = cuda_fail(h, e, "cudaEventCreate"); rve_destroy(h); return s; }
   if (o.timing)
     for (int k = 0; k < kTSlots; ++k) {
       e = cudaEventCreate(&h->ev_a[k]);
@@ -956,10 +1044,97 @@ rve_status rve_step(rve_t h, int n, long long* iters) {
   cudaError_t e = cudaSetDevice(h->opt.device);
   if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
   for (int i = 0; i < n; ++i) {
-    rve_status s = h->opt.precision == RVE_FP64 ? step_one<double>(h, iters) : step_one<float>(h, iters);
+    rve_status s = step_one(h, iters);
     if (s) return s;
   }
   return RVE_OK;
+}
+
+rve_status rve_step_batch(rve_t* hs, int n, int n_increments, long long* iters, int* failed) {
+  if (failed) *failed = -1;
+  if (iters) *iters = 0;
+  if (n < 0 || n_increments < 0 || (n > 0 && !hs)) return fail(nullptr, RVE_ERR_INVALID_ARG, "bad batch arguments");
+  for (int i = 0; i < n; ++i) {
+    if (!hs[i]) return fail(nullptr, RVE_ERR_INVALID_ARG, "NULL handle in the batch");
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) return fail(nullptr, RVE_ERR_INVALID_ARG, "a handle is listed twice in the batch");
+    if (hs[i]->opt.device != hs[0]->opt.device)
+      return fail(nullptr, RVE_ERR_INVALID_ARG, "all handles of a batch must be on one device");
+  }
+  if (n == 0 || n_increments == 0) return RVE_OK;
+  cudaError_t e = cudaSetDevice(hs[0]->opt.device);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaSetDevice");
+  // Each handle runs on a private stream, ordered after the work already enqueued on its
+  // own stream and before anything enqueued there after this call.
+  std::vector<cudaStream_t> orig(n), priv(n, nullptr);
+  rve_status first = RVE_OK;
+  int first_i = -1;
+  auto note = [&](int i, rve_status st) {
+    if (st != RVE_OK && first == RVE_OK) {
+      first = st;
+      first_i = i;
+    }
+  };
+  int made = 0;
+  for (; made < n; ++made) {
+    rve_s* h = hs[made];
+    orig[made] = h->stream;
+    e = cudaStreamCreateWithFlags(&priv[made], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_sync, h->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(priv[made], h->ev_sync, 0);
+    if (e != cudaSuccess) {
+      note(made, cuda_fail(h, e, "batch stream set-up"));
+      if (priv[made]) cudaStreamDestroy(priv[made]);
+      break;
+    }
+    h->stream = priv[made];
+  }
+  std::vector<int> left(n, n_increments);
+  std::vector<char> active(n, 0);
+  int n_active = 0;
+  if (first == RVE_OK)
+    for (int i = 0; i < n; ++i) {
+      rve_status st = inc_begin_any(hs[i]);
+      if (st) note(i, st);
+      else { active[i] = 1; ++n_active; }
+    }
+  // Round-robin over the handles: resume each one whose last enqueued phase finished.
+  while (n_active > 0) {
+    bool progressed = false;
+    for (int i = 0; i < n; ++i) {
+      if (!active[i]) continue;
+      rve_s* h = hs[i];
+      const cudaError_t q = cudaEventQuery(h->ev_sync);
+      if (q == cudaErrorNotReady) continue;
+      progressed = true;
+      bool fin = false;
+      rve_status st;
+      if (q != cudaSuccess) {
+        h->inc_phase = 0;
+        st = cuda_fail(h, q, "cudaEventQuery");
+      } else {
+        st = inc_advance_any(h, &fin, iters);
+      }
+      if (st == RVE_OK && fin && --left[i] > 0) st = inc_begin_any(h);
+      if (st != RVE_OK || (fin && left[i] == 0)) {
+        note(i, st);
+        active[i] = 0;
+        --n_active;
+      }
+    }
+    if (!progressed) std::this_thread::yield();
+  }
+  for (int i = 0; i < made; ++i) {
+    rve_s* h = hs[i];
+    e = cudaEventRecord(h->ev_sync, priv[i]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(orig[i], h->ev_sync, 0);
+    if (e != cudaSuccess) note(i, cuda_fail(h, e, "batch stream join"));
+    h->stream = orig[i];
+    cudaStreamDestroy(priv[i]);
+  }
+  if (failed) *failed = first_i;
+  if (first != RVE_OK) g_err = "handle " + std::to_string(first_i) + ": " + hs[first_i]->err;
+  return first;
 }
 
 rve_status rve_get_effective(rve_t h, rve_effective* last, rve_effective* hist, int cap, int* n_hist) {

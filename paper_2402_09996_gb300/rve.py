@@ -32,6 +32,7 @@ STATUS = {
     6: "RVE_ERR_STATE",
     7: "RVE_ERR_UNSUPPORTED",
 }
+STATUS_CODES = {name: code for code, name in STATUS.items()}
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
@@ -99,9 +100,10 @@ class Effective(C.Structure):
 
 
 class RVEError(RuntimeError):
-    def __init__(self, status: int, message: str):
+    def __init__(self, status: int, message: str, index: int = -1):
         super().__init__(f"{STATUS.get(status, status)}: {message}")
         self.status = status
+        self.index = index  # failing solver of a batch call, else -1
 
 
 _lib = None
@@ -111,6 +113,7 @@ EXPORTED = [
     "rve_set_mixed_load", "rve_step", "rve_get_effective", "rve_get_fields", "rve_save_state",
     "rve_load_state", "rve_last_error", "rve_destroy", "rve_material_point", "rve_fft_r2c",
     "rve_fft_c2r", "rve_label_voronoi", "rve_kernel_times", "rve_get_residuals", "rve_label_voronoi_noalloc",
+    "rve_step_batch",
 ]
 NOALLOC_MAX_PARENTS = 4096  # RVE_NOALLOC_MAX_PARENTS of include/rve.h
 
@@ -146,6 +149,7 @@ def load_library(path: str | os.PathLike | None = None):
     lib.rve_kernel_times.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong), i]
     lib.rve_get_residuals.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double), i, C.POINTER(i)]
     lib.rve_label_voronoi_noalloc.argtypes = [i, i, i, i, vp, vp, vp, vp, vp]
+    lib.rve_step_batch.argtypes = [C.POINTER(vp), i, i, C.POINTER(C.c_longlong), C.POINTER(i)]
     for name in EXPORTED:
         getattr(lib, name).restype = C.c_int
     lib.rve_options_default.restype = None
@@ -354,6 +358,23 @@ class RVE:
 
 
 # ---- kernel-level entry points ----------------------------------------------
+def step_batch(solvers, n_increments=1) -> int:
+    """Advance several RVE solvers by n_increments each, concurrently (rve_step_batch).
+    Returns the total fixed-point iterations; raises RVEError naming the first failing
+    solver (the others still ran all increments)."""
+    solvers = list(solvers)
+    if not solvers:
+        return 0
+    lib = load_library()
+    arr = (C.c_void_p * len(solvers))(*[s.h for s in solvers])
+    it = C.c_longlong(0)
+    failed = C.c_int(-1)
+    st = lib.rve_step_batch(arr, len(solvers), int(n_increments), C.byref(it), C.byref(failed))
+    if st != 0:
+        raise RVEError(st, lib.rve_last_error(None).decode(), index=failed.value)
+    return int(it.value)
+
+
 def material_point(R, eps_n, eps, state, dt, n_sub, precision=FP64, **material):
     """One increment of the per-voxel constitutive update on CUDA tensors.
 

@@ -301,6 +301,104 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_ensemble(args):
+    """Batched ensemble: 16 RVEs of 64^3..160^3 (half twinned) stepped together with
+    rve_step_batch in FP32 fields, against the FP64 plain path (one RVE at a time) timed
+    on a bounded sample.  One step = one load increment of every member."""
+    import torch
+
+    from paper_2402_09996_gb300 import build_lib, inputs, rve
+
+    build_lib.build()
+    members = inputs.workload_ensemble()
+    dt = 0.5
+    stream = torch.cuda.current_stream()
+
+    def build():
+        out = []
+        for inp in members:
+            s = rve.RVE(rve.label_voronoi(inp), inp.euler, precision=rve.FP32, n_sub=0)
+            s.set_mixed_load(dt=dt)
+            out.append(s)
+        rve.step_batch(out, args.warmup)
+        torch.cuda.synchronize()
+        return out, [sum(h["iterations"] for h in s.history()) for s in out]
+
+    def timed(fn, solvers, before):
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        fn()
+        t1.record(stream)
+        torch.cuda.synchronize()
+        its = [sum(h["iterations"] for h in s.history()) - b for s, b in zip(solvers, before)]
+        return t0.elapsed_time(t1), its
+
+    # the same increments twice: every member stepped alone in turn, then all together
+    solvers, before = build()
+    nvox = [s.nvox for s in solvers]
+    ms_seq, its_seq = timed(lambda: [s.step(args.steps) for s in solvers], solvers, before)
+    for s in solvers:
+        s.close()
+    solvers, before = build()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    ms, its = timed(lambda: rve.step_batch(solvers, args.steps), solvers, before)
+    clk = clocks.stop()
+    for s in solvers:
+        s.close()
+    voxit = float(sum(n * i for n, i in zip(nvox, its)))
+    value = voxit / (ms * 1e-3)
+    seq_value = float(sum(n * i for n, i in zip(nvox, its_seq))) / (ms_seq * 1e-3)
+
+    # FP64 plain path on a bounded sample: the first 64^3 twinned member alone, its first
+    # warm-up increments untimed, then one timed increment in the plastic regime
+    inp = members[0]
+    s64 = rve.RVE(rve.label_voronoi(inp), inp.euler, precision=rve.FP64, n_sub=0)
+    s64.set_mixed_load(dt=dt)
+    s64.step(args.warmup)
+    torch.cuda.synchronize()
+    u0 = torch.cuda.Event(enable_timing=True)
+    u1 = torch.cuda.Event(enable_timing=True)
+    u0.record(stream)
+    it64 = s64.step(1)
+    u1.record(stream)
+    torch.cuda.synchronize()
+    fp64_value = s64.nvox * it64 / (u0.elapsed_time(u1) * 1e-3)
+    s64.close()
+    n_sub = 4
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": METRIC,
+        "n_gpus": 1,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "ensemble of 16 RVEs: 4 each of 64^3, 96^3, 128^3, 160^3 (50/125/241/400 grains), "
+                               "two of each size twinned (p_twin 0.5); FP32 fields + FP64 norms; uniaxial tension "
+                               "1e-3/s, dt 0.5 s; all members stepped together (rve_step_batch)",
+                   "voxels": int(sum(nvox)), "increments_timed": f"{args.warmup + 1}..{args.warmup + args.steps}",
+                   "fixed_point_iterations_timed": its, "n_sub": n_sub,
+                   "l2": "inputs larger than L2 (state ~6 GB)"},
+        "whole_step_alu": {"achieved": flops_per_voxit(n_sub) * value / 1e12,
+                           "peak": FP32_LANES_PER_SM * N_SM * 2 * 2070.0 * 1e6 / 1e12, "unit": "TFLOP/s",
+                           "what": "algorithmic flops of the whole iteration over the whole batch time"},
+        "fp32_sequential": {"value": seq_value, "unit": METRIC, "ms_per_step": ms_seq / args.steps,
+                            "what": "the same increments, each member stepped alone in turn (rve_step)"},
+        "fp64_plain": {"value": fp64_value, "unit": METRIC,
+                       "sample": f"64^3 twinned member alone in FP64, increment {args.warmup + 1}, {it64} iterations"},
+        "speedup_fp32_batched_vs_fp64_plain": value / fp64_value,
+        "clocks": clk,
+    }
+    print(json.dumps(line))
+
+
 def run_profile_case(args):
     """A small case for `ncu --profile-from-start off`: the kernels of --steps increments in
     the plastic regime, on inputs of a few hundred MB, after --warmup untimed increments."""
@@ -330,6 +428,8 @@ def main_args(argv=None):
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="twinned128", choices=["twinned128", "ensemble"],
+                    help="ensemble: the 16-RVE batched workload (prints its own JSON line)")
     ap.add_argument("--profile-case", type=int, default=0, metavar="N",
                     help="profiling case: an N^3 twinned RVE (60 grains, p=0.5, seed 11), "
                          "--warmup increments, then --steps increments between "
@@ -346,6 +446,8 @@ def main():
         run_reference(args)
     elif args.profile_case:
         run_profile_case(args)
+    elif args.workload == "ensemble":
+        run_ensemble(args)
     else:
         run_gpu(args)
 

@@ -151,3 +151,21 @@ def workload_plain_16():
 def workload_twinned_128():
     """128^3 voxels, 200 grains, each twinned with probability 0.5 (FP32 fields)."""
     return make_inputs((128, 128, 128), 200, 0.5, seed=1000 * 1 + 0)
+
+
+ENSEMBLE_SIZES = (64, 96, 128, 160)
+ENSEMBLE_GRAINS = (50, 125, 241, 400)  # 50 at 64^3 to 400 at 160^3 (see workload_ensemble)
+
+
+def workload_ensemble():
+    """16 realizations: 4 each of 64^3, 96^3, 128^3 and 160^3 voxels; the first two of each
+    size twinned (p_twin 0.5), the other two untwinned; grain counts 50, 125, 241, 400,
+    i.e. n = 50 (V / 64^3)^(ln 8 / ln 15.625), the power law through (64^3, 50) and
+    (160^3, 400); realization r (0..15) draws with seed 3000 + r."""
+    out = []
+    r = 0
+    for n, g in zip(ENSEMBLE_SIZES, ENSEMBLE_GRAINS):
+        for j in range(4):
+            out.append(make_inputs((n, n, n), g, 0.5 if j < 2 else 0.0, seed=1000 * 3 + r))
+            r += 1
+    return out

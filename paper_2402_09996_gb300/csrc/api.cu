@@ -322,6 +322,15 @@ void release(rve_s* h) {
   h->st_host = nullptr;
 }
 
+// Rate-root tables: one when the twin exponent equals the slip exponent, else two (slip,
+// twin).  The x pass stages them in shared memory after its FFT buffers.
+int root_tab_len(const rve_material& m) { return m.nt == m.n ? kRootTabLen : 2 * kRootTabLen; }
+
+size_t xsmem_total(const rve_s* h) {
+  const size_t elem = h->opt.precision == RVE_FP64 ? sizeof(double) : sizeof(float);
+  return h->xsmem + (size_t)root_tab_len(h->mat) * elem;
+}
+
 template <typename T>
 MatDev<T> make_mat(const rve_s* h) {
   const rve_material& m = h->mat;
@@ -345,6 +354,7 @@ MatDev<T> make_mat(const rve_s* h) {
   M.lg_K = (T)std::log2(m.K);
   M.lg_Kt = (T)std::log2(m.Kt);
   M.lg_eta = (T)(m.eta > 0 ? std::log2(m.eta) : 0.0);
+  M.tab_twin = m.nt == m.n ? 0 : kRootTabLen;
   return M;
 }
 
@@ -459,7 +469,7 @@ rve_status alloc_fields(rve_s* h) {
     h->L = (int)std::max(fill, std::min(most, keep));
   }
   h->xgrid = (int)((h->NL + h->L - 1) / h->L);
-  h->xsmem = (size_t)(h->nx + 6 * h->L * h->nx) * 2 * sizeof(T) + 2 * kRootTab * sizeof(T);
+  h->xsmem = (size_t)(h->nx + 6 * h->L * h->nx) * 2 * sizeof(T);  // FFT buffers; + tables: xsmem_total
   const size_t budget = 96 * 1024;
   // y and z passes: tiles of HC kx values x 6 components (two buffers of padded lines);
   // about 50 KB per CTA so that four CTAs share an SM
@@ -484,28 +494,38 @@ rve_status alloc_fields(rve_s* h) {
   return RVE_OK;
 }
 
-// Deviation table of the regularised-rate root (constitutive.cuh, reg_rate_tab): on
-// kRootTab nodes lb in [-kRootSpan, kRootSpan], d = log2 u* - min(0, -lb) where u* in
-// (0, 1] solves u^n + 2^lb u = 1 (bisection to double precision).
+// Root table of the regularised rate (constitutive.cuh, reg_rate_tab) for exponent n:
+// D = log2 u*, u* in (0, 1] the root of u^n + 2^x u = 1 (bisection to double precision),
+// on the nodes x_k = -kRootSpan + k / kRootPerUnit, k = 0..kRootIv, stored per interval
+// as the line through its two end nodes, D = a_i + b_i t with t = (x + kRootSpan)
+// kRootPerUnit - 1/2.  The kink of the asymptotes min(0, -x) sits on the node x = 0, so
+// every interval is smooth.
 void root_table(double n, double* out) {
-  for (int k = 0; k < kRootTab; ++k) {
-    const double lb = -kRootSpan + 2.0 * kRootSpan * (double)k / (double)(kRootTab - 1);
-    const double beta = std::exp2(lb);
+  std::vector<double> D(kRootIv + 1);
+  for (int k = 0; k <= kRootIv; ++k) {
+    const double x = -kRootSpan + (double)k / kRootPerUnit;
+    const double beta = std::exp2(x);
     double lo = 0.0, hi = 1.0;
     for (int i = 0; i < 200; ++i) {
       const double mid = 0.5 * (lo + hi);
       if (std::pow(mid, n) + beta * mid - 1.0 > 0.0) hi = mid;
       else lo = mid;
     }
-    out[k] = std::log2(0.5 * (lo + hi)) - std::min(0.0, -lb);
+    D[k] = std::log2(0.5 * (lo + hi));
+  }
+  for (int i = 0; i < kRootIv; ++i) {
+    const double b = D[i + 1] - D[i];
+    out[2 * i] = D[i] + b * (0.5 - (double)i);
+    out[2 * i + 1] = b;
   }
 }
 
 template <typename T>
 std::vector<T> root_tables(const rve_material& m) {
-  std::vector<double> d(2 * kRootTab);
+  std::vector<double> d(2 * kRootTabLen);
   root_table(m.n, d.data());
-  root_table(m.nt, d.data() + kRootTab);
+  root_table(m.nt, d.data() + kRootTabLen);
+  d.resize(root_tab_len(m));
   return std::vector<T>(d.begin(), d.end());
 }
 
@@ -513,7 +533,7 @@ template <typename T>
 rve_status upload_root_tab(rve_s* h) {
   const std::vector<T> t = root_tables<T>(h->mat);
   if (!h->root_tab) {
-    rve_status s = dalloc(h, &h->root_tab, t.size() * sizeof(T));
+    rve_status s = dalloc(h, &h->root_tab, (size_t)2 * kRootTabLen * sizeof(T));  // room for two tables
     if (s) return s;
   }
   RVE_CUDA(h, cudaMemcpyAsync(h->root_tab, t.data(), t.size() * sizeof(T), cudaMemcpyHostToDevice, h->stream));
@@ -681,7 +701,7 @@ rve_status enqueue_iterations(rve_s* h) {
     const int it = h->inc_it0 + b;
     XArgs<T> xa = x_args<T>(h, h->spec[r.s_in(it)], h->spec[r.s_out(it)], it);
     tstart(h, 4 * b + 0, RVE_K_XPASS);
-    RVE_CUDA(h, launch_xpass<T>(xa, np, false, h->xgrid, h->xsmem, s));
+    RVE_CUDA(h, launch_xpass<T>(xa, np, false, h->xgrid, xsmem_total(h), s));
     tstop(h, 4 * b + 0);
     LineArgs<T> ya = y_args<T>(h, h->spec[r.s_out(it)]);
     tstart(h, 4 * b + 1, RVE_K_YFWD);
@@ -776,7 +796,7 @@ rve_status inc_advance(rve_s* h, bool* finished, long long* iters) {
     for (int c = 0; c < 6; ++c) h->inc_E[c] = stat.E[it & 1][c];
     XArgs<T> ca = x_args<T>(h, h->spec[r.s_in(it)], nullptr, it);
     tstart(h, kSlotCommit, RVE_K_COMMIT);
-    RVE_CUDA(h, launch_xpass<T>(ca, np_of(h), true, h->xgrid, h->xsmem, s));
+    RVE_CUDA(h, launch_xpass<T>(ca, np_of(h), true, h->xgrid, xsmem_total(h), s));
     tstop(h, kSlotCommit);
     RVE_CUDA(h, cudaMemcpyAsync(h->st_host, h->st, sizeof(IterStatus), cudaMemcpyDeviceToHost, s));
     RVE_CUDA(h, cudaEventRecord(h->ev_sync, s));

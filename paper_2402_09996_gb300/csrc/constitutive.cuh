@@ -63,30 +63,53 @@ __device__ __forceinline__ void hooke(const MatDev<T>& M, const T* e, T* s) {
   s[5] = T(2) * M.C66 * e[5];
 }
 
+// Integer Schmid coefficients of system s on the six components (11, 22, 33, 23, 13, 12):
+// n . x . l = sum_c schmid_k(s, c) x_c for a symmetric x, with schmid_k = n_i l_i on the
+// diagonal and n_i l_j + n_j l_i on the shear components.
+__host__ __device__ __forceinline__ constexpr int schmid_k(int s, int c) {
+  return c == 0   ? sys_n(s, 0) * sys_l(s, 0)
+         : c == 1 ? sys_n(s, 1) * sys_l(s, 1)
+         : c == 2 ? sys_n(s, 2) * sys_l(s, 2)
+         : c == 3 ? sys_n(s, 1) * sys_l(s, 2) + sys_n(s, 2) * sys_l(s, 1)
+         : c == 4 ? sys_n(s, 0) * sys_l(s, 2) + sys_n(s, 2) * sys_l(s, 0)
+                  : sys_n(s, 0) * sys_l(s, 1) + sys_n(s, 1) * sys_l(s, 0);
+}
+
+// sum_c schmid_k(s, c) x_c.  With s a constant (unrolled loops) the zero coefficients
+// drop out and unit ones become additions (a product with 0.0 would not fold under IEEE
+// rules).
+template <typename T>
+__device__ __forceinline__ T schmid_sum(int s, const T* x) {
+  T r = T(0);
+  bool any = false;
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    const int k = schmid_k(s, c);
+    if (k != 0) {
+      const T term = k == 1 ? x[c] : (k == -1 ? -x[c] : T(k) * x[c]);
+      r = any ? r + term : term;
+      any = true;
+    }
+  }
+  return r;
+}
+
+// acc_c += schmid_k(s, c) w
+template <typename T>
+__device__ __forceinline__ void schmid_add(int s, T w, T* acc) {
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    const int k = schmid_k(s, c);
+    if (k == 1) acc[c] += w;
+    else if (k == -1) acc[c] -= w;
+    else if (k != 0) acc[c] += T(k) * w;
+  }
+}
+
 // tau = sigma : m_s = (n . sigma . l) / (|n||l|)
 template <typename T>
 __device__ __forceinline__ T resolved(int s, const T* g) {
-  const T n0 = T(sys_n(s, 0)), n1 = T(sys_n(s, 1)), n2 = T(sys_n(s, 2));
-  const T l0 = T(sys_l(s, 0)), l1 = T(sys_l(s, 1)), l2 = T(sys_l(s, 2));
-  const T a0 = g[0] * l0 + g[5] * l1 + g[4] * l2;
-  const T a1 = g[5] * l0 + g[1] * l1 + g[3] * l2;
-  const T a2 = g[4] * l0 + g[3] * l1 + g[2] * l2;
-  return sys_scale<T>(s) * (n0 * a0 + n1 * a1 + n2 * a2);
-}
-
-// acc += w * m_s
-template <typename T>
-__device__ __forceinline__ void add_schmid(int s, T w, T* acc) {
-  const T n0 = T(sys_n(s, 0)), n1 = T(sys_n(s, 1)), n2 = T(sys_n(s, 2));
-  const T l0 = T(sys_l(s, 0)), l1 = T(sys_l(s, 1)), l2 = T(sys_l(s, 2));
-  const T f = w * sys_scale<T>(s);
-  const T h = T(0.5) * f;
-  acc[0] += f * (n0 * l0);
-  acc[1] += f * (n1 * l1);
-  acc[2] += f * (n2 * l2);
-  acc[3] += h * (n1 * l2 + n2 * l1);
-  acc[4] += h * (n0 * l2 + n2 * l0);
-  acc[5] += h * (n0 * l1 + n1 * l0);
+  return sys_scale<T>(s) * schmid_sum<T>(s, g);
 }
 
 // ---------------------------------------------------------------- powers -------------
@@ -143,8 +166,9 @@ template <typename T> __device__ __forceinline__ T fast_log2(T x);
 template <> __device__ __forceinline__ float fast_log2<float>(float x) { return __log2f(x); }
 template <> __device__ __forceinline__ double fast_log2<double>(double x) { return log2(x); }
 template <typename T> __device__ __forceinline__ T fast_exp2(T x);
-// (used only for Newton starting values, which the Newton steps correct: the hardware
-// approximation, relative error below 2^-22, subnormal results flushed to zero)
+// Float: the hardware approximation (relative error below 2^-22, subnormal results
+// flushed to zero), used for Newton starting values and the hardening terms
+// exp(-b v) = 2^(-b v log2 e) in (0, 1].
 template <> __device__ __forceinline__ float fast_exp2<float>(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -159,17 +183,26 @@ template <> __device__ __forceinline__ double fast_exp<double>(double x) { retur
 template <typename T> __device__ __forceinline__ T fast_div(T a, T b);
 template <> __device__ __forceinline__ float fast_div<float>(float a, float b) { return __fdividef(a, b); }
 template <> __device__ __forceinline__ double fast_div<double>(double a, double b) { return a / b; }
+// 1/x for the last Newton correction, which needs only a few correct digits in float
+template <typename T> __device__ __forceinline__ T fast_rcp(T x);
+template <> __device__ __forceinline__ float fast_rcp<float>(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+template <> __device__ __forceinline__ double fast_rcp<double>(double x) { return 1.0 / x; }
 
 // ---------------------------------------------------------------- rate roots ---------
 // The regularised rate rho >= 0 solves rho = P < (a - eta rho) / Kn >^n  (Sec. 4), and
 // rho = 0 when a <= 0 or P <= 0.  With z = (a - eta rho)/Kn the root solves
 // phi(z) = c z^n + Kn z - a = 0, c = eta P, and rho = P z^n.  Scaling z = zB u with
 // zB = (a/c)^(1/n) leaves u^n + beta u - 1 = 0, beta = Kn zB / a, whose root u*(beta)
-// depends on log2(beta) alone.  Its deviation d = log2 u* - min(0, -log2 beta) from the
-// two asymptotes is tabulated on kRootTab nodes over [-kRootSpan, kRootSpan] (one node
-// at 0, where the asymptotes cross); linear interpolation starts Newton within 3e-5,
-// so a fixed number of Newton steps reaches round-off (1 in float, 3 in double) and the
-// solve has no data-dependent branch.  Logarithms are base 2.
+// depends on x = log2(beta) alone.  log2 u*(x) is tabulated per exponent as kRootIv
+// linear pieces over [-kRootSpan, kRootSpan] (the kink of its asymptotes min(0, -x) sits
+// on a node); outside that range the end pieces continue along the asymptotes.  The
+// interpolated start is within 3e-5 of the root, so a fixed number of Newton steps
+// reaches round-off (1 in float, 3 in double) and the solve has no data-dependent
+// branch.  Logarithms are base 2.
 
 template <typename T> struct TabNewton;
 template <> struct TabNewton<float> { static constexpr int value = 1; };
@@ -177,11 +210,12 @@ template <> struct TabNewton<double> { static constexpr int value = 3; };
 
 // Coefficients of the branch-free solve for one class of systems at one RK stage: the
 // slip systems (P = 1), or the twins at the stage's prefactor P.  With la = log2 a:
-// log2 zB = a1 la + b1 and log2 beta = a2 la + b2.  P <= 0 is solved as P = 1 (finite
+// log2 zB = a1 la + b1, and the table coordinate of x = log2 beta is
+// t = (x + kRootSpan) kRootPerUnit - 1/2 = a2 la + b2.  P <= 0 is solved as P = 1 (finite
 // dummy arithmetic) and the rate is scaled by Pout = 0.
 template <typename T>
 struct RootCoef {
-  T Pout, c, cn, Kn, a1, b1, a2, b2;
+  T Pout, c, cn, n, Kn, a1, b1, a2, b2;
 };
 
 template <typename T>
@@ -191,56 +225,63 @@ __device__ __forceinline__ RootCoef<T> root_coef(T P, T Kn, T n, T inv_n, T lg_K
   q.Pout = pos ? P : T(0);
   q.c = eta * (pos ? P : T(1));
   q.cn = n * q.c;
+  q.n = n;
   q.Kn = Kn;
   q.a1 = inv_n;
   q.b1 = -(lg_eta + (pos ? lg_P : T(0))) * inv_n;
-  q.a2 = inv_n - T(1);
-  q.b2 = lg_Kn + q.b1;
+  q.a2 = (inv_n - T(1)) * T(kRootPerUnit);
+  q.b2 = (lg_Kn + q.b1 + T(kRootSpan)) * T(kRootPerUnit) - T(0.5);
   return q;
 }
 
-// t = i + f with integer i = floor(t) and f in [0, 1], for 0 <= t < 2^22.  In float the
-// integer part comes from rounding t - 1/2 at the 1.5 * 2^23 binade (unit spacing), which
-// keeps the split on the FMA/ALU pipes.
-template <typename T> __device__ __forceinline__ int floor_split(T t, T& f);
-template <> __device__ __forceinline__ int floor_split<float>(float t, float& f) {
-  const float m = (t - 0.5f) + 12582912.0f;
-  f = t - (m - 12582912.0f);
-  return __float_as_int(m) - 0x4B400000;
+// Table interval of the coordinate t: floor(t + 1/2) clamped to [0, kRootIv - 1] (any t,
+// NaN included, gives an index inside the table).  In float the rounding happens at the
+// 1.5 * 2^23 binade, where the spacing is 1, keeping it off the conversion pipe.
+template <typename T> __device__ __forceinline__ int root_interval(T t);
+template <> __device__ __forceinline__ int root_interval<float>(float t) {
+  const float m = t + 12582912.0f;
+  const int i = __float_as_int(m) - 0x4B400000;
+  return min(max(i, 0), kRootIv - 1);
 }
-template <> __device__ __forceinline__ int floor_split<double>(double t, double& f) {
-  const int i = (int)t;
-  f = t - double(i);
-  return i;
+template <> __device__ __forceinline__ int root_interval<double>(double t) {
+  double u = t + 0.5;
+  u = u > 0.0 ? u : 0.0;
+  u = u < double(kRootIv - 1) ? u : double(kRootIv - 1);
+  return (int)u;
 }
+
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
 
 // Branch-free solve (eta > 0, integer exponent): inactive systems run the same arithmetic
 // on a dummy positive argument and return 0, so all systems of a stage form one basic
-// block the compiler can interleave.  tab: kRootTab deviations for this exponent.
+// block the compiler can interleave.  tab: kRootIv (a_i, b_i) pairs for this exponent.
+// The last Newton step is folded into the power: with dz = -phi/phi',
+// rho = P (z + dz)^n = P (z^n + n z^(n-1) dz) + O(dz^2), |dz/z| < 3e-5 from the table
+// start (the dropped term, n(n-1)/2 (dz/z)^2 < 4e-8 for n = 10, is below float
+// round-off; in double two full steps come first).
 template <typename T, int NP>
 __device__ __forceinline__ T reg_rate_tab(T a, const RootCoef<T>& q, int n_int, const T* tab) {
-  constexpr T S = T((kRootTab - 1) / (2.0 * kRootSpan));  // table nodes per unit of log2 beta
   const bool on = a > T(0);
   const T aa = on ? a : T(1);
   const T la = fast_log2<T>(aa);
   const T lzB = la * q.a1 + q.b1;
-  const T lb = la * q.a2 + q.b2;
-  T t = lb * S + T(kRootSpan) * S;
-  t = t > T(0) ? t : T(0);
-  t = t < T(kRootTab - 1) - T(1.0 / 1024) ? t : T(kRootTab - 1) - T(1.0 / 1024);  // i <= kRootTab - 2
-  T f;
-  const int i = floor_split<T>(t, f);
-  const T d = tab[i] + f * (tab[i + 1] - tab[i]);
-  T z = fast_exp2<T>(lzB + d - (lb > T(0) ? lb : T(0)));
+  const T t = la * q.a2 + q.b2;
+  const auto ab = reinterpret_cast<const typename Vec2<T>::type*>(tab)[root_interval<T>(t)];
+  T z = fast_exp2<T>(lzB + (ab.x + ab.y * t));
 #pragma unroll
-  for (int it = 0; it < TabNewton<T>::value; ++it) {
+  for (int it = 0; it + 1 < TabNewton<T>::value; ++it) {
     const T zn1 = zpow<T, (NP > 0 ? NP - 1 : 0)>(z, n_int - 1);
-    const T czn1 = q.c * zn1;
-    const T phi = czn1 * z + (q.Kn * z - aa);
+    const T phi = (q.c * zn1) * z + (q.Kn * z - aa);
     z = z - fast_div<T>(phi, q.cn * zn1 + q.Kn);
   }
-  z = z > T(0) ? z : T(0);
-  return on ? q.Pout * zpow<T, NP>(z, n_int) : T(0);
+  const T zn1 = zpow<T, (NP > 0 ? NP - 1 : 0)>(z, n_int - 1);
+  const T phi = (q.c * zn1) * z + (q.Kn * z - aa);
+  const T r = fast_rcp<T>(q.cn * zn1 + q.Kn);
+  const T nn = NP > 0 ? T(NP) : q.n;
+  const T rho = zn1 * z - nn * ((zn1 * phi) * r);
+  return on ? q.Pout * rho : T(0);
 }
 
 // Generic solve (any eta >= 0 and exponent n >= 1): per-system branch, a smooth-minimum
@@ -279,7 +320,7 @@ template <typename T, int NP>
 __device__ __forceinline__ T stage_rate(const MatDev<T>& M, const RootCoef<T>& q, T a, T P, bool twin, T lg_P,
                                         const T* tab) {
   if constexpr (NP != 0) {
-    return twin ? reg_rate_tab<T, NP>(a, q, M.nt_int, tab + kRootTab) : reg_rate_tab<T, NP>(a, q, M.n_int, tab);
+    return twin ? reg_rate_tab<T, NP>(a, q, M.nt_int, tab + M.tab_twin) : reg_rate_tab<T, NP>(a, q, M.n_int, tab);
   } else {
     return twin ? reg_rate<T>(a, P, M.Kt, M.nt, M.nt_int, M.inv_nt, M.smt, M.lg_Kt, M.eta, M.lg_eta, lg_P)
                 : reg_rate<T>(a, P, M.K, M.n, M.n_int, M.inv_n, M.sm, M.lg_K, M.eta, M.lg_eta, lg_P);
@@ -288,31 +329,37 @@ __device__ __forceinline__ T stage_rate(const MatDev<T>& M, const RootCoef<T>& q
 
 // Evaluates the rates at elastic strain e0 + s*de - yt.ep and state yt, adds
 // wacc * rates to acc and overwrites yt with y0 + cnext * rates.
-// tab: 2*kRootTab deviations (slip exponent n, then twin exponent nt), NP != 0 only.
+// tab: the rate-root tables (slip exponent at 0, twin exponent at M.tab_twin), NP != 0 only.
 // Each system is resolved, solved and folded into acc / yt before the next one (yt.v and
-// yt.al of system k are read before they are overwritten; the hardening terms g use the
+// yt.al of system k are read before they are overwritten; the hardening terms use the
 // stage's yt.v, computed first).  With NP != 0 the solves are branch-free, so the whole
 // stage is one basic block the compiler interleaves; this order keeps fewer values live
-// than solving all 16 systems first (7 % faster x pass on the 128^3 workload).
+// than solving all 16 systems first.
+// Rewritten forms (same quantities): with e_k = exp(-b v_k) = 1 - g_k,
+//   r_k = r0_k + Q (h_off sum g + (h_diag - h_off) g_k) = (r0_k + Q (h_off (N - sum e) + dq)) - Q dq e_k;
+// the slip stresses share the Schmid scale 1/sqrt6 (applied once to sigma), and the
+// plastic strain rate is summed with integer Schmid coefficients, scaled once at the end.
 template <typename T, int NP>
 __device__ __forceinline__ void rk_stage(const MatDev<T>& M, const T* e0, const T* de, T s,
                                          const MPState<T>& y0, MPState<T>& yt, MPState<T>& acc, T wacc,
                                          T cnext, const T* tab) {
+  constexpr double kLog2e = 1.44269504088896340736;
   T e[6], sg[6];
 #pragma unroll
   for (int c = 0; c < 6; ++c) e[c] = e0[c] + s * de[c] - yt.ep[c];
   hooke<T>(M, e, sg);
-  T g[16];
-  T Sslip = T(0), Stw = T(0), vtw = T(0);
+  T ex[16];
+  T Es = T(0), Et = T(0), vtw = T(0);
+  const T cb_s = -M.b_s * T(kLog2e), cb_t = -M.b_b * T(kLog2e);
 #pragma unroll
   for (int k = 0; k < 12; ++k) {
-    g[k] = T(1) - fast_exp<T>(-M.b_s * yt.v[k]);
-    Sslip += g[k];
+    ex[k] = fast_exp2<T>(cb_s * yt.v[k]);
+    Es += ex[k];
   }
 #pragma unroll
   for (int k = 12; k < 16; ++k) {
-    g[k] = T(1) - fast_exp<T>(-M.b_b * yt.v[k]);
-    Stw += g[k];
+    ex[k] = fast_exp2<T>(cb_t * yt.v[k]);
+    Et += ex[k];
     vtw += yt.v[k];
   }
   const T ftot = T(1.41421356237309504880) * vtw;
@@ -322,19 +369,26 @@ __device__ __forceinline__ void rk_stage(const MatDev<T>& M, const T* e0, const 
   const T Ptw = (M.Kc * T(0.70710678118654752440)) * fm_left;
   const T lg_Ptw = fast_log2<T>(Ptw > T(0) ? Ptw : T(1));
   const T dq = M.h_diag - M.h_off;
+  const T Qdq_s = M.Q_s * dq, Qdq_t = M.Q_b * dq;
+  const T Rb_s = M.Q_s * (M.h_off * (T(12) - Es) + dq);
+  const T Rb_t = M.Q_b * (M.h_off * (T(4) - Et) + dq);
   RootCoef<T> qs, qt;
   if constexpr (NP != 0) {
     qs = root_coef<T>(T(1), M.K, M.n, M.inv_n, M.lg_K, M.eta, M.lg_eta, T(0));
     qt = root_coef<T>(Ptw, M.Kt, M.nt, M.inv_nt, M.lg_Kt, M.eta, M.lg_eta, lg_Ptw);
   }
-  T dep[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+  T ss[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) ss[c] = sg[c] * sys_scale<T>(0);
+  T du_s[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+  T du_t[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
 #pragma unroll
   for (int k = 0; k < 12; ++k) {
-    const T tek = resolved<T>(k, sg) - M.c * yt.al[k];
-    const T ak = fabs(tek) - (M.r0[k] + M.Q_s * (M.h_off * Sslip + dq * g[k]));
+    const T tek = schmid_sum<T>(k, ss) - M.c * yt.al[k];
+    const T ak = fabs(tek) - ((M.r0[k] + Rb_s) - Qdq_s * ex[k]);
     const T rk = stage_rate<T, NP>(M, qs, ak, T(1), false, T(0), tab);
     const T gd = tek < T(0) ? -rk : rk;
-    add_schmid<T>(k, gd * wslip, dep);
+    schmid_add<T>(k, gd, du_s);
     const T ald = gd - M.d * rk * yt.al[k];
     acc.v[k] += wacc * rk;
     yt.v[k] = y0.v[k] + cnext * rk;
@@ -343,16 +397,21 @@ __device__ __forceinline__ void rk_stage(const MatDev<T>& M, const T* e0, const 
   }
 #pragma unroll
   for (int k = 12; k < 16; ++k) {
-    const T ak = resolved<T>(k, sg) - (M.r0[k] + M.Q_b * (M.h_off * Stw + dq * g[k]));
+    const T ak = sys_scale<T>(k) * schmid_sum<T>(k, sg) - ((M.r0[k] + Rb_t) - Qdq_t * ex[k]);
     const T rk = stage_rate<T, NP>(M, qt, ak, Ptw, true, lg_Ptw, tab);
-    add_schmid<T>(k, rk, dep);
+    schmid_add<T>(k, rk, du_t);
     acc.v[k] += wacc * rk;
     yt.v[k] = y0.v[k] + cnext * rk;
   }
+  // eps_p rate = (1 - sum f) sum_s gdot_s m_s + sum_b gdot_b m_b, m = scale sym(n x l)
+  const T fs = wslip * sys_scale<T>(0);
+  const T fsh = T(0.5) * fs;
 #pragma unroll
   for (int c = 0; c < 6; ++c) {
-    acc.ep[c] += wacc * dep[c];
-    yt.ep[c] = y0.ep[c] + cnext * dep[c];
+    const T dep = c < 3 ? fs * du_s[c] + sys_scale<T>(12) * du_t[c]
+                        : fsh * du_s[c] + (T(0.5) * sys_scale<T>(12)) * du_t[c];
+    acc.ep[c] += wacc * dep;
+    yt.ep[c] = y0.ep[c] + cnext * dep;
   }
 }
 

@@ -53,6 +53,7 @@ struct MatDev {
   T sm, smt;          // smooth-min exponents: 1 / log2(1/u1), u1^n + u1 = 1
   T lg_K, lg_Kt;      // log2 K, log2 Kt
   T lg_eta;           // log2 eta (eta > 0)
+  int tab_twin;       // offset of the twin exponent's root table: 0 when nt = n, else kRootTabLen
 };
 
 // Mixed-load controller data (always double).
@@ -87,9 +88,13 @@ struct ConvDev {
 
 constexpr int kNumRed = 9;  // reduction slots per CTA
 
-// Regularised-rate root table (constitutive.cuh): kRootTab nodes of log2(beta) over
-// [-kRootSpan, kRootSpan], one node at 0.
-constexpr int kRootTab = 2049;
+// Regularised-rate root table (constitutive.cuh, reg_rate_tab): log2 u*(beta) as kRootIv
+// linear pieces over log2 beta in [-kRootSpan, kRootSpan] (nodes every 1/kRootPerUnit,
+// one at 0).  Interval i holds (a_i, b_i) with log2 u* = a_i + b_i t on it, in the
+// absolute coordinate t = (log2 beta + kRootSpan) kRootPerUnit - 1/2.
+constexpr int kRootIv = 2048;
 constexpr double kRootSpan = 16.0;
+constexpr double kRootPerUnit = kRootIv / (2.0 * kRootSpan);
+constexpr int kRootTabLen = 2 * kRootIv;  // values per exponent
 
 }  // namespace rve

@@ -203,7 +203,7 @@ struct rve_s {
   void *ep = nullptr, *v = nullptr, *al = nullptr, *eps_n = nullptr, *sig_n = nullptr;
   uint32_t* grain = nullptr;
   void* Rg = nullptr;
-  void* root_tab = nullptr;  // 2 * kRootTab rate-root deviations (slip n, twin nt)
+  void* root_tab = nullptr;  // kRootTabs rate-root table values (slip systems, twin exponent)
   void *tw_x = nullptr, *tw_y = nullptr, *tw_z = nullptr;
   void *kx = nullptr, *ky = nullptr, *kz = nullptr;
   double* partial = nullptr;
@@ -322,13 +322,11 @@ void release(rve_s* h) {
   h->st_host = nullptr;
 }
 
-// Rate-root tables: one when the twin exponent equals the slip exponent, else two (slip,
-// twin).  The x pass stages them in shared memory after its FFT buffers.
-int root_tab_len(const rve_material& m) { return m.nt == m.n ? kRootTabLen : 2 * kRootTabLen; }
-
+// The x pass stages the two rate-root tables (kRootTabs values) in shared memory after
+// its FFT buffers.
 size_t xsmem_total(const rve_s* h) {
   const size_t elem = h->opt.precision == RVE_FP64 ? sizeof(double) : sizeof(float);
-  return h->xsmem + (size_t)root_tab_len(h->mat) * elem;
+  return h->xsmem + (size_t)kRootTabs * elem;
 }
 
 template <typename T>
@@ -354,7 +352,6 @@ MatDev<T> make_mat(const rve_s* h) {
   M.lg_K = (T)std::log2(m.K);
   M.lg_Kt = (T)std::log2(m.Kt);
   M.lg_eta = (T)(m.eta > 0 ? std::log2(m.eta) : 0.0);
-  M.tab_twin = m.nt == m.n ? 0 : kRootTabLen;
   return M;
 }
 
@@ -520,12 +517,23 @@ void root_table(double n, double* out) {
   }
 }
 
+// The two tables of a material: the slip systems' lines in log2 a (P = 1, so the
+// coefficients of constitutive.cuh root_coef are constants: alpha_i = b1 + a_i + b_i b2,
+// beta_i = a1 + b_i a2), then the twin exponent's lines in the table coordinate t.
 template <typename T>
 std::vector<T> root_tables(const rve_material& m) {
-  std::vector<double> d(2 * kRootTabLen);
+  std::vector<double> d(kRootTabs, 0.0);
   root_table(m.n, d.data());
+  if (m.eta > 0) {
+    const double a1 = 1.0 / m.n, b1 = -std::log2(m.eta) / m.n;
+    const double a2 = (a1 - 1.0) * kRootPerUnit, b2 = (std::log2(m.K) + b1 + kRootSpan) * kRootPerUnit - 0.5;
+    for (int i = 0; i < kRootIv; ++i) {
+      const double ai = d[2 * i], bi = d[2 * i + 1];
+      d[2 * i] = b1 + ai + bi * b2;
+      d[2 * i + 1] = a1 + bi * a2;
+    }
+  }
   root_table(m.nt, d.data() + kRootTabLen);
-  d.resize(root_tab_len(m));
   return std::vector<T>(d.begin(), d.end());
 }
 
@@ -533,7 +541,7 @@ template <typename T>
 rve_status upload_root_tab(rve_s* h) {
   const std::vector<T> t = root_tables<T>(h->mat);
   if (!h->root_tab) {
-    rve_status s = dalloc(h, &h->root_tab, (size_t)2 * kRootTabLen * sizeof(T));  // room for two tables
+    rve_status s = dalloc(h, &h->root_tab, (size_t)kRootTabs * sizeof(T));
     if (s) return s;
   }
   RVE_CUDA(h, cudaMemcpyAsync(h->root_tab, t.data(), t.size() * sizeof(T), cudaMemcpyHostToDevice, h->stream));

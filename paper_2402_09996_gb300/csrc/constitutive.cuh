@@ -215,7 +215,7 @@ template <> struct TabNewton<double> { static constexpr int value = 3; };
 // dummy arithmetic) and the rate is scaled by Pout = 0.
 template <typename T>
 struct RootCoef {
-  T Pout, c, cn, n, Kn, a1, b1, a2, b2;
+  T Pout, c, cn, Kn, Kn_n, a1, b1, a2, b2;
 };
 
 template <typename T>
@@ -225,8 +225,8 @@ __device__ __forceinline__ RootCoef<T> root_coef(T P, T Kn, T n, T inv_n, T lg_K
   q.Pout = pos ? P : T(0);
   q.c = eta * (pos ? P : T(1));
   q.cn = n * q.c;
-  q.n = n;
   q.Kn = Kn;
+  q.Kn_n = Kn * inv_n;
   q.a1 = inv_n;
   q.b1 = -(lg_eta + (pos ? lg_P : T(0))) * inv_n;
   q.a2 = (inv_n - T(1)) * T(kRootPerUnit);
@@ -254,13 +254,28 @@ template <typename T> struct Vec2;
 template <> struct Vec2<float> { using type = float2; };
 template <> struct Vec2<double> { using type = double2; };
 
+// Newton steps from z and the rate.  All but the last step are full; the last one is
+// folded into the power: with dz = -phi/phi', phi = z (c z^(n-1) + Kn) - a and
+// phi' = n (c z^(n-1) + Kn/n), rho = P (z + dz)^n = P z^(n-1) (z + n dz) + O(dz^2);
+// |dz/z| < 3e-5 from the table start, so the dropped term n(n-1)/2 (dz/z)^2 < 4e-8 (n = 10)
+// is below float round-off (in double two full steps come first).
+template <typename T, int NP>
+__device__ __forceinline__ T root_newton(T z, T aa, const RootCoef<T>& q, int n_int) {
+#pragma unroll
+  for (int it = 0; it + 1 < TabNewton<T>::value; ++it) {
+    const T zn1 = zpow<T, (NP > 0 ? NP - 1 : 0)>(z, n_int - 1);
+    const T phi = (q.c * zn1) * z + (q.Kn * z - aa);
+    z = z - fast_div<T>(phi, q.cn * zn1 + q.Kn);
+  }
+  const T zn1 = zpow<T, (NP > 0 ? NP - 1 : 0)>(z, n_int - 1);
+  const T phi = z * (q.c * zn1 + q.Kn) - aa;
+  const T r = fast_rcp<T>(q.c * zn1 + q.Kn_n);  // = n / phi'
+  return q.Pout * (zn1 * (z - phi * r));
+}
+
 // Branch-free solve (eta > 0, integer exponent): inactive systems run the same arithmetic
 // on a dummy positive argument and return 0, so all systems of a stage form one basic
-// block the compiler can interleave.  tab: kRootIv (a_i, b_i) pairs for this exponent.
-// The last Newton step is folded into the power: with dz = -phi/phi',
-// rho = P (z + dz)^n = P (z^n + n z^(n-1) dz) + O(dz^2), |dz/z| < 3e-5 from the table
-// start (the dropped term, n(n-1)/2 (dz/z)^2 < 4e-8 for n = 10, is below float
-// round-off; in double two full steps come first).
+// block the compiler can interleave.  tab: kRootIv (a_i, b_i) pairs, log2 u* = a_i + b_i t.
 template <typename T, int NP>
 __device__ __forceinline__ T reg_rate_tab(T a, const RootCoef<T>& q, int n_int, const T* tab) {
   const bool on = a > T(0);
@@ -269,19 +284,24 @@ __device__ __forceinline__ T reg_rate_tab(T a, const RootCoef<T>& q, int n_int, 
   const T lzB = la * q.a1 + q.b1;
   const T t = la * q.a2 + q.b2;
   const auto ab = reinterpret_cast<const typename Vec2<T>::type*>(tab)[root_interval<T>(t)];
-  T z = fast_exp2<T>(lzB + (ab.x + ab.y * t));
-#pragma unroll
-  for (int it = 0; it + 1 < TabNewton<T>::value; ++it) {
-    const T zn1 = zpow<T, (NP > 0 ? NP - 1 : 0)>(z, n_int - 1);
-    const T phi = (q.c * zn1) * z + (q.Kn * z - aa);
-    z = z - fast_div<T>(phi, q.cn * zn1 + q.Kn);
-  }
-  const T zn1 = zpow<T, (NP > 0 ? NP - 1 : 0)>(z, n_int - 1);
-  const T phi = (q.c * zn1) * z + (q.Kn * z - aa);
-  const T r = fast_rcp<T>(q.cn * zn1 + q.Kn);
-  const T nn = NP > 0 ? T(NP) : q.n;
-  const T rho = zn1 * z - nn * ((zn1 * phi) * r);
-  return on ? q.Pout * rho : T(0);
+  const T z = fast_exp2<T>(lzB + (ab.x + ab.y * t));
+  const T rho = root_newton<T, NP>(z, aa, q, n_int);
+  return on ? rho : T(0);
+}
+
+// The same for the slip systems, whose coefficients do not depend on the stage (P = 1):
+// their table holds log2 z0 = alpha_i + beta_i la directly (alpha_i = b1 + a_i + b_i b2,
+// beta_i = a1 + b_i a2, built on the host for the material's K, n and eta).
+template <typename T, int NP>
+__device__ __forceinline__ T reg_rate_slip(T a, const RootCoef<T>& q, int n_int, const T* tab) {
+  const bool on = a > T(0);
+  const T aa = on ? a : T(1);
+  const T la = fast_log2<T>(aa);
+  const T t = la * q.a2 + q.b2;
+  const auto ab = reinterpret_cast<const typename Vec2<T>::type*>(tab)[root_interval<T>(t)];
+  const T z = fast_exp2<T>(ab.x + ab.y * la);
+  const T rho = root_newton<T, NP>(z, aa, q, n_int);
+  return on ? rho : T(0);
 }
 
 // Generic solve (any eta >= 0 and exponent n >= 1): per-system branch, a smooth-minimum
@@ -320,7 +340,7 @@ template <typename T, int NP>
 __device__ __forceinline__ T stage_rate(const MatDev<T>& M, const RootCoef<T>& q, T a, T P, bool twin, T lg_P,
                                         const T* tab) {
   if constexpr (NP != 0) {
-    return twin ? reg_rate_tab<T, NP>(a, q, M.nt_int, tab + M.tab_twin) : reg_rate_tab<T, NP>(a, q, M.n_int, tab);
+    return twin ? reg_rate_tab<T, NP>(a, q, M.nt_int, tab + kRootTabLen) : reg_rate_slip<T, NP>(a, q, M.n_int, tab);
   } else {
     return twin ? reg_rate<T>(a, P, M.Kt, M.nt, M.nt_int, M.inv_nt, M.smt, M.lg_Kt, M.eta, M.lg_eta, lg_P)
                 : reg_rate<T>(a, P, M.K, M.n, M.n_int, M.inv_n, M.sm, M.lg_K, M.eta, M.lg_eta, lg_P);
@@ -329,7 +349,7 @@ __device__ __forceinline__ T stage_rate(const MatDev<T>& M, const RootCoef<T>& q
 
 // Evaluates the rates at elastic strain e0 + s*de - yt.ep and state yt, adds
 // wacc * rates to acc and overwrites yt with y0 + cnext * rates.
-// tab: the rate-root tables (slip exponent at 0, twin exponent at M.tab_twin), NP != 0 only.
+// tab: the rate-root tables (slip systems' at 0, twin exponent's at kRootTabLen), NP != 0 only.
 // Each system is resolved, solved and folded into acc / yt before the next one (yt.v and
 // yt.al of system k are read before they are overwritten; the hardening terms use the
 // stage's yt.v, computed first).  With NP != 0 the solves are branch-free, so the whole
@@ -387,7 +407,7 @@ __device__ __forceinline__ void rk_stage(const MatDev<T>& M, const T* e0, const 
     const T tek = schmid_sum<T>(k, ss) - M.c * yt.al[k];
     const T ak = fabs(tek) - ((M.r0[k] + Rb_s) - Qdq_s * ex[k]);
     const T rk = stage_rate<T, NP>(M, qs, ak, T(1), false, T(0), tab);
-    const T gd = tek < T(0) ? -rk : rk;
+    const T gd = copysign(rk, tek);  // rk = 0 unless |tek| > r > 0
     schmid_add<T>(k, gd, du_s);
     const T ald = gd - M.d * rk * yt.al[k];
     acc.v[k] += wacc * rk;

@@ -36,7 +36,7 @@ cudaError_t launch_material_point_np(const MatDev<T>& M, long long nvox, const T
   if (nvox <= 0) return cudaSuccess;
   const int thr = 128;
   const long long grid = (nvox + thr - 1) / thr;
-  const size_t smem = (size_t)(kRootTabLen + M.tab_twin) * sizeof(T);
+  const size_t smem = (size_t)(kRootTabs) * sizeof(T);
   cudaError_t e = set_smem<T>((const void*)k_material_point<T, NP>, smem);
   if (e != cudaSuccess) return e;
   k_material_point<T, NP><<<(unsigned)grid, thr, smem, s>>>(M, nvox, R, eps_n, eps, state, sigma, dt, nsub,

@@ -53,7 +53,6 @@ struct MatDev {
   T sm, smt;          // smooth-min exponents: 1 / log2(1/u1), u1^n + u1 = 1
   T lg_K, lg_Kt;      // log2 K, log2 Kt
   T lg_eta;           // log2 eta (eta > 0)
-  int tab_twin;       // offset of the twin exponent's root table: 0 when nt = n, else kRootTabLen
 };
 
 // Mixed-load controller data (always double).
@@ -95,6 +94,7 @@ constexpr int kNumRed = 9;  // reduction slots per CTA
 constexpr int kRootIv = 2048;
 constexpr double kRootSpan = 16.0;
 constexpr double kRootPerUnit = kRootIv / (2.0 * kRootSpan);
-constexpr int kRootTabLen = 2 * kRootIv;  // values per exponent
+constexpr int kRootTabLen = 2 * kRootIv;  // values per table
+constexpr int kRootTabs = 2 * kRootTabLen;  // slip systems' table, then the twin exponent's
 
 }  // namespace rve

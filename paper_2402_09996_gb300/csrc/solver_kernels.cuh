@@ -96,7 +96,7 @@ struct XArgs {
   T* sig_n;
   const uint32_t* grain;
   const T* Rg;
-  const T* root_tab;  // rate-root tables: kRootTabLen + M.tab_twin values
+  const T* root_tab;  // rate-root tables: kRootTabs values
   MatDev<T> M;
   LoadDev ld;
   const int* done;  // iteration launches return at once when *done != 0 (NULL: always run)
@@ -109,20 +109,21 @@ struct XArgs {
 };
 
 constexpr int kXThreads = 128;
-// minimum resident x-pass CTAs per SM requested from the register allocator
-#ifndef RVE_X_MINB
-#define RVE_X_MINB 1
-#endif
+// Minimum resident x-pass CTAs per SM requested from the register allocator.  Float: 3
+// (at most 168 registers; the constitutive update is latency-bound at 2 CTAs, and 3 run
+// 8 % faster on the 128^3 workload despite a few spilled values).  Double: 1.
+template <typename T> struct XMinBlocks { static constexpr int value = 1; };
+template <> struct XMinBlocks<float> { static constexpr int value = 3; };
 
 template <typename T, bool COMMIT, int NP>
-__global__ void __launch_bounds__(kXThreads, RVE_X_MINB) k_xpass(const XArgs<T> a) {
+__global__ void __launch_bounds__(kXThreads, XMinBlocks<T>::value) k_xpass(const XArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[32][kNumRed];
   __shared__ int s_last;
   C2<T>* tw = reinterpret_cast<C2<T>*>(smem_raw);
   C2<T>* b0 = tw + a.nx;
   C2<T>* b1 = b0 + 3 * a.L * a.nx;
-  T* tab = reinterpret_cast<T*>(b1 + 3 * a.L * a.nx);  // kRootTabLen + M.tab_twin
+  T* tab = reinterpret_cast<T*>(b1 + 3 * a.L * a.nx);  // kRootTabs
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int nx = a.nx, H = a.H, half = nx / 2;
   const size_t NL = (size_t)a.ny * a.nz;
@@ -133,7 +134,7 @@ __global__ void __launch_bounds__(kXThreads, RVE_X_MINB) k_xpass(const XArgs<T> 
 
   for (int i = tid; i < nx; i += nthr) tw[i] = a.tw[i];
   if (NP != 0)
-    for (int i = tid; i < kRootTabLen + a.M.tab_twin; i += nthr) tab[i] = a.root_tab[i];
+    for (int i = tid; i < kRootTabs; i += nthr) tab[i] = a.root_tab[i];
   // pack component pairs (2p, 2p+1) of each line as one complex Hermitian-extended
   // sequence Z = A + iB, so one complex inverse FFT yields both real lines
   // (spectra are component-interleaved: entry (line, kx, c) at (line * H + kx) * 6 + c,
@@ -500,9 +501,9 @@ __global__ void k_material_point(const MatDev<T> M, long long nvox, const T* __r
                                  const T* __restrict__ eps_n, const T* __restrict__ eps, T* state,
                                  T* sigma, T dt, int nsub, const T* __restrict__ root_tab) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* tab = reinterpret_cast<T*>(smem_raw);  // kRootTabLen + M.tab_twin
+  T* tab = reinterpret_cast<T*>(smem_raw);  // kRootTabs
   if (NP != 0)
-    for (int k = threadIdx.x; k < kRootTabLen + M.tab_twin; k += blockDim.x) tab[k] = root_tab[k];
+    for (int k = threadIdx.x; k < kRootTabs; k += blockDim.x) tab[k] = root_tab[k];
   __syncthreads();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nvox) return;

@@ -399,6 +399,66 @@ def run_ensemble(args):
     print(json.dumps(line))
 
 
+def run_precision(args):
+    """Precision study on the twinned 256^3 RVE (1000 grains): the same --steps increments
+    in FP32 fields (FP64 norms) and in FP64 throughout, both on this GPU; reports the
+    relative difference of every effective result per increment and of the local fields
+    at the end, and the throughput of each precision.  (The FP64 GPU path itself matches
+    the FP64 oracle to 1e-9 on the 16^3 history and on sampled voxels; see tests/.)"""
+    import torch
+
+    from paper_2402_09996_gb300 import build_lib, inputs, rve
+
+    build_lib.build()
+    inp = inputs.workload_twinned_256()
+    gid = rve.label_voronoi(inp)
+    stream = torch.cuda.current_stream()
+    runs = {}
+    for name, prec in (("fp32", rve.FP32), ("fp64", rve.FP64)):
+        s = rve.RVE(gid, inp.euler, precision=prec, n_sub=0)
+        s.set_mixed_load(dt=0.5)
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        its = s.step(args.steps)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1)
+        runs[name] = {"hist": s.history(), "ms": ms, "iters": its, "nvox": s.nvox,
+                      "sig": s.field(rve.FIELD_STRESS), "v": s.field(rve.FIELD_V), "eps": s.field(rve.FIELD_STRAIN)}
+        s.close()
+    a, b = runs["fp32"], runs["fp64"]
+
+    def rel(x, y):
+        x, y = np.asarray(x, dtype=np.float64), np.asarray(y, dtype=np.float64)
+        return float(np.max(np.abs(x - y)) / max(float(np.max(np.abs(y))), 1e-300))
+
+    per_inc = []
+    for ha, hb in zip(a["hist"], b["hist"]):
+        per_inc.append({"increment": hb["increment"], "E33": hb["E"][2], "S33_fp64": hb["S"][2],
+                        "iterations": [ha["iterations"], hb["iterations"]],
+                        "S": rel(ha["S"], hb["S"]), "mean_S_eq": rel(ha["mean_S_eq"], hb["mean_S_eq"]),
+                        "S_eq_of_mean": rel(ha["S_eq_of_mean"], hb["S_eq_of_mean"]),
+                        "mean_f": rel(ha["mean_f"], hb["mean_f"]), "mean_v": rel(ha["mean_v"], hb["mean_v"])})
+    l2 = lambda x, y: float(np.linalg.norm(x - y) / np.linalg.norm(y))  # noqa: E731
+    nv = a["nvox"]
+    f32 = np.sqrt(2.0) * a["v"][12:]
+    f64 = np.sqrt(2.0) * b["v"][12:]
+    line = {
+        "metric": "relative difference FP32 fields vs FP64 (GPU)",
+        "workload": "twinned RVE 256^3, 1000 Voronoi grains (p_twin 0.5), uniaxial tension 1e-3/s, dt 0.5 s",
+        "increments": args.steps,
+        "per_increment": per_inc,
+        "local_final": {"sigma_L2": l2(a["sig"], b["sig"]), "sigma_max_abs_MPa": float(np.max(np.abs(a["sig"] - b["sig"]))),
+                        "strain_L2": l2(a["eps"], b["eps"]), "v_L2": l2(a["v"][:12], b["v"][:12]),
+                        "f_L2": l2(f32, f64) if np.any(f64) else 0.0},
+        "throughput": {"fp32": nv * a["iters"] / (a["ms"] * 1e-3), "fp64": nv * b["iters"] / (b["ms"] * 1e-3),
+                       "unit": METRIC},
+    }
+    print(json.dumps(line))
+
+
 def run_profile_case(args):
     """A small case for `ncu --profile-from-start off`: the kernels of --steps increments in
     the plastic regime, on inputs of a few hundred MB, after --warmup untimed increments."""
@@ -428,8 +488,9 @@ def main_args(argv=None):
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="twinned128", choices=["twinned128", "ensemble"],
-                    help="ensemble: the 16-RVE batched workload (prints its own JSON line)")
+    ap.add_argument("--workload", default="twinned128", choices=["twinned128", "ensemble", "precision256"],
+                    help="ensemble: the 16-RVE batched workload; precision256: FP32 vs FP64 on the 256^3 RVE "
+                         "over --steps increments (each prints its own JSON line)")
     ap.add_argument("--profile-case", type=int, default=0, metavar="N",
                     help="profiling case: an N^3 twinned RVE (60 grains, p=0.5, seed 11), "
                          "--warmup increments, then --steps increments between "
@@ -448,6 +509,8 @@ def main():
         run_profile_case(args)
     elif args.workload == "ensemble":
         run_ensemble(args)
+    elif args.workload == "precision256":
+        run_precision(args)
     else:
         run_gpu(args)
 

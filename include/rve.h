@@ -78,6 +78,12 @@ typedef struct {
   void* alloc_ctx;    /* passed back to alloc/free */
   int timing;         /* nonzero: record CUDA events around every kernel launch on the
                          handle's stream and accumulate per-kernel times (rve_kernel_times) */
+  int graphs;         /* nonzero (default): run each increment's fixed-point loop on the device
+                         as one CUDA graph launch (a conditional while-node repeats the
+                         iteration until the residual kernel decides; the commit follows in the
+                         same graph), so the host waits once per increment.  The graphs are
+                         built on first use per buffer rotation (three per handle) and rebuilt
+                         after rve_set_mixed_load.  Ignored when timing is set. */
 } rve_options;
 
 /* Kernel kinds reported by rve_kernel_times. */

@@ -237,6 +237,10 @@ struct rve_s {
   double inc_dE0[6] = {0, 0, 0, 0, 0, 0};
   double inc_E[6] = {0, 0, 0, 0, 0, 0};
   double inc_e = 0.0, inc_c = 0.0;
+  // device-side increment loops (opt.graphs): one executable graph per buffer rotation
+  cudaGraph_t graph[3] = {nullptr, nullptr, nullptr};
+  cudaGraphExec_t gexec[3] = {nullptr, nullptr, nullptr};
+  cudaStream_t cap[2] = {nullptr, nullptr};  // capture streams
 };
 
 namespace {
@@ -305,7 +309,21 @@ void tcollect(rve_s* h, int work_iters) {
     }
 }
 
+void drop_graphs(rve_s* h) {
+  for (int k = 0; k < 3; ++k) {
+    if (h->gexec[k]) cudaGraphExecDestroy(h->gexec[k]);
+    if (h->graph[k]) cudaGraphDestroy(h->graph[k]);
+    h->gexec[k] = nullptr;
+    h->graph[k] = nullptr;
+  }
+}
+
 void release(rve_s* h) {
+  drop_graphs(h);
+  for (int k = 0; k < 2; ++k) {
+    if (h->cap[k]) cudaStreamDestroy(h->cap[k]);
+    h->cap[k] = nullptr;
+  }
   if (h->ev_sync) cudaEventDestroy(h->ev_sync);
   h->ev_sync = nullptr;
   for (int k = 0; k < kTSlots; ++k) {
@@ -694,6 +712,39 @@ int max_iter_of(const rve_s* h) { return h->opt.max_iter > 0 ? h->opt.max_iter :
 
 int np_of(const rve_s* h) { return rate_variant(h->mat.eta, is_small_int(h->mat.n), is_small_int(h->mat.nt)); }
 
+// One fixed-point iteration (x pass, forward y, z + Green, inverse y) on stream s:
+// strain spectrum si -> so, tau_hat spectra pi -> po.  it < 0: the kernels take the
+// iteration index from the device (graph mode) and the residual kernel clears `cond`
+// once it decides.  `slot` >= 0 brackets the launches with timing events.
+template <typename T>
+rve_status enqueue_one(rve_s* h, cudaStream_t s, int it, int si, int so, int pi, int po,
+                       const cudaGraphConditionalHandle* cond, int slot) {
+  const int np = np_of(h);
+  const int zgrid_x = (h->H + h->zHC - 1) / h->zHC;
+  const int ygrid_x = (h->H + h->yHC - 1) / h->yHC;
+  const bool timed = slot >= 0;
+  XArgs<T> xa = x_args<T>(h, h->spec[si], h->spec[so], it);
+  if (timed) tstart(h, 4 * slot + 0, RVE_K_XPASS);
+  RVE_CUDA(h, launch_xpass<T>(xa, np, false, h->xgrid, xsmem_total(h), s));
+  if (timed) tstop(h, 4 * slot + 0);
+  LineArgs<T> ya = y_args<T>(h, h->spec[so]);
+  if (timed) tstart(h, 4 * slot + 1, RVE_K_YFWD);
+  RVE_CUDA(h, launch_line<T>(ya, -1, dim3(ygrid_x, h->nz), h->ysmem, s));
+  if (timed) tstop(h, 4 * slot + 1);
+  ZArgs<T> za = z_args<T>(h, h->spec[so], h->P[pi], h->P[po], it);
+  if (cond) {
+    za.has_cond = 1;
+    za.cond = *cond;
+  }
+  if (timed) tstart(h, 4 * slot + 2, RVE_K_ZGREEN);
+  RVE_CUDA(h, launch_zgreen<T>(za, dim3(zgrid_x, h->ny), h->zsmem, s));
+  if (timed) tstop(h, 4 * slot + 2);
+  if (timed) tstart(h, 4 * slot + 3, RVE_K_YINV);
+  RVE_CUDA(h, launch_line<T>(ya, +1, dim3(ygrid_x, h->nz), h->ysmem, s));
+  if (timed) tstop(h, 4 * slot + 3);
+  return RVE_OK;
+}
+
 // Enqueues iterations inc_it0 .. inc_it0 + inc_nb - 1, then the status copy and ev_sync.
 // The residual kernel decides convergence on the device; later launches of the batch
 // return at once.
@@ -701,47 +752,118 @@ template <typename T>
 rve_status enqueue_iterations(rve_s* h) {
   cudaStream_t s = h->stream;
   const Rotation r(h);
-  const int np = np_of(h);
-  const int zgrid_x = (h->H + h->zHC - 1) / h->zHC;
-  const int ygrid_x = (h->H + h->yHC - 1) / h->yHC;
   h->inc_nb = std::min(kBatch, max_iter_of(h) - h->inc_it0);
   for (int b = 0; b < h->inc_nb; ++b) {
     const int it = h->inc_it0 + b;
-    XArgs<T> xa = x_args<T>(h, h->spec[r.s_in(it)], h->spec[r.s_out(it)], it);
-    tstart(h, 4 * b + 0, RVE_K_XPASS);
-    RVE_CUDA(h, launch_xpass<T>(xa, np, false, h->xgrid, xsmem_total(h), s));
-    tstop(h, 4 * b + 0);
-    LineArgs<T> ya = y_args<T>(h, h->spec[r.s_out(it)]);
-    tstart(h, 4 * b + 1, RVE_K_YFWD);
-    RVE_CUDA(h, launch_line<T>(ya, -1, dim3(ygrid_x, h->nz), h->ysmem, s));
-    tstop(h, 4 * b + 1);
-    ZArgs<T> za = z_args<T>(h, h->spec[r.s_out(it)], h->P[r.p_in(it)], h->P[r.p_out(it)], it);
-    tstart(h, 4 * b + 2, RVE_K_ZGREEN);
-    RVE_CUDA(h, launch_zgreen<T>(za, dim3(zgrid_x, h->ny), h->zsmem, s));
-    tstop(h, 4 * b + 2);
-    tstart(h, 4 * b + 3, RVE_K_YINV);
-    RVE_CUDA(h, launch_line<T>(ya, +1, dim3(ygrid_x, h->nz), h->ysmem, s));
-    tstop(h, 4 * b + 3);
+    rve_status st = enqueue_one<T>(h, s, it, r.s_in(it), r.s_out(it), r.p_in(it), r.p_out(it), nullptr, b);
+    if (st) return st;
   }
   RVE_CUDA(h, cudaMemcpyAsync(h->st_host, h->st, sizeof(IterStatus), cudaMemcpyDeviceToHost, s));
   RVE_CUDA(h, cudaEventRecord(h->ev_sync, s));
   return RVE_OK;
 }
 
+bool use_graphs(const rve_s* h) { return h->opt.graphs && !h->opt.timing; }
+
+// Graph of one increment for the current buffer rotation (h->sb): iteration 0
+// (S0 -> S1), then a while-node whose body runs two iterations (S1 -> S2, S2 -> S1) and a
+// guard kernel, then the commit (a no-op unless the increment converged; it reads the
+// converged iteration's spectrum) and the status copy to the host.  The loop ends when the
+// residual kernel decides (converged, NaN, or the iteration cap) or, independently, after
+// max_iter / 2 + 2 body executions.
+template <typename T>
+rve_status build_graph(rve_s* h) {
+  const int key = h->sb;
+  const Rotation r(h);
+  for (int k = 0; k < 2; ++k)
+    if (!h->cap[k]) RVE_CUDA(h, cudaStreamCreateWithFlags(&h->cap[k], cudaStreamNonBlocking));
+  cudaStream_t cs = h->cap[0], cb = h->cap[1];
+  cudaGraph_t g = nullptr;
+  RVE_CUDA(h, cudaGraphCreate(&g, 0));
+  h->graph[key] = g;  // destroyed by drop_graphs
+  cudaGraphConditionalHandle cond;
+  RVE_CUDA(h, cudaGraphConditionalHandleCreate(&cond, g, 1u, cudaGraphCondAssignDefault));
+  RVE_CUDA(h, cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  rve_status st = RVE_OK;
+  cudaError_t e = cudaSuccess;
+  bool body_open = false;
+  do {
+    if ((st = enqueue_one<T>(h, cs, -1, r.s0, r.s1, r.p0, r.p1, &cond, -1))) break;
+    cudaStreamCaptureStatus cst;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    if ((e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, nullptr, &deps, nullptr, &nd)) != cudaSuccess) break;
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t wn;
+    if ((e = cudaGraphAddNode(&wn, g, deps, nullptr, nd, &cp)) != cudaSuccess) break;
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if ((e = cudaStreamUpdateCaptureDependencies(cs, &wn, nullptr, 1, cudaStreamSetCaptureDependencies)) != cudaSuccess)
+      break;
+    if ((e = cudaStreamBeginCaptureToGraph(cb, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed)) != cudaSuccess)
+      break;
+    body_open = true;
+    if ((st = enqueue_one<T>(h, cb, -1, r.s1, r.s2, r.p1, r.p2, &cond, -1))) break;
+    if ((st = enqueue_one<T>(h, cb, -1, r.s2, r.s1, r.p2, r.p1, &cond, -1))) break;
+    if ((e = launch_loop_guard<T>(h->st, max_iter_of(h) / 2 + 2, cond, cb)) != cudaSuccess) break;
+    cudaGraph_t bout = nullptr;
+    body_open = false;
+    if ((e = cudaStreamEndCapture(cb, &bout)) != cudaSuccess) break;
+    XArgs<T> ca = x_args<T>(h, h->spec[r.s0], nullptr, -1);
+    ca.pick = 1;
+    ca.cand[0] = (const C2<T>*)h->spec[r.s0];
+    ca.cand[1] = (const C2<T>*)h->spec[r.s1];
+    ca.cand[2] = (const C2<T>*)h->spec[r.s2];
+    if ((e = launch_xpass<T>(ca, np_of(h), true, h->xgrid, xsmem_total(h), cs)) != cudaSuccess) break;
+    if ((e = cudaMemcpyAsync(h->st_host, h->st, sizeof(IterStatus), cudaMemcpyDeviceToHost, cs)) != cudaSuccess) break;
+  } while (false);
+  if (body_open) {
+    cudaGraph_t tmp = nullptr;
+    cudaStreamEndCapture(cb, &tmp);
+  }
+  cudaGraph_t out = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(cs, &out);
+  if (st == RVE_OK && e != cudaSuccess) st = cuda_fail(h, e, "graph capture");
+  if (st == RVE_OK && e2 != cudaSuccess) st = cuda_fail(h, e2, "cudaStreamEndCapture");
+  if (st == RVE_OK) {
+    e = cudaGraphInstantiate(&h->gexec[key], g, 0);
+    if (e != cudaSuccess) st = cuda_fail(h, e, "cudaGraphInstantiate");
+  }
+  if (st != RVE_OK) {
+    cudaGetLastError();
+    drop_graphs(h);
+  }
+  return st;
+}
+
 // Starts increment n -> n+1: macroscopic step and initial guess (a1), then the first
-// batch of iterations.
+// batch of iterations (or the whole increment as one graph launch).
 template <typename T>
 rve_status inc_begin(rve_s* h) {
   cudaStream_t s = h->stream;
   initial_increment(h, h->inc_dE0);
-  // E^(0) into slot 0 of the device status record; clear the NaN flag and the decision
+  // E^(0) into slot 0 of the device status record; clear the NaN flag, the decision and
+  // the device-side iteration counters
   for (int c = 0; c < 6; ++c) h->st_host->E[0][c] = h->E_n[c] + h->inc_dE0[c];
   RVE_CUDA(h, cudaMemcpyAsync(h->st->E[0], h->st_host->E[0], 6 * sizeof(double), cudaMemcpyHostToDevice, s));
-  RVE_CUDA(h, cudaMemsetAsync(&h->st->nan_flag, 0, 3 * sizeof(int), s));
+  RVE_CUDA(h, cudaMemsetAsync(&h->st->nan_flag, 0, 5 * sizeof(int), s));
   const Rotation r(h);
   tstart(h, kSlotShift, RVE_K_SHIFT);
   RVE_CUDA(h, launch_shift<T>((C2<T>*)h->spec[r.s0], (C2<T>*)h->backup, h->NL, h->H, h->inc_dE0, false, s));
   tstop(h, kSlotShift);
+  if (use_graphs(h)) {
+    if (!h->gexec[h->sb]) {
+      rve_status st = build_graph<T>(h);
+      if (st) return st;
+    }
+    RVE_CUDA(h, cudaGraphLaunch(h->gexec[h->sb], s));
+    RVE_CUDA(h, cudaEventRecord(h->ev_sync, s));
+    h->inc_phase = 3;
+    return RVE_OK;
+  }
   h->inc_it0 = 0;
   h->inc_phase = 1;
   rve_status st = enqueue_iterations<T>(h);
@@ -749,77 +871,43 @@ rve_status inc_begin(rve_s* h) {
   return st;
 }
 
-// Resumes after ev_sync completed.  Sets *finished when the increment is committed (or
-// has failed and been rolled back; the status says which).
+// The increment's iterations are over (status in st_host): fetch the residual history and,
+// unless it converged, roll the start-of-increment shift back and report.
 template <typename T>
-rve_status inc_advance(rve_s* h, bool* finished, long long* iters) {
+rve_status close_iterations(rve_s* h, const IterStatus& stat) {
   cudaStream_t s = h->stream;
   const Rotation r(h);
-  *finished = false;
-  if (h->inc_phase == 1) {
-    const int done = h->st_host->done;
-    const int it0 = h->inc_it0, nb = h->inc_nb;
-    tcollect(h, done ? h->st_host->done_it - it0 + 1 : nb);
-    const int max_iter = max_iter_of(h);
-    if (!done && it0 + nb < max_iter) {
-      h->inc_it0 += nb;
-      rve_status st = enqueue_iterations<T>(h);
-      if (st) { h->inc_phase = 0; *finished = true; }
-      return st;
-    }
-    const IterStatus stat = *h->st_host;
-    const int last = stat.done ? stat.done_it : max_iter - 1;
-    {
-      std::vector<double> hh(2 * (size_t)(last + 1));
-      h->inc_phase = 0;
-      *finished = true;  // unless the commit below is enqueued
-      RVE_CUDA(h, cudaMemcpyAsync(hh.data(), h->dhist, hh.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
-      RVE_CUDA(h, cudaStreamSynchronize(s));
-      h->res_e.resize(last + 1);
-      h->res_c.resize(last + 1);
-      for (int i = 0; i <= last; ++i) {
-        h->res_e[i] = hh[2 * i];
-        h->res_c[i] = hh[2 * i + 1];
-      }
-    }
-    if (stat.done != 1) {
-      // roll back: undo the start-of-increment shift of the committed spectrum
-      RVE_CUDA(h, launch_shift<T>((C2<T>*)h->spec[r.s0], (C2<T>*)h->backup, h->NL, h->H, h->inc_dE0, true, s));
-      RVE_CUDA(h, cudaStreamSynchronize(s));
-      if (stat.done == 2)
-        return fail(h, RVE_ERR_NAN, std::string("NaN or Inf in the ") +
-                                        ((stat.nan_flag & 1) ? "mean stress" : "equilibrium residual") +
-                                        " at increment " + std::to_string(h->increment + 1) + ", iteration " +
-                                        std::to_string(last));
-      char buf[200];
-      std::snprintf(buf, sizeof(buf), "increment %d: no convergence in %d iterations (e=%.3e, cF=%.3e)",
-                    h->increment + 1, max_iter, stat.e_eq, stat.cF);
-      return fail(h, RVE_ERR_NOT_CONVERGED, buf);
-    }
-    // a8: commit the converged iterate
-    const int it = stat.done_it;
-    h->inc_last = it;
-    h->inc_e = stat.e_eq;
-    h->inc_c = stat.cF;
-    for (int c = 0; c < 6; ++c) h->inc_E[c] = stat.E[it & 1][c];
-    XArgs<T> ca = x_args<T>(h, h->spec[r.s_in(it)], nullptr, it);
-    tstart(h, kSlotCommit, RVE_K_COMMIT);
-    RVE_CUDA(h, launch_xpass<T>(ca, np_of(h), true, h->xgrid, xsmem_total(h), s));
-    tstop(h, kSlotCommit);
-    RVE_CUDA(h, cudaMemcpyAsync(h->st_host, h->st, sizeof(IterStatus), cudaMemcpyDeviceToHost, s));
-    RVE_CUDA(h, cudaEventRecord(h->ev_sync, s));
-    h->inc_phase = 2;
-    *finished = false;
-    return RVE_OK;
+  const int max_iter = max_iter_of(h);
+  const int last = stat.done ? stat.done_it : std::max(0, std::min(stat.it_dev, max_iter) - 1);
+  std::vector<double> hh(2 * (size_t)(last + 1));
+  RVE_CUDA(h, cudaMemcpyAsync(hh.data(), h->dhist, hh.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  RVE_CUDA(h, cudaStreamSynchronize(s));
+  h->res_e.resize(last + 1);
+  h->res_c.resize(last + 1);
+  for (int i = 0; i <= last; ++i) {
+    h->res_e[i] = hh[2 * i];
+    h->res_c[i] = hh[2 * i + 1];
   }
-  if (h->inc_phase != 2) {
-    *finished = true;
-    return fail(h, RVE_ERR_STATE, "no increment in progress");
-  }
-  // the commit completed: advance the host state
-  *finished = true;
-  h->inc_phase = 0;
-  tcollect(h, 0);
+  if (stat.done == 1) return RVE_OK;
+  RVE_CUDA(h, launch_shift<T>((C2<T>*)h->spec[r.s0], (C2<T>*)h->backup, h->NL, h->H, h->inc_dE0, true, s));
+  RVE_CUDA(h, cudaStreamSynchronize(s));
+  if (stat.done == 2)
+    return fail(h, RVE_ERR_NAN, std::string("NaN or Inf in the ") +
+                                    ((stat.nan_flag & 1) ? "mean stress" : "equilibrium residual") + " at increment " +
+                                    std::to_string(h->increment + 1) + ", iteration " + std::to_string(last));
+  if (stat.done == 0)
+    return fail(h, RVE_ERR_STATE, "increment " + std::to_string(h->increment + 1) +
+                                      ": the device loop ended without a decision");
+  char buf[200];
+  std::snprintf(buf, sizeof(buf), "increment %d: no convergence in %d iterations (e=%.3e, cF=%.3e)",
+                h->increment + 1, max_iter, stat.e_eq, stat.cF);
+  return fail(h, RVE_ERR_NOT_CONVERGED, buf);
+}
+
+// The commit completed (status in st_host): advance the host state and record the
+// increment's effective results.
+rve_status finish_increment(rve_s* h, long long* iters) {
+  const Rotation r(h);
   const int it = h->inc_last;
   h->sb = r.s_in(it);
   h->pb = r.p_in(it);
@@ -848,6 +936,64 @@ rve_status inc_advance(rve_s* h, bool* finished, long long* iters) {
   if (iters) *iters += it + 1;
   if (h->st_host->nan_flag) return fail(h, RVE_ERR_NAN, "NaN or Inf in the committed fields");
   return RVE_OK;
+}
+
+void note_converged(rve_s* h, const IterStatus& stat) {
+  const int it = stat.done_it;
+  h->inc_last = it;
+  h->inc_e = stat.e_eq;
+  h->inc_c = stat.cF;
+  for (int c = 0; c < 6; ++c) h->inc_E[c] = stat.E[it & 1][c];
+}
+
+// Resumes after ev_sync completed.  Sets *finished when the increment is committed (or
+// has failed and been rolled back; the status says which).
+template <typename T>
+rve_status inc_advance(rve_s* h, bool* finished, long long* iters) {
+  cudaStream_t s = h->stream;
+  const Rotation r(h);
+  *finished = true;
+  const int phase = h->inc_phase;
+  h->inc_phase = 0;
+  if (phase == 3) {  // the whole increment ran as one graph (the commit included)
+    const IterStatus stat = *h->st_host;
+    rve_status st = close_iterations<T>(h, stat);
+    if (st) return st;
+    note_converged(h, stat);
+    return finish_increment(h, iters);
+  }
+  if (phase == 1) {
+    const int done = h->st_host->done;
+    const int it0 = h->inc_it0, nb = h->inc_nb;
+    tcollect(h, done ? h->st_host->done_it - it0 + 1 : nb);
+    if (!done && it0 + nb < max_iter_of(h)) {
+      h->inc_it0 += nb;
+      h->inc_phase = 1;
+      *finished = false;
+      rve_status st = enqueue_iterations<T>(h);
+      if (st) { h->inc_phase = 0; *finished = true; }
+      return st;
+    }
+    const IterStatus stat = *h->st_host;
+    rve_status st = close_iterations<T>(h, stat);
+    if (st) return st;
+    // a8: commit the converged iterate
+    note_converged(h, stat);
+    const int it = stat.done_it;
+    XArgs<T> ca = x_args<T>(h, h->spec[r.s_in(it)], nullptr, it);
+    tstart(h, kSlotCommit, RVE_K_COMMIT);
+    RVE_CUDA(h, launch_xpass<T>(ca, np_of(h), true, h->xgrid, xsmem_total(h), s));
+    tstop(h, kSlotCommit);
+    RVE_CUDA(h, cudaMemcpyAsync(h->st_host, h->st, sizeof(IterStatus), cudaMemcpyDeviceToHost, s));
+    RVE_CUDA(h, cudaEventRecord(h->ev_sync, s));
+    h->inc_phase = 2;
+    *finished = false;
+    return RVE_OK;
+  }
+  if (phase != 2) return fail(h, RVE_ERR_STATE, "no increment in progress");
+  // the commit completed
+  tcollect(h, 0);
+  return finish_increment(h, iters);
 }
 
 rve_status inc_begin_any(rve_s* h) {
@@ -943,6 +1089,7 @@ void rve_options_default(rve_options* o) {
   o->max_iter = 1000;
   o->fixed_iters = 0;
   o->tol = 1e-6;
+  o->graphs = 1;
 }
 
 void rve_material_default(rve_material* m) {
@@ -1044,6 +1191,7 @@ rve_status rve_set_material(rve_t h, const rve_material* m) {
   if (s) return s;
   h->mat = *m;
   reference_medium(h->mat, &h->lam0, &h->mu0);
+  drop_graphs(h);  // the material is baked into the increment graphs
   return h->opt.precision == RVE_FP64 ? upload_root_tab<double>(h) : upload_root_tab<float>(h);
 }
 
@@ -1062,6 +1210,7 @@ rve_status rve_set_mixed_load(rve_t h, const double Edot[6], const uint8_t ctrl[
     h->Sigma[c] = Sigma[c];
   }
   h->dt = dt;
+  drop_graphs(h);  // the load and dt are baked into the increment graphs
   return RVE_OK;
 }
 

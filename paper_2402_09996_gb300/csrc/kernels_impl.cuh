@@ -114,6 +114,12 @@ cudaError_t launch_xfft(const XFftArgs<T>& a, int sign, dim3 grid, size_t smem, 
 }
 
 template <typename T>
+cudaError_t launch_loop_guard(IterStatus* st, int limit, cudaGraphConditionalHandle cond, cudaStream_t s) {
+  k_loop_guard<T><<<1, 32, 0, s>>>(st, limit, cond);
+  return cudaGetLastError();
+}
+
+template <typename T>
 __global__ void k_to_double(const T* __restrict__ src, double* __restrict__ dst, long long n) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) dst[i] = (double)src[i];
@@ -151,6 +157,7 @@ cudaError_t launch_von_mises(const T* sig6, double* dst, long long nvox, cudaStr
   template cudaError_t launch_shift<T>(C2<T>*, C2<T>*, long long, int, const double*, bool, cudaStream_t);        \
   template cudaError_t launch_xfft<T>(const XFftArgs<T>&, int, dim3, size_t, cudaStream_t);                       \
   template cudaError_t launch_to_double<T>(const T*, double*, long long, cudaStream_t);                           \
-  template cudaError_t launch_von_mises<T>(const T*, double*, long long, cudaStream_t);
+  template cudaError_t launch_von_mises<T>(const T*, double*, long long, cudaStream_t);                          \
+  template cudaError_t launch_loop_guard<T>(IterStatus*, int, cudaGraphConditionalHandle, cudaStream_t);
 
 }  // namespace rve

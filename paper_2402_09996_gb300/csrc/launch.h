@@ -49,6 +49,8 @@ template <typename T>
 cudaError_t launch_to_double(const T* src, double* dst, long long n, cudaStream_t s);
 template <typename T>
 cudaError_t launch_von_mises(const T* sig6, double* dst, long long nvox, cudaStream_t s);
+template <typename T>
+cudaError_t launch_loop_guard(IterStatus* st, int limit, cudaGraphConditionalHandle cond, cudaStream_t s);
 
 int x_threads();
 int line_threads();

@@ -74,6 +74,8 @@ struct IterStatus {
   int nan_flag;
   int done;             // 0 iterating; 1 converged; 2 NaN/Inf; 3 iteration cap reached
   int done_it;          // iteration at which `done` was set
+  int it_dev;           // device-driven iteration index (graph mode: advanced by the residual kernel)
+  int guard;            // executions of the graph loop body (graph mode)
   int pad;
 };
 

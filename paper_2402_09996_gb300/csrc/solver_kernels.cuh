@@ -105,7 +105,11 @@ struct XArgs {
   double* partial;
   unsigned int* counter;
   IterStatus* st;
-  int it;
+  int it;  // iteration index; < 0: read it from st->it_dev (graph mode)
+  // graph-mode commit: runs only if the increment converged, reading the strain spectrum
+  // of the converged iteration it* (cand[0] for it* = 0, cand[1] for odd, cand[2] for even)
+  int pick;
+  const C2<T>* cand[3];
 };
 
 constexpr int kXThreads = 128;
@@ -131,6 +135,13 @@ __global__ void __launch_bounds__(kXThreads, XMinBlocks<T>::value) k_xpass(const
   const int nl = min(a.L, (int)(NL - line0));
   if (a.done && *a.done) return;  // increment already decided: speculative launch
   const size_t nvox = (size_t)a.nvox;
+  const int it = a.it >= 0 ? a.it : a.st->it_dev;
+  const C2<T>* spec_in = a.spec_in;
+  if (COMMIT && a.pick) {
+    if (a.st->done != 1) return;  // not converged: the host rolls the increment back
+    const int k = a.st->done_it;
+    spec_in = k == 0 ? a.cand[0] : ((k & 1) ? a.cand[1] : a.cand[2]);
+  }
 
   for (int i = tid; i < nx; i += nthr) tw[i] = a.tw[i];
   if (NP != 0)
@@ -145,8 +156,8 @@ __global__ void __launch_bounds__(kXThreads, XMinBlocks<T>::value) k_xpass(const
     const int xi = r % H, l = r / H;
     const int q = p * nl + l;
     const size_t e0 = (((size_t)line0 + l) * H + xi) * 6 + 2 * p;
-    C2<T> A = a.spec_in[e0];
-    C2<T> B = a.spec_in[e0 + 1];
+    C2<T> A = spec_in[e0];
+    C2<T> B = spec_in[e0 + 1];
     if (xi == 0 || xi == half) {
       A.y = T(0);
       B.y = T(0);
@@ -261,8 +272,8 @@ __global__ void __launch_bounds__(kXThreads, XMinBlocks<T>::value) k_xpass(const
           ns += sm * sm;
         }
         st->cF = ld.any_free ? sqrt(nm) / sqrt(ns) : 0.0;
-        const double* Ec = st->E[a.it & 1];
-        double* En = st->E[(a.it + 1) & 1];
+        const double* Ec = st->E[it & 1];
+        double* En = st->E[(it + 1) & 1];
         for (int c = 0; c < 6; ++c) {
           double em = Ec[c] * mandel_w(c);
           if (ld.free_mask[c]) {
@@ -350,7 +361,9 @@ struct ZArgs {
   double* partial;
   unsigned int* counter;
   IterStatus* st;
-  int it;
+  int it;  // iteration index; < 0: read it from st->it_dev and advance it (graph mode)
+  int has_cond;  // graph mode: clear the loop condition once the increment is decided
+  cudaGraphConditionalHandle cond;
 };
 
 constexpr int kZThreads = 256;
@@ -382,7 +395,8 @@ __global__ void __launch_bounds__(kZThreads) k_zgreen(const ZArgs<T> a) {
   C2<T>* res = smem_fft<T, -1>(b0, b1, a.dz, 6 * hc, ps, tw, tid, nthr);
   C2<T>* oth = (res == b0) ? b1 : b0;
 
-  const double* En = a.st->E[(a.it + 1) & 1];
+  const int it = a.it >= 0 ? a.it : a.st->it_dev;
+  const double* En = a.st->E[(it + 1) & 1];
   const T coef = (a.lam0 + a.mu0) / (a.mu0 * (a.lam0 + T(2) * a.mu0));
   double rs = 0.0;
   for (int w = tid; w < hc * nz; w += nthr) {
@@ -480,18 +494,31 @@ __global__ void __launch_bounds__(kZThreads) k_zgreen(const ZArgs<T> a) {
       st->nan_flag |= !isfinite(v[0]) ? 2 : 0;
       // convergence decision (equilibrium and stress-constraint errors of iteration it)
       const ConvDev& cv = a.conv;
-      cv.hist[2 * a.it] = st->e_eq;
-      cv.hist[2 * a.it + 1] = st->cF;
+      cv.hist[2 * it] = st->e_eq;
+      cv.hist[2 * it + 1] = st->cF;
       int code = 0;
       if (st->nan_flag) code = 2;
-      else if (cv.fixed_iters > 0 ? a.it + 1 >= cv.fixed_iters : (st->e_eq < cv.tol && st->cF < cv.tol)) code = 1;
-      else if (a.it + 1 >= cv.max_iter) code = 3;
+      else if (cv.fixed_iters > 0 ? it + 1 >= cv.fixed_iters : (st->e_eq < cv.tol && st->cF < cv.tol)) code = 1;
+      else if (it + 1 >= cv.max_iter) code = 3;
       if (code) {
-        st->done_it = a.it;
+        st->done_it = it;
         st->done = code;
       }
+      if (a.it < 0) st->it_dev = it + 1;
+      if (code && a.has_cond) cudaGraphSetConditional(a.cond, 0u);
       *a.counter = 0u;
     }
+  }
+}
+
+// Graph mode: second bound on the device-side iteration loop, independent of the
+// residual kernel's decision: after `limit` executions of the loop body (two iterations
+// each) the loop condition is cleared.
+template <typename T>
+__global__ void k_loop_guard(IterStatus* st, int limit, cudaGraphConditionalHandle cond) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    const int g = ++st->guard;
+    if (g >= limit || st->done) cudaGraphSetConditional(cond, 0u);
   }
 }
 

@@ -169,3 +169,8 @@ def workload_ensemble():
             out.append(make_inputs((n, n, n), g, 0.5 if j < 2 else 0.0, seed=1000 * 3 + r))
             r += 1
     return out
+
+
+def workload_twinned_256():
+    """256^3 voxels, 1000 grains, each twinned with probability 0.5 (precision study)."""
+    return make_inputs((256, 256, 256), 1000, 0.5, seed=1000 * 2 + 0)

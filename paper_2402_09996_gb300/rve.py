@@ -52,6 +52,7 @@ class Options(C.Structure):
         ("free", FREE_FN),
         ("alloc_ctx", C.c_void_p),
         ("timing", C.c_int),
+        ("graphs", C.c_int),
     ]
 
 
@@ -231,7 +232,7 @@ class RVE:
     """
 
     def __init__(self, grain_id, euler, precision=FP64, green=GREEN_WILLOT, n_sub=0, tol=1e-6, max_iter=1000,
-                 fixed_iters=0, device=0, use_torch=True, timing=False):
+                 fixed_iters=0, device=0, use_torch=True, timing=False, graphs=True):
         self.lib = load_library()
         euler = np.ascontiguousarray(np.asarray(euler, dtype=np.float64))
         shape = tuple(grain_id.shape)
@@ -243,6 +244,7 @@ class RVE:
         opt.precision, opt.green, opt.n_sub = precision, green, n_sub
         opt.tol, opt.max_iter, opt.fixed_iters, opt.device = tol, max_iter, fixed_iters, device
         opt.timing = 1 if timing else 0
+        opt.graphs = 1 if graphs else 0
         self._allocator = None
         on_dev = 0
         if use_torch:

@@ -1,5 +1,6 @@
-"""Parity at the full benchmark size: the twinned 128^3 RVE (200 grains, p_twin 0.5) in
-FP32 fields with FP64 norms, the workload and launch configuration `bench.py` times.
+"""Parity at full sizes: the twinned 128^3 RVE (200 grains, p_twin 0.5) in FP32 fields
+with FP64 norms, the workload and launch configuration `bench.py` times, and the twinned
+256^3 RVE (1000 grains) of the precision study (sampled voxels and means).
 
 The oracle cannot run this grid, so the checks are the ones that hold at any size:
 * sampled voxels: the oracle's material-point update (Sec. 3 law, RK4 along the linear
@@ -114,3 +115,60 @@ def test_converged_fields_are_in_equilibrium_and_compatible(lib, cuda, solved):
     assert np.max(np.abs(np.delete(S, 2))) < 1e-5 * abs(S[2])
     # the state fields came back in the documented layouts
     assert tensor_to_six(six_to_tensor(eps6[:, :2, :2, :2])).shape == (6, 2, 2, 2)
+
+
+@pytest.fixture(scope="module")
+def solved256():
+    """The twinned 256^3 RVE (1000 grains) in FP32: fields stay on the device and only
+    sampled voxels and means come back."""
+    import torch
+
+    from paper_2402_09996_gb300 import inputs, rve
+
+    inp = inputs.workload_twinned_256()
+    gid = rve.label_voronoi(inp)
+    rng = np.random.default_rng(256)
+    flat = np.sort(rng.choice(gid.size, N_SAMPLE, replace=False))
+    idx = torch.as_tensor(flat, device="cuda")
+
+    def grab(s, which):
+        buf = torch.empty((rve.FIELD_COMPONENTS[which],) + s.shape, dtype=torch.float64, device="cuda")
+        s.field(which, out=buf)
+        f = buf.reshape(buf.shape[0], -1)
+        return f[:, idx].cpu().numpy(), f.mean(dim=1).cpu().numpy()
+
+    s = rve.RVE(gid, inp.euler, precision=rve.FP32)
+    s.set_mixed_load(dt=0.5)
+    s.step(WARM_INCREMENTS)
+    before = {k: grab(s, k)[0] for k in (rve.FIELD_STRAIN, rve.FIELD_EPS_P, rve.FIELD_V, rve.FIELD_ALPHA)}
+    s.step(1)
+    after = {k: grab(s, k) for k in (rve.FIELD_STRESS, rve.FIELD_STRAIN, rve.FIELD_EPS_P, rve.FIELD_V,
+                                      rve.FIELD_ALPHA)}
+    hist = s.history()
+    s.close()
+    return inp, gid.reshape(-1)[flat], before, after, hist
+
+
+def test_256_sampled_voxels_match_oracle_material_point(lib, cuda, solved256):
+    from paper_2402_09996_gb300 import rve
+
+    inp, gsample, before, after, hist = solved256
+    R = np.stack([orc.bunge_rotation(inp.euler[g]) for g in gsample]).astype(np.float32).astype(np.float64)
+    dt = 0.5
+    v = before[rve.FIELD_V].T
+    sig_ref, ep_ref, v_ref, al_ref = orc.material_point_increment(
+        orc.Material(), R, six_to_tensor(before[rve.FIELD_STRAIN]), six_to_tensor(after[rve.FIELD_STRAIN][0]),
+        six_to_tensor(before[rve.FIELD_EPS_P]), v, before[rve.FIELD_ALPHA].T, dt, orc.default_n_sub(dt))
+    sig = six_to_tensor(after[rve.FIELD_STRESS][0])
+    err = np.linalg.norm(sig - sig_ref, axis=(1, 2)) / np.linalg.norm(sig_ref, axis=(1, 2))
+    assert np.max(err) < 2e-4, np.max(err)
+    assert np.max(np.abs(six_to_tensor(after[rve.FIELD_EPS_P][0]) - ep_ref)) < 2e-4 * np.max(np.abs(ep_ref))
+    assert np.max(np.abs(after[rve.FIELD_V][0].T - v_ref)) < 2e-4 * np.max(np.abs(v_ref))
+    assert np.max(np.abs(after[rve.FIELD_ALPHA][0].T - al_ref)) < 2e-4 * np.max(np.abs(al_ref))
+    assert np.mean(np.any(v_ref > v, axis=1)) > 0.5
+    # means: strain = macroscopic strain, stress = reported effective stress, free stresses ~ 0
+    E, S = hist[-1]["E"], hist[-1]["S"]
+    assert hist[-1]["residual"] < 1e-6 and hist[-1]["stress_residual"] < 1e-6
+    assert np.max(np.abs(after[rve.FIELD_STRAIN][1] - E)) < 1e-6 * abs(E[2])
+    assert np.max(np.abs(after[rve.FIELD_STRESS][1] - S)) < 1e-5 * abs(S[2])
+    assert np.max(np.abs(np.delete(S, 2))) < 1e-5 * abs(S[2])

@@ -183,3 +183,33 @@ def test_invalid_arguments(lib, cuda):
             s.set_mixed_load(strain_ctrl=(0,) * 6)
         with pytest.raises(rve.RVEError):
             s.set_material(K=-1.0)
+
+
+@pytest.mark.parametrize("shape,prec,fixed", [((12, 10, 6), "fp64", 0), ((24, 20, 32), "fp32", 0),
+                                              ((16, 8, 8), "fp64", 5)])
+def test_graph_loop_equals_host_driven_loop(lib, cuda, shape, prec, fixed):
+    """The increment as one CUDA graph launch (device-side while loop, commit in the graph)
+    gives exactly the results of the host-driven iteration batches."""
+    from paper_2402_09996_gb300 import inputs, rve
+
+    inp = inputs.make_inputs(shape, 6, 0.5, seed=sum(shape) + fixed)
+    gid = label_rve(inp)
+    p = rve.FP64 if prec == "fp64" else rve.FP32
+    out = []
+    for graphs in (False, True):
+        with _rve(gid, inp.euler, precision=p, graphs=graphs, fixed_iters=fixed) as s:
+            s.set_mixed_load(dt=0.5)
+            res = []
+            for _ in range(3):
+                s.step(1)
+                res.append(s.residuals())
+            out.append((s.history(), res, s.field(rve.FIELD_STRESS), s.field(rve.FIELD_ALPHA)))
+    (h0, r0, s0, a0), (h1, r1, s1, a1) = out
+    for g, r in zip(h1, h0):
+        assert g["iterations"] == r["iterations"]
+        assert np.array_equal(g["S"], r["S"]) and np.array_equal(g["E"], r["E"])
+        for key in ("residual", "stress_residual", "mean_S_eq", "mean_v", "mean_f"):
+            assert g[key] == r[key]
+    for (e1, c1), (e0, c0) in zip(r1, r0):
+        assert np.array_equal(e1, e0) and np.array_equal(c1, c0)
+    assert np.array_equal(s1, s0) and np.array_equal(a1, a0)

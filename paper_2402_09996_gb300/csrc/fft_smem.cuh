@@ -61,6 +61,13 @@ __device__ __forceinline__ void small_dft(C2<T>* v) {
   }
 }
 
+// floor(x / d) for x, d < 2^16 with m = ceil(2^32 / d) (d >= 2): x m / 2^32 exceeds x / d
+// by less than x / 2^32 < 1/d, which cannot carry past the next integer.
+__device__ __forceinline__ unsigned div_small(unsigned x, unsigned d, unsigned m) {
+  return d == 1u ? x : __umulhi(x, m);
+}
+__device__ __forceinline__ unsigned recip_small(unsigned d) { return d > 1u ? 0xFFFFFFFFu / d + 1u : 0u; }
+
 template <typename T, int SIGN, int R>
 __device__ __forceinline__ void stockham_stage(const C2<T>* __restrict__ x, C2<T>* __restrict__ y,
                                                int n, int nseq, int stride, int Ns,
@@ -68,10 +75,14 @@ __device__ __forceinline__ void stockham_stage(const C2<T>* __restrict__ x, C2<T
   const int nb = n / R;        // butterflies per sequence
   const int tstride = n / (Ns * R);
   const int total = nseq * nb;
+  // the butterfly index splits by multiply-high reciprocals (exact below 2^16), else by division
+  const bool small = total < 65536;
+  const unsigned m_nb = recip_small((unsigned)nb), m_ns = recip_small((unsigned)Ns);
   for (int w = tid; w < total; w += nthr) {
-    const int q = w / nb;
+    const int q = small ? (int)div_small((unsigned)w, (unsigned)nb, m_nb) : w / nb;
     const int j = w - q * nb;
-    const int k = j % Ns;
+    const int jd = small ? (int)div_small((unsigned)j, (unsigned)Ns, m_ns) : j / Ns;
+    const int k = j - jd * Ns;
     const C2<T>* xs = x + q * stride;
     C2<T>* ys = y + q * stride;
     C2<T> v[R];
@@ -85,7 +96,7 @@ __device__ __forceinline__ void stockham_stage(const C2<T>* __restrict__ x, C2<T
       v[r] = a;
     }
     small_dft<T, SIGN, R>(v);
-    const int base = (j / Ns) * Ns * R + k;
+    const int base = jd * Ns * R + k;
 #pragma unroll
     for (int r = 0; r < R; ++r) ys[base + r * Ns] = v[r];
   }

@@ -308,6 +308,50 @@ struct LineArgs {
   long long stride, A, B;
 };
 
+// Moves a tile between global memory and shared-memory FFT sequences.  Global: n rows of
+// `row` contiguous complex values, row j at g + j * gstride.  Shared: value r of row j at
+// s[q(r) * ps + j], q(r) = (r % NC) * hc + r / NC (component-interleaved rows become one
+// sequence per component and kx).  Each thread keeps one column (or, in float with an even
+// row, a 16-byte pair of columns) and walks the rows, so the loop carries no divisions and
+// several loads are in flight.  Returns without a barrier.
+template <typename T, bool LOAD>
+__device__ __forceinline__ void tile_move(C2<T>* s, int ps, C2<T>* g, size_t gstride, int n, int row, int NC, int hc,
+                                          int tid, int nthr) {
+  constexpr bool kPairable = sizeof(C2<T>) == 8;
+  if (kPairable && (row % 2) == 0 && (reinterpret_cast<size_t>(g) % 16) == 0 && (gstride % 2) == 0) {
+    const int rp = row / 2;
+    const int R = nthr / rp;
+    if (tid >= R * rp) return;
+    const int r = 2 * (tid % rp), j0 = tid / rp;
+    C2<T>* s0 = s + (size_t)((r % NC) * hc + r / NC) * ps;
+    C2<T>* s1 = s + (size_t)(((r + 1) % NC) * hc + (r + 1) / NC) * ps;
+    float4* gv = reinterpret_cast<float4*>(g + r);
+    const size_t vstride = gstride / 2;
+#pragma unroll 4
+    for (int j = j0; j < n; j += R) {
+      if (LOAD) {
+        const float4 v = gv[(size_t)j * vstride];
+        s0[j] = mk<T>(T(v.x), T(v.y));
+        s1[j] = mk<T>(T(v.z), T(v.w));
+      } else {
+        const C2<T> a0 = s0[j], a1 = s1[j];
+        gv[(size_t)j * vstride] = make_float4(float(a0.x), float(a0.y), float(a1.x), float(a1.y));
+      }
+    }
+    return;
+  }
+  const int R = nthr / row;
+  if (tid >= R * row) return;
+  const int r = tid % row, j0 = tid / row;
+  C2<T>* sq = s + (size_t)((r % NC) * hc + r / NC) * ps;
+  C2<T>* gr = g + r;
+#pragma unroll 4
+  for (int j = j0; j < n; j += R) {
+    if (LOAD) sq[j] = gr[(size_t)j * gstride];
+    else gr[(size_t)j * gstride] = sq[j];
+  }
+}
+
 constexpr int kLineThreads = 256;
 
 template <typename T, int SIGN>
@@ -327,17 +371,25 @@ __global__ void __launch_bounds__(kLineThreads) k_line(const LineArgs<T> a) {
   const size_t base = (size_t)(o / a.n_o2) * a.A + (size_t)(o % a.n_o2) * a.B + (size_t)h0 * a.hstride;
   const int row = hc * NC;  // values per line position, contiguous when hstride == NC
   for (int i = tid; i < n; i += nthr) tw[i] = a.tw[i];
-  for (int w = tid; w < row * n; w += nthr) {
-    const int rc = w % row, j = w / row;
-    const int c = rc % NC, hh = rc / NC;
-    b0[(size_t)(c * hc + hh) * ps + j] = a.spec[base + (size_t)j * a.stride + (size_t)hh * a.hstride + c];
+  if (a.hstride == NC) {  // the row's values are contiguous
+    tile_move<T, true>(b0, ps, a.spec + base, (size_t)a.stride, n, row, NC, hc, tid, nthr);
+  } else {
+    for (int w = tid; w < row * n; w += nthr) {
+      const int rc = w % row, j = w / row;
+      const int c = rc % NC, hh = rc / NC;
+      b0[(size_t)(c * hc + hh) * ps + j] = a.spec[base + (size_t)j * a.stride + (size_t)hh * a.hstride + c];
+    }
   }
   __syncthreads();
   C2<T>* res = smem_fft<T, SIGN>(b0, b1, a.d, row, ps, tw, tid, nthr);
-  for (int w = tid; w < row * n; w += nthr) {
-    const int rc = w % row, j = w / row;
-    const int c = rc % NC, hh = rc / NC;
-    a.spec[base + (size_t)j * a.stride + (size_t)hh * a.hstride + c] = res[(size_t)(c * hc + hh) * ps + j];
+  if (a.hstride == NC) {
+    tile_move<T, false>(res, ps, a.spec + base, (size_t)a.stride, n, row, NC, hc, tid, nthr);
+  } else {
+    for (int w = tid; w < row * n; w += nthr) {
+      const int rc = w % row, j = w / row;
+      const int c = rc % NC, hh = rc / NC;
+      a.spec[base + (size_t)j * a.stride + (size_t)hh * a.hstride + c] = res[(size_t)(c * hc + hh) * ps + j];
+    }
   }
 }
 
@@ -386,11 +438,7 @@ __global__ void __launch_bounds__(kZThreads) k_zgreen(const ZArgs<T> a) {
   const size_t H = a.H, ny = a.ny;
   for (int i = tid; i < nz; i += nthr) tw[i] = a.tw[i];
   // component-interleaved spectra: for each kz the CTA's hc * 6 values are contiguous
-  for (int w = tid; w < 6 * hc * nz; w += nthr) {
-    const int rc = w % (6 * hc), kz = w / (6 * hc);
-    const int c = rc % 6, hh = rc / 6;
-    b0[(size_t)(c * hc + hh) * ps + kz] = a.spec[(((size_t)kz * ny + j) * H + h0 + hh) * 6 + c];
-  }
+  tile_move<T, true>(b0, ps, a.spec + ((size_t)j * H + h0) * 6, ny * H * 6, nz, 6 * hc, 6, hc, tid, nthr);
   __syncthreads();
   C2<T>* res = smem_fft<T, -1>(b0, b1, a.dz, 6 * hc, ps, tw, tid, nthr);
   C2<T>* oth = (res == b0) ? b1 : b0;
@@ -474,11 +522,7 @@ __global__ void __launch_bounds__(kZThreads) k_zgreen(const ZArgs<T> a) {
   }
   __syncthreads();
   C2<T>* out = smem_fft<T, +1>(res, oth, a.dz, 6 * hc, ps, tw, tid, nthr);
-  for (int w = tid; w < 6 * hc * nz; w += nthr) {
-    const int rc = w % (6 * hc), kz = w / (6 * hc);
-    const int c = rc % 6, hh = rc / 6;
-    a.spec[(((size_t)kz * ny + j) * H + h0 + hh) * 6 + c] = out[(size_t)(c * hc + hh) * ps + kz];
-  }
+  tile_move<T, false>(out, ps, a.spec + ((size_t)j * H + h0) * 6, ny * H * 6, nz, 6 * hc, 6, hc, tid, nthr);
   double v[kNumRed];
   v[0] = rs;
 #pragma unroll

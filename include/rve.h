@@ -84,6 +84,11 @@ typedef struct {
                          same graph), so the host waits once per increment.  The graphs are
                          built on first use per buffer rotation (three per handle) and rebuilt
                          after rve_set_mixed_load.  Ignored when timing is set. */
+  int autotune;       /* nonzero (default): before the first increment, time the y and z FFT
+                         passes for kx tile widths 1, 2, 4, 8, 16 on scratch buffers and keep the
+                         fastest (results do not depend on the widths) */
+  int y_tile, z_tile; /* > 0: force the kx tile width of the y (z) pass, overriding the
+                         autotuner and the default (at most 16; clamped to nx/2 + 1) */
 } rve_options;
 
 /* Kernel kinds reported by rve_kernel_times. */

@@ -241,6 +241,10 @@ struct rve_s {
   cudaGraph_t graph[3] = {nullptr, nullptr, nullptr};
   cudaGraphExec_t gexec[3] = {nullptr, nullptr, nullptr};
   cudaStream_t cap[2] = {nullptr, nullptr};  // capture streams
+  // FFT tile autotuner (opt.autotune): runs once, before the first increment
+  bool tuned = false;
+  IterStatus* st_tune = nullptr;  // scratch status and history for timing the z pass
+  double* hist_tune = nullptr;
 };
 
 namespace {
@@ -454,6 +458,17 @@ rve_status upload_tables(rve_s* h) {
   return RVE_OK;
 }
 
+// Dynamic shared memory of the y pass (twiddles + two buffers of HC*6 padded lines) and of
+// the z pass (the same + HC*nz residual terms).
+template <typename T>
+size_t y_smem(const rve_s* h, int hc) {
+  return (size_t)(h->ny + 12 * hc * (h->ny + 1)) * 2 * sizeof(T);
+}
+template <typename T>
+size_t z_smem(const rve_s* h, int hc) {
+  return (size_t)(h->nz + 12 * hc * (h->nz + 1)) * 2 * sizeof(T) + (size_t)hc * h->nz * sizeof(double);
+}
+
 template <typename T>
 rve_status alloc_fields(rve_s* h) {
   const size_t spec = (size_t)6 * h->NL * h->H * 2 * sizeof(T);
@@ -485,20 +500,20 @@ rve_status alloc_fields(rve_s* h) {
   }
   h->xgrid = (int)((h->NL + h->L - 1) / h->L);
   h->xsmem = (size_t)(h->nx + 6 * h->L * h->nx) * 2 * sizeof(T);  // FFT buffers; + tables: xsmem_total
-  const size_t budget = 96 * 1024;
   // y and z passes: tiles of HC kx values x 6 components (two buffers of padded lines);
-  // about 50 KB per CTA so that four CTAs share an SM
+  // default about 50 KB per CTA so that four CTAs share an SM (the autotuner may change it)
   const size_t tile_budget = 50 * 1024;
-  (void)budget;
   h->yHC = (int)std::max<size_t>(1, std::min<size_t>(16, tile_budget / (2 * 6 * 2 * sizeof(T) * (h->ny + 1))));
-  h->yHC = std::min(h->yHC, h->H);
-  h->ysmem = (size_t)(h->ny + 12 * h->yHC * (h->ny + 1)) * 2 * sizeof(T);
   h->zHC = (int)std::max<size_t>(1, std::min<size_t>(16, tile_budget / (2 * 6 * 2 * sizeof(T) * (h->nz + 1))));
+  if (h->opt.y_tile > 0) h->yHC = h->opt.y_tile;
+  if (h->opt.z_tile > 0) h->zHC = h->opt.z_tile;
+  h->yHC = std::min(h->yHC, h->H);
   h->zHC = std::min(h->zHC, h->H);
-  h->zsmem = (size_t)(h->nz + 12 * h->zHC * (h->nz + 1)) * 2 * sizeof(T);
-  const int zgrid = ((h->H + h->zHC - 1) / h->zHC) * h->ny;
-  const int maxgrid = std::max(h->xgrid, zgrid);
-  if ((s = dalloc(h, (void**)&h->partial, (size_t)maxgrid * kNumRed * sizeof(double)))) return s;
+  h->ysmem = y_smem<T>(h, h->yHC);
+  h->zsmem = z_smem<T>(h, h->zHC);
+  // x-pass partials per CTA; z-pass partials per (ky, kx) column
+  const size_t npart = std::max((size_t)h->xgrid * kNumRed, (size_t)h->ny * h->H);
+  if ((s = dalloc(h, (void**)&h->partial, npart * sizeof(double)))) return s;
   if ((s = dalloc(h, (void**)&h->counter, 64))) return s;
   RVE_CUDA(h, cudaMemsetAsync(h->counter, 0, 64, h->stream));
   if ((s = dalloc(h, (void**)&h->st, sizeof(IterStatus)))) return s;
@@ -506,6 +521,9 @@ rve_status alloc_fields(rve_s* h) {
   RVE_CUDA(h, cudaMallocHost((void**)&h->st_host, sizeof(IterStatus)));
   const int max_iter = h->opt.max_iter > 0 ? h->opt.max_iter : 1000;
   if ((s = dalloc(h, (void**)&h->dhist, (size_t)2 * max_iter * sizeof(double)))) return s;
+  if ((s = dalloc(h, (void**)&h->st_tune, sizeof(IterStatus)))) return s;
+  RVE_CUDA(h, cudaMemsetAsync(h->st_tune, 0, sizeof(IterStatus), h->stream));
+  if ((s = dalloc(h, (void**)&h->hist_tune, 2 * sizeof(double)))) return s;
   return RVE_OK;
 }
 
@@ -839,11 +857,109 @@ rve_status build_graph(rve_s* h) {
   return st;
 }
 
+// FFT tile autotuner: times the y and z passes for kx tile widths 1, 2, 4, 8, 16 on scratch
+// buffers (a non-committed strain spectrum, the non-committed tau_hat spectra, a scratch
+// status record) and keeps the fastest.  No result depends on the widths: every
+// sequence's FFT is the same arithmetic, and the residual is summed per (ky, kx) column.
+template <typename T>
+rve_status tune_tiles(rve_s* h) {
+  h->tuned = true;
+  const bool ty = h->opt.y_tile <= 0, tz = h->opt.z_tile <= 0;
+  if (!ty && !tz) return RVE_OK;
+  cudaStream_t s = h->stream;
+  int smax = 0;
+  RVE_CUDA(h, cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->opt.device));
+  void* sp = h->spec[(h->sb + 1) % 3];
+  void* pp = h->P[(h->pb + 1) % 3];
+  void* po = h->P[(h->pb + 2) % 3];
+  const size_t spec_bytes = (size_t)6 * h->NL * h->H * 2 * sizeof(T);
+  RVE_CUDA(h, cudaMemsetAsync(sp, 0, spec_bytes, s));
+  RVE_CUDA(h, cudaMemsetAsync(pp, 0, spec_bytes, s));
+  RVE_CUDA(h, cudaMemsetAsync(h->st_tune, 0, sizeof(IterStatus), s));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  RVE_CUDA(h, cudaEventCreate(&e0));
+  cudaError_t e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_fail(h, e, "cudaEventCreate");
+  }
+  // 1 warm-up launch, then 3 timed
+  auto timed = [&](auto launch, float* ms) -> cudaError_t {
+    cudaError_t r = launch();
+    if (r == cudaSuccess) r = cudaEventRecord(e0, s);
+    for (int k = 0; k < 3 && r == cudaSuccess; ++k) r = launch();
+    if (r == cudaSuccess) r = cudaEventRecord(e1, s);
+    if (r == cudaSuccess) r = cudaEventSynchronize(e1);
+    if (r == cudaSuccess) r = cudaEventElapsedTime(ms, e0, e1);
+    return r;
+  };
+  const int cands[5] = {1, 2, 4, 8, 16};
+  if (ty) {
+    float best = 1e30f;
+    int bhc = h->yHC;
+    for (int c : cands) {
+      if (c > h->H && c != cands[0] && std::min(c / 2, h->H) == h->H) continue;  // same as the previous width
+      const int hc = std::min(c, h->H);
+      const size_t sm = y_smem<T>(h, hc);
+      if (sm > (size_t)smax) continue;
+      LineArgs<T> ya = y_args<T>(h, sp);
+      ya.HC = hc;
+      ya.done = nullptr;
+      const dim3 grid((h->H + hc - 1) / hc, h->nz);
+      float ms = 0.f;
+      e = timed([&] { return launch_line<T>(ya, -1, grid, sm, s); }, &ms);
+      if (e != cudaSuccess) break;
+      if (ms < best) {
+        best = ms;
+        bhc = hc;
+      }
+    }
+    h->yHC = bhc;
+    h->ysmem = y_smem<T>(h, bhc);
+  }
+  if (e == cudaSuccess && tz) {
+    float best = 1e30f;
+    int bhc = h->zHC;
+    for (int c : cands) {
+      if (c > h->H && c != cands[0] && std::min(c / 2, h->H) == h->H) continue;
+      const int hc = std::min(c, h->H);
+      const size_t sm = z_smem<T>(h, hc);
+      if (sm > (size_t)smax) continue;
+      ZArgs<T> za = z_args<T>(h, sp, pp, po, 0);
+      za.HC = hc;
+      za.st = h->st_tune;
+      za.done = &h->st_tune->done;
+      za.conv.hist = h->hist_tune;
+      za.conv.fixed_iters = 1 << 30;  // never decides
+      za.conv.max_iter = 1 << 30;
+      za.has_cond = 0;
+      const dim3 grid((h->H + hc - 1) / hc, h->ny);
+      float ms = 0.f;
+      e = timed([&] { return launch_zgreen<T>(za, grid, sm, s); }, &ms);
+      if (e != cudaSuccess) break;
+      if (ms < best) {
+        best = ms;
+        bhc = hc;
+      }
+    }
+    h->zHC = bhc;
+    h->zsmem = z_smem<T>(h, bhc);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return cuda_fail(h, e, "tile autotuner");
+  return RVE_OK;
+}
+
 // Starts increment n -> n+1: macroscopic step and initial guess (a1), then the first
 // batch of iterations (or the whole increment as one graph launch).
 template <typename T>
 rve_status inc_begin(rve_s* h) {
   cudaStream_t s = h->stream;
+  if (h->opt.autotune && !h->tuned) {
+    rve_status st = tune_tiles<T>(h);
+    if (st) return st;
+  }
   initial_increment(h, h->inc_dE0);
   // E^(0) into slot 0 of the device status record; clear the NaN flag, the decision and
   // the device-side iteration counters
@@ -1090,6 +1206,9 @@ void rve_options_default(rve_options* o) {
   o->fixed_iters = 0;
   o->tol = 1e-6;
   o->graphs = 1;
+  o->autotune = 1;
+  o->y_tile = 0;
+  o->z_tile = 0;
 }
 
 void rve_material_default(rve_material* m) {
@@ -1114,6 +1233,8 @@ rve_status rve_create(rve_t* out, int nx, int ny, int nz, const uint32_t* grain_
   rve_options_default(&o);
   if (opt) o = *opt;
   if (o.precision != RVE_FP64 && o.precision != RVE_FP32) return fail(nullptr, RVE_ERR_INVALID_ARG, "bad precision");
+  if (o.y_tile < 0 || o.y_tile > 16 || o.z_tile < 0 || o.z_tile > 16)
+    return fail(nullptr, RVE_ERR_INVALID_ARG, "y_tile and z_tile must be in 0..16");
   if (o.green != RVE_GREEN_WILLOT && o.green != RVE_GREEN_MS) return fail(nullptr, RVE_ERR_INVALID_ARG, "bad green");
   if (o.n_sub < 0 || o.fixed_iters < 0 || o.max_iter < 0 || !(o.tol > 0)) return fail(nullptr, RVE_ERR_INVALID_ARG, "bad options");
   if ((o.alloc == nullptr) != (o.free == nullptr)) return fail(nullptr, RVE_ERR_INVALID_ARG, "alloc and free go together");

@@ -430,6 +430,7 @@ __global__ void __launch_bounds__(kZThreads) k_zgreen(const ZArgs<T> a) {
   const int ps = nz + 1;  // padded sequence stride
   C2<T>* b0 = tw + nz;
   C2<T>* b1 = b0 + (size_t)6 * a.HC * ps;
+  double* cres = reinterpret_cast<double*>(b1 + (size_t)6 * a.HC * ps);  // HC * nz residual terms
   const int tid = threadIdx.x, nthr = blockDim.x;
   if (a.done && *a.done) return;
   const int j = blockIdx.y;
@@ -446,7 +447,6 @@ __global__ void __launch_bounds__(kZThreads) k_zgreen(const ZArgs<T> a) {
   const int it = a.it >= 0 ? a.it : a.st->it_dev;
   const double* En = a.st->E[(it + 1) & 1];
   const T coef = (a.lam0 + a.mu0) / (a.mu0 * (a.lam0 + T(2) * a.mu0));
-  double rs = 0.0;
   for (int w = tid; w < hc * nz; w += nthr) {
     const int hh = w % hc, kz = w / hc;
     const int h = h0 + hh;
@@ -484,7 +484,7 @@ __global__ void __launch_bounds__(kZThreads) k_zgreen(const ZArgs<T> a) {
       const double r2x = (double)d[4].x * k0 + (double)d[3].x * k1 + (double)d[2].x * k2;
       const double r2y = (double)d[4].y * k0 + (double)d[3].y * k1 + (double)d[2].y * k2;
       const double wgt = (h == 0 || 2 * h == a.nx) ? 1.0 : 2.0;
-      rs += wgt * (r0x * r0x + r0y * r0y + r1x * r1x + r1y * r1y + r2x * r2x + r2y * r2y);
+      cres[hh * nz + kz] = wgt * (r0x * r0x + r0y * r0y + r1x * r1x + r1y * r1y + r2x * r2x + r2y * r2y);
     }
     const T kk = k0 * k0 + k1 * k1 + k2 * k2;
     C2<T> e[6];
@@ -523,12 +523,47 @@ __global__ void __launch_bounds__(kZThreads) k_zgreen(const ZArgs<T> a) {
   __syncthreads();
   C2<T>* out = smem_fft<T, +1>(res, oth, a.dz, 6 * hc, ps, tw, tid, nthr);
   tile_move<T, false>(out, ps, a.spec + ((size_t)j * H + h0) * 6, ny * H * 6, nz, 6 * hc, 6, hc, tid, nthr);
-  double v[kNumRed];
-  v[0] = rs;
+  // residual: one partial per (ky, kx) column, summed over kz in a fixed order (lane l
+  // takes kz = l, l + 32, ...; then a fixed shuffle tree), so the total does not depend on
+  // how many kx columns a CTA holds
+  {
+    const int lane = tid & 31, wid = tid >> 5, nw = nthr >> 5;
+    for (int hh = wid; hh < hc; hh += nw) {
+      double cv = 0.0;
+      for (int kz = lane; kz < nz; kz += 32) cv += cres[hh * nz + kz];
+      warp_sum<1>(&cv);
+      if (lane == 0) {
+        a.partial[(size_t)j * H + h0 + hh] = cv;
+        __threadfence();
+      }
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    const unsigned int prev = atomicAdd(a.counter, 1u);
+    s_last = (prev == block_count() - 1) ? 1 : 0;
+  }
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    double v[kNumRed];
 #pragma unroll
-  for (int i = 1; i < kNumRed; ++i) v[i] = 0.0;
-  if (publish_partial<1>(v, a.partial, a.counter, red, &s_last)) {
-    total_partials<1>(a.partial, v, red);
+    for (int i = 0; i < kNumRed; ++i) v[i] = 0.0;
+    {  // four independent accumulators keep the loads in flight; fixed order
+      const size_t np = ny * H;
+      double q0 = 0.0, q1 = 0.0, q2 = 0.0, q3 = 0.0;
+      size_t b = tid;
+      for (; b + 3 * (size_t)nthr < np; b += 4 * (size_t)nthr) {
+        q0 += __ldcg(&a.partial[b]);
+        q1 += __ldcg(&a.partial[b + nthr]);
+        q2 += __ldcg(&a.partial[b + 2 * (size_t)nthr]);
+        q3 += __ldcg(&a.partial[b + 3 * (size_t)nthr]);
+      }
+      for (; b < np; b += nthr) q0 += __ldcg(&a.partial[b]);
+      v[0] = (q0 + q1) + (q2 + q3);
+    }
+    block_sum<1>(v, red);
     if (tid == 0) {
       IterStatus* st = a.st;
       const double* S = st->sig_mean;

@@ -53,6 +53,9 @@ class Options(C.Structure):
         ("alloc_ctx", C.c_void_p),
         ("timing", C.c_int),
         ("graphs", C.c_int),
+        ("autotune", C.c_int),
+        ("y_tile", C.c_int),
+        ("z_tile", C.c_int),
     ]
 
 
@@ -232,7 +235,8 @@ class RVE:
     """
 
     def __init__(self, grain_id, euler, precision=FP64, green=GREEN_WILLOT, n_sub=0, tol=1e-6, max_iter=1000,
-                 fixed_iters=0, device=0, use_torch=True, timing=False, graphs=True):
+                 fixed_iters=0, device=0, use_torch=True, timing=False, graphs=True, autotune=True, y_tile=0,
+                 z_tile=0):
         self.lib = load_library()
         euler = np.ascontiguousarray(np.asarray(euler, dtype=np.float64))
         shape = tuple(grain_id.shape)
@@ -245,6 +249,8 @@ class RVE:
         opt.tol, opt.max_iter, opt.fixed_iters, opt.device = tol, max_iter, fixed_iters, device
         opt.timing = 1 if timing else 0
         opt.graphs = 1 if graphs else 0
+        opt.autotune = 1 if autotune else 0
+        opt.y_tile, opt.z_tile = int(y_tile), int(z_tile)
         self._allocator = None
         on_dev = 0
         if use_torch:

@@ -213,3 +213,28 @@ def test_graph_loop_equals_host_driven_loop(lib, cuda, shape, prec, fixed):
     for (e1, c1), (e0, c0) in zip(r1, r0):
         assert np.array_equal(e1, e0) and np.array_equal(c1, c0)
     assert np.array_equal(s1, s0) and np.array_equal(a1, a0)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_fft_tile_widths_do_not_change_results(lib, cuda, prec):
+    """The y / z pass kx tile widths (forced to 1 or 16, or chosen by the autotuner) leave
+    every result bit-identical: each sequence's FFT is the same arithmetic and the
+    residual is summed per (ky, kx) column in a fixed order."""
+    from paper_2402_09996_gb300 import inputs, rve
+
+    inp = inputs.make_inputs((20, 24, 32), 7, 0.5, seed=99)
+    gid = label_rve(inp)
+    p = rve.FP64 if prec == "fp64" else rve.FP32
+    out = []
+    for kw in ({"y_tile": 1, "z_tile": 1}, {"y_tile": 16, "z_tile": 16}, {"y_tile": 3, "z_tile": 5}, {}):
+        with _rve(gid, inp.euler, precision=p, **kw) as s:
+            s.set_mixed_load(dt=0.5)
+            s.step(3)
+            out.append((s.history(), s.residuals(), s.field(rve.FIELD_STRESS)))
+    h0, (e0, c0), s0 = out[0]
+    for h1, (e1, c1), s1 in out[1:]:
+        for g, r in zip(h1, h0):
+            assert g["iterations"] == r["iterations"]
+            assert np.array_equal(g["S"], r["S"]) and g["residual"] == r["residual"]
+        assert np.array_equal(e1, e0) and np.array_equal(c1, c0)
+        assert np.array_equal(s1, s0)

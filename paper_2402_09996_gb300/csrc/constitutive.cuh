@@ -18,7 +18,7 @@
 //
 // Template parameter NP selects how the regularised rates are solved:
 //   NP > 0   eta > 0 and n = nt = NP (compile-time power): table start, branch-free;
-//   NP = -1  eta > 0 and integer n, nt (run-time powers):   table start, branch-free;
+//   NP = -1  eta > 0, any real n, nt >= 1 (powers as 2^(p log2 z)): table start, branch-free;
 //   NP = 0   anything else (eta = 0 or non-integer exponents): generic per-system solve.
 #pragma once
 
@@ -215,7 +215,7 @@ template <> struct TabNewton<double> { static constexpr int value = 3; };
 // dummy arithmetic) and the rate is scaled by Pout = 0.
 template <typename T>
 struct RootCoef {
-  T Pout, c, cn, Kn, Kn_n, a1, b1, a2, b2;
+  T Pout, c, cn, Kn, Kn_n, a1, b1, a2, b2, nm1;
 };
 
 template <typename T>
@@ -231,7 +231,18 @@ __device__ __forceinline__ RootCoef<T> root_coef(T P, T Kn, T n, T inv_n, T lg_K
   q.b1 = -(lg_eta + (pos ? lg_P : T(0))) * inv_n;
   q.a2 = (inv_n - T(1)) * T(kRootPerUnit);
   q.b2 = (lg_Kn + q.b1 + T(kRootSpan)) * T(kRootPerUnit) - T(0.5);
+  q.nm1 = n - T(1);
   return q;
+}
+
+// z^(n-1) for the table-started Newton steps (z > 0): a compile-time product for NP > 0,
+// 2^((n-1) log2 z) for a real exponent (NP = -1; in float the hardware log2 / exp2, whose
+// relative error stays far below the 2e-4 the float path is held to).
+template <typename T, int NP>
+__device__ __forceinline__ T root_zn1(T z, const RootCoef<T>& q, int n_int) {
+  if constexpr (NP > 0) return cpow<NP - 1, T>(z);
+  else if constexpr (NP < 0) return fast_exp2<T>(q.nm1 * fast_log2<T>(z));
+  else return ipow_sel<T>(z, n_int - 1);
 }
 
 // Table interval of the coordinate t: floor(t + 1/2) clamped to [0, kRootIv - 1] (any t,
@@ -263,11 +274,11 @@ template <typename T, int NP>
 __device__ __forceinline__ T root_newton(T z, T aa, const RootCoef<T>& q, int n_int) {
 #pragma unroll
   for (int it = 0; it + 1 < TabNewton<T>::value; ++it) {
-    const T zn1 = zpow<T, (NP > 0 ? NP - 1 : 0)>(z, n_int - 1);
+    const T zn1 = root_zn1<T, NP>(z, q, n_int);
     const T phi = (q.c * zn1) * z + (q.Kn * z - aa);
     z = z - fast_div<T>(phi, q.cn * zn1 + q.Kn);
   }
-  const T zn1 = zpow<T, (NP > 0 ? NP - 1 : 0)>(z, n_int - 1);
+  const T zn1 = root_zn1<T, NP>(z, q, n_int);
   const T phi = z * (q.c * zn1 + q.Kn) - aa;
   const T r = fast_rcp<T>(q.c * zn1 + q.Kn_n);  // = n / phi'
   return q.Pout * (zn1 * (z - phi * r));

@@ -13,9 +13,11 @@ template <typename T> struct ZArgs;
 template <typename T> struct XFftArgs;
 
 // Rate-solve variants of the constitutive kernels (see constitutive.cuh): NP = 10 for
-// eta > 0 and n = nt = 10, NP = 0 for anything else.
+// eta > 0 and n = nt = 10, NP = -1 for eta > 0 and other exponents >= 1, NP = 0 (generic
+// per-system solve) for eta = 0.
 inline int rate_variant(double eta, int n_int, int nt_int) {
-  return (eta > 0.0 && n_int == 10 && nt_int == 10) ? 10 : 0;
+  if (!(eta > 0.0)) return 0;
+  return (n_int == 10 && nt_int == 10) ? 10 : -1;
 }
 
 // Per-variant entry points (each instantiated in its own translation unit).
@@ -27,13 +29,16 @@ cudaError_t launch_material_point_np(const MatDev<T>& M, long long nvox, const T
 
 template <typename T>
 cudaError_t launch_xpass(const XArgs<T>& a, int np, bool commit, int grid, size_t smem, cudaStream_t s) {
-  return np == 10 ? launch_xpass_np<T, 10>(a, commit, grid, smem, s) : launch_xpass_np<T, 0>(a, commit, grid, smem, s);
+  if (np == 10) return launch_xpass_np<T, 10>(a, commit, grid, smem, s);
+  if (np < 0) return launch_xpass_np<T, -1>(a, commit, grid, smem, s);
+  return launch_xpass_np<T, 0>(a, commit, grid, smem, s);
 }
 template <typename T>
 cudaError_t launch_material_point(const MatDev<T>& M, int np, long long nvox, const T* R, const T* eps_n, const T* eps,
                                   T* state, T* sigma, T dt, int nsub, const T* root_tab, cudaStream_t s) {
-  return np == 10 ? launch_material_point_np<T, 10>(M, nvox, R, eps_n, eps, state, sigma, dt, nsub, root_tab, s)
-                  : launch_material_point_np<T, 0>(M, nvox, R, eps_n, eps, state, sigma, dt, nsub, root_tab, s);
+  if (np == 10) return launch_material_point_np<T, 10>(M, nvox, R, eps_n, eps, state, sigma, dt, nsub, root_tab, s);
+  if (np < 0) return launch_material_point_np<T, -1>(M, nvox, R, eps_n, eps, state, sigma, dt, nsub, root_tab, s);
+  return launch_material_point_np<T, 0>(M, nvox, R, eps_n, eps, state, sigma, dt, nsub, root_tab, s);
 }
 
 template <typename T>

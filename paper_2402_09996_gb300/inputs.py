@@ -174,3 +174,205 @@ def workload_ensemble():
 def workload_twinned_256():
     """256^3 voxels, 1000 grains, each twinned with probability 0.5 (precision study)."""
     return make_inputs((256, 256, 256), 1000, 0.5, seed=1000 * 2 + 0)
+
+
+# ---------------------------------------------------------------------------------
+# The paper's own microstructure model (Sec. 2): Matern-hardcore Voronoi tessellation,
+# neighbouring twins and inclusion twins.  Geometry and random draws only.
+# ---------------------------------------------------------------------------------
+TWIN_MISORIENTATION_DEG = 69.79  # the misorientation angle printed in Sec. 2.2
+# habit planes of the tetragonal lattice read with c/a = 1, each with the in-plane axis the
+# twin rotation turns about: (011) with [100], (101) with [010]
+HABIT_NORMALS = np.array([[0.0, 1.0, 1.0], [1.0, 0.0, 1.0]]) / math.sqrt(2.0)
+HABIT_AXES = np.array([[1.0, 0.0, 0.0], [0.0, 1.0, 0.0]])
+
+
+def poisson(rng: SplitMix64, mean: float) -> int:
+    """Poisson draw as the number of unit-rate exponential arrivals before `mean`."""
+    t = 0.0
+    k = 0
+    while True:
+        t -= math.log(1.0 - rng.uniform())
+        if t > mean:
+            return k
+        k += 1
+
+
+def matern_hardcore_seeds(rng: SplitMix64, n_expected: float, r_hard: float) -> np.ndarray:
+    """Matern hard-core process of type II on the periodic unit cube (Sec. 2.1): a Poisson
+    process with marks, a point removed when another point within distance r_hard has a
+    smaller mark.  The parent intensity l_p solves (1 - exp(-l_p v)) / v = n_expected,
+    v = 4/3 pi r_hard^3, so the thinned pattern has n_expected points on average.
+    Returns (n, 3) points in [0, 1)^3; every periodic pairwise distance is >= r_hard."""
+    v = 4.0 / 3.0 * math.pi * r_hard ** 3
+    if n_expected * v >= 1.0:
+        raise ValueError("intensity too high for this hard-core radius")
+    lam_p = -math.log(1.0 - n_expected * v) / v if v > 0 else n_expected
+    n_p = poisson(rng, lam_p)
+    pts = rng.uniforms(3 * n_p).reshape(n_p, 3)
+    marks = rng.uniforms(n_p)
+    keep = np.ones(n_p, dtype=bool)
+    for i in range(n_p):
+        d = pts - pts[i]
+        d -= np.round(d)
+        close = np.einsum("ij,ij->i", d, d) < r_hard * r_hard
+        close[i] = False
+        if np.any(marks[close] < marks[i]):
+            keep[i] = False
+    return pts[keep]
+
+
+def _rodrigues(axis: np.ndarray, angle: float) -> np.ndarray:
+    a = axis / np.linalg.norm(axis)
+    K = np.array([[0.0, -a[2], a[1]], [a[2], 0.0, -a[0]], [-a[1], a[0], 0.0]])
+    return np.eye(3) + math.sin(angle) * K + (1.0 - math.cos(angle)) * (K @ K)
+
+
+def _align(h: np.ndarray, n: np.ndarray) -> np.ndarray:
+    """A rotation mapping unit vector h onto unit vector n."""
+    c = float(np.dot(h, n))
+    ax = np.cross(h, n)
+    s = float(np.linalg.norm(ax))
+    if s < 1e-15:
+        if c > 0:
+            return np.eye(3)
+        perp = np.cross(h, [1.0, 0.0, 0.0])
+        if np.linalg.norm(perp) < 1e-6:
+            perp = np.cross(h, [0.0, 1.0, 0.0])
+        return _rodrigues(perp, math.pi)
+    return _rodrigues(ax, math.atan2(s, c))
+
+
+def _haar_rotation(rng: SplitMix64) -> np.ndarray:
+    u = rng.uniforms(3)
+    return _bunge_matrix(np.array([2.0 * math.pi * u[0], math.acos(1.0 - 2.0 * u[1]), 2.0 * math.pi * u[2]]))
+
+
+def grain_adjacency(gid: np.ndarray):
+    """Sorted unique pairs (a, b), a < b, of labels meeting across a voxel face (periodic)."""
+    pairs = []
+    for ax in range(3):
+        a = gid.reshape(-1)
+        b = np.roll(gid, -1, axis=ax).reshape(-1)
+        m = a != b
+        lo = np.minimum(a[m], b[m]).astype(np.int64)
+        hi = np.maximum(a[m], b[m]).astype(np.int64)
+        pairs.append(lo * (1 << 32) + hi)
+    u = np.unique(np.concatenate(pairs)) if pairs else np.zeros(0, dtype=np.int64)
+    return np.stack([u >> 32, u & 0xFFFFFFFF], axis=1)
+
+
+@dataclass
+class PaperMicrostructure:
+    """gid (nz, ny, nx) uint32 labels; euler (n_grains, 3) Bunge angles (crystal -> sample);
+    seeds (n_voronoi, 3); pairs: neighbouring twins (k, l, habit index, habit sign);
+    inclusions: rows (parent, child id, habit index, x (3, voxel units), thickness)."""
+
+    gid: np.ndarray
+    euler: np.ndarray
+    seeds: np.ndarray
+    pairs: list
+    inclusions: list
+
+    @property
+    def n_grains(self) -> int:
+        return self.euler.shape[0]
+
+
+def paper_microstructure(shape, label, n_expected: float = 1920.0, r_hard_vox: float = 5.0, p_neigh: float = 0.0,
+                         p_incl: float = 0.0, delta=(0.1, 0.3), seed: int = 0) -> PaperMicrostructure:
+    """The paper's stochastic microstructure (Sec. 2.1-2.3) on an (nz, ny, nx) grid.
+
+    `label(inp)` must return the Voronoi label map of an RVEInputs without twins (the GPU
+    labeller and the oracle's agree bit for bit).  Steps, in the paper's order:
+    1. Matern hard-core seeds: n_expected grains on average, hard-core radius r_hard_vox
+       voxels (relative to nx; the window is periodic).
+    2. Neighbouring twins: N ~ Poisson(p_neigh N_W / 2), redrawn until N <= N_W / 2; pairs of
+       adjacent unassigned grains (k, l) are drawn at random; O_k is Haar-uniform under the
+       condition that a habit plane ((011) or (101), chosen at random) lies in the joint
+       facet, whose normal is the direction between the two Voronoi seeds; O_l is O_k turned
+       by the misorientation angle about [100] or [010] respectively.  Assigned grains are
+       not drawn again, so no twin chains form.
+    3. The remaining grains get Haar-uniform orientations.
+    4. Inclusion twins: each grain, with probability p_incl, gets an inclusion I = the voxels
+       of G within a slab of thickness delta ~ U[delta_- ved(G), delta_+ ved(G)] around the
+       plane through a random boundary voxel of G parallel to the habit plane that the
+       chosen axis ([100] or [010]) fixes; O_I = O_G turned by the misorientation angle
+       about that axis; I becomes a new grain.  ved(G) = (6 V / pi)^(1/3) in voxels.
+    """
+    nz, ny, nx = shape
+    rng = SplitMix64(seed)
+    seeds = matern_hardcore_seeds(rng, n_expected, r_hard_vox / nx)
+    n = seeds.shape[0]
+    base = RVEInputs((nz, ny, nx), seeds, np.zeros((2 * n, 3)), np.zeros(n, dtype=np.uint8), np.zeros((n, 3)))
+    gid = np.asarray(label(base)).astype(np.uint32).reshape(nz, ny, nx)
+    theta = math.radians(TWIN_MISORIENTATION_DEG)
+    R = [None] * n
+    # 2. neighbouring twins
+    adj = grain_adjacency(gid)
+    nbrs = [[] for _ in range(n)]
+    for a, b in adj:
+        nbrs[int(a)].append(int(b))
+        nbrs[int(b)].append(int(a))
+    n_pairs = poisson(rng, p_neigh * n / 2.0)
+    while n_pairs > n // 2:
+        n_pairs = poisson(rng, p_neigh * n / 2.0)
+    free = np.ones(n, dtype=bool)
+    pairs = []
+    while len(pairs) < n_pairs:
+        cand = [g for g in range(n) if free[g] and any(free[m] for m in nbrs[g])]
+        if not cand:
+            break
+        k = cand[min(len(cand) - 1, int(rng.uniform() * len(cand)))]
+        fn = [m for m in nbrs[k] if free[m]]
+        l_ = fn[min(len(fn) - 1, int(rng.uniform() * len(fn)))]
+        hi = min(1, int(rng.uniform() * 2.0))
+        sign = 1.0 if rng.uniform() < 0.5 else -1.0
+        psi = 2.0 * math.pi * rng.uniform()
+        d = seeds[l_] - seeds[k]
+        d -= np.round(d)
+        nrm = sign * d / np.linalg.norm(d)
+        h = HABIT_NORMALS[hi]
+        R[k] = _align(h, nrm) @ _rodrigues(h, psi)
+        R[l_] = R[k] @ _rodrigues(HABIT_AXES[hi], theta)
+        free[k] = free[l_] = False
+        pairs.append((k, l_, hi, sign))
+    # 3. the remaining grains
+    for g in range(n):
+        if R[g] is None:
+            R[g] = _haar_rotation(rng)
+    # 4. inclusion twins
+    flat = gid.reshape(-1)
+    order = np.argsort(flat, kind="stable")
+    starts = np.searchsorted(flat[order], np.arange(n + 1))
+    boundary = np.zeros(flat.shape, dtype=bool)
+    for ax in range(3):
+        boundary |= (gid != np.roll(gid, 1, axis=ax)).reshape(-1)
+        boundary |= (gid != np.roll(gid, -1, axis=ax)).reshape(-1)
+    inclusions = []
+    new_gid = flat.copy()
+    dims = np.array([nx, ny, nz], dtype=np.float64)
+    for g in range(n):
+        if not rng.uniform() < p_incl:
+            continue
+        ai = min(1, int(rng.uniform() * 2.0))
+        vox = order[starts[g]:starts[g + 1]]
+        bvox = vox[boundary[vox]]
+        u_pt, u_th = rng.uniform(), rng.uniform()
+        if bvox.size == 0:
+            continue
+        xv = int(bvox[min(bvox.size - 1, int(u_pt * bvox.size))])
+        x = np.array([xv % nx, (xv // nx) % ny, xv // (nx * ny)], dtype=np.float64)
+        ved = (6.0 * vox.size / math.pi) ** (1.0 / 3.0)
+        thick = ved * (delta[0] + u_th * (delta[1] - delta[0]))
+        nrm = R[g] @ HABIT_NORMALS[ai]
+        yv = np.stack([vox % nx, (vox // nx) % ny, vox // (nx * ny)], axis=1).astype(np.float64)
+        dd = yv - x
+        dd -= dims * np.round(dd / dims)
+        inside = np.abs(dd @ nrm) <= 0.5 * thick
+        child = len(R)
+        new_gid[vox[inside]] = child
+        R.append(R[g] @ _rodrigues(HABIT_AXES[ai], theta))
+        inclusions.append((g, child, ai, x, thick))
+    euler = np.stack([_bunge_angles(r) for r in R])
+    return PaperMicrostructure(new_gid.reshape(nz, ny, nx), euler, seeds, pairs, inclusions)

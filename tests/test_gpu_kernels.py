@@ -84,3 +84,46 @@ def test_material_point_matches_oracle(lib, cuda, prec, n, dt):
     if n > 100:
         active = np.any(np.abs(v_ref - v) > 0, axis=1)
         assert 0.05 < active.mean() < 0.999
+
+
+PAPER_SET = dict(C33=183000.0, r0_ord=130.0, r0_sup=200.0, r0_twin=130.0, K=104.0, Kt=104.0, n=6.42, nt=6.42,
+                 Q_s=9.57, Q_b=10.5, Kc=1.45, fm=0.8, eta=1.0e4, c=0.0, d=0.0)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("which", ["paper", "int5_7", "eta0"])
+def test_material_point_other_rate_laws_match_oracle(lib, cuda, prec, which):
+    """The branch-free solve with real exponents (the paper's n = nt = 6.42; integer n = 5,
+    nt = 7) and the generic solve without regularisation (eta = 0; a slow Norton law, K =
+    3000 MPa s^(1/n), keeps the explicit RK4 stable at these increments) against the oracle."""
+    import dataclasses
+
+    import torch
+
+    from paper_2402_09996_gb300 import rve
+
+    mat_kw = {"paper": PAPER_SET, "int5_7": dict(n=5.0, nt=7.0),
+              "eta0": dict(eta=0.0, n=2.5, nt=2.5, K=3000.0, Kt=3000.0)}[which]
+    p = rve.FP64 if prec == "fp64" else rve.FP32
+    tdt = torch.float64 if p == rve.FP64 else torch.float32
+    n = 600
+    R, eps_n, eps, ep, v, al = _random_material_points(n, 31, scale=3.0 if which == "paper" else 1.0)
+    if p == rve.FP32:
+        R, eps_n, eps, ep, v, al = (a.astype(np.float32).astype(np.float64) for a in (R, eps_n, eps, ep, v, al))
+    dt = 0.5
+    nsub = orc.default_n_sub(dt)
+    mat = dataclasses.replace(orc.Material(), **mat_kw)
+    sig_ref, ep_ref, v_ref, al_ref = orc.material_point_increment(mat, R, eps_n, eps, ep, v, al, dt, nsub)
+    state = np.concatenate([tensor_to_six(ep), v.T, al.T], axis=0)
+    to_dev = lambda a: torch.tensor(np.ascontiguousarray(a), device=cuda, dtype=tdt)  # noqa: E731
+    st = to_dev(state)
+    sig = rve.material_point(to_dev(R.reshape(n, 9)), to_dev(tensor_to_six(eps_n)), to_dev(tensor_to_six(eps)), st,
+                             dt, nsub, p, **mat_kw).cpu().numpy()
+    st = st.cpu().numpy()
+    tol = 1e-10 if p == rve.FP64 else 2e-4
+    assert rel_err(six_to_tensor(sig), sig_ref) < tol
+    assert rel_err(six_to_tensor(st[:6]), ep_ref) < tol
+    assert rel_err(st[6:22].T, v_ref) < tol
+    assert rel_err(st[22:].T, al_ref) < tol
+    active = np.any(np.abs(v_ref - v) > 0, axis=1)
+    assert 0.05 < active.mean() < 0.999

@@ -238,3 +238,30 @@ def test_fft_tile_widths_do_not_change_results(lib, cuda, prec):
             assert np.array_equal(g["S"], r["S"]) and g["residual"] == r["residual"]
         assert np.array_equal(e1, e0) and np.array_equal(c1, c0)
         assert np.array_equal(s1, s0)
+
+
+def test_paper_parameter_set_matches_oracle(lib, cuda):
+    """The paper's parameter set (Sec. 3: K = Kt = 104, n = nt = 6.42, Q = 9.57 / 10.5,
+    r0 = 130 / 200 / 130 MPa, C33 = 183 GPa; no kinematic hardening), which runs the
+    real-exponent rate solve, against the oracle on a ragged twinned RVE under
+    shortening."""
+    import dataclasses
+
+    from paper_2402_09996_gb300 import inputs, rve
+
+    paper = dict(C33=183000.0, r0_ord=130.0, r0_sup=200.0, r0_twin=130.0, K=104.0, Kt=104.0, n=6.42, nt=6.42,
+                 Q_s=9.57, Q_b=10.5, Kc=1.45, fm=0.8, eta=1.0e4, c=0.0, d=0.0)
+    inp = inputs.make_inputs((12, 10, 6), 5, 0.5, seed=7)
+    gid = label_rve(inp)
+    edot = (0, 0, -2e-3, 0, 0, 0)
+    ref = orc.OracleRVE(np.asarray(gid, dtype=np.int64), inp.euler, dataclasses.replace(orc.Material(), **paper),
+                        orc.Options())
+    ref.set_load(orc.Load(Edot=np.array(edot, dtype=np.float64), dt=0.5))
+    ref.run(4)
+    with _rve(gid, inp.euler, precision=rve.FP64) as s:
+        s.set_material(**paper)
+        s.set_mixed_load(Edot=edot, dt=0.5)
+        s.step(4)
+        got = s.history()
+    _compare_histories(got, ref.history, 1e-8)
+    assert ref.history[-1]["mean_v"] > 0  # plastic by the end

@@ -240,6 +240,24 @@ rve_status rve_material_point(int precision, const rve_material* mat, long long 
                               const void* R, const void* eps_n, const void* eps, void* state,
                               void* sigma, double dt, int n_sub, void* stream);
 
+/* Reverse (vector-Jacobian) pass of rve_material_point: the constitutive building block of
+ * the adjoint of a load history (differentiating the Sec. 3 law, the Sec. 4 regularised
+ * rates implicitly, and the RK4 substeps).  For given adjoints of the outputs it returns the
+ * adjoints of the inputs and of the material parameters.
+ *   R, eps_n, eps, state  the forward inputs (as rve_material_point; state at t_n, read only);
+ *   sigma_b   6*nvox   adjoint of the stress at t_{n+1};
+ *   state_b   34*nvox  in: adjoint of the state at t_{n+1}; out: adjoint of the state at t_n;
+ *   eps_b, eps_n_b 6*nvox out: adjoints of eps and eps_n;
+ *   R_b       9*nvox   out: adjoint of the rotation entries (component-major, row-major R);
+ *   param_b   9*nvox   out: per-voxel adjoints of r0_ord, r0_sup, r0_twin, Q_s, Q_b, b_s,
+ *                      b_b, c, d (sum over voxels for the gradient).
+ * With sigma_b a unit vector and state_b zero, eps_b is a row of the algorithmic tangent
+ * d sigma / d eps.  n_sub <= 16.  Synchronises the stream before returning. */
+rve_status rve_material_point_vjp(int precision, const rve_material* mat, long long nvox, const void* R,
+                                  const void* eps_n, const void* eps, const void* state, const void* sigma_b,
+                                  void* state_b, void* eps_b, void* eps_n_b, void* R_b, void* param_b, double dt,
+                                  int n_sub, void* stream);
+
 /* Forward 3-D real-to-complex FFT of ncomp component-major real fields into the
  * solver's half-spectrum layout [comp][kz][ky][kx], kx in [0, nx/2], unnormalised
  * (the transform used in the Green-operator step, Sec. 3).  in: ncomp*nvox reals;

@@ -1,0 +1,478 @@
+// Reverse (vector-Jacobian) pass of the per-voxel Meric-Cailletaud update (Sec. 3 law,
+// Sec. 4 regularised rates, RK4 substeps along the linear strain path): given adjoints of
+// the outputs (stress at t_{n+1} and state at t_{n+1}) it returns adjoints of the inputs
+// (strain at t_n and t_{n+1}, state at t_n, rotation) and of the material parameters.
+// This is the constitutive building block of the adjoint of the load history; with unit
+// stress adjoints it gives the rows of the algorithmic tangent d sigma / d eps.
+//
+// The forward values are recomputed with the same code as the primal (constitutive.cuh):
+// each RK4 substep's start state is stored, and each stage is re-evaluated before it is
+// reversed.  The regularised rate rho(a, P) solving rho = P ((a - eta rho)/K)^n is
+// differentiated implicitly: with z = (a - eta rho)/K and D = K + eta P n z^(n-1),
+//   d rho / d a = P n z^(n-1) / D,   d rho / d P = K z^n / D   (0 where rho = 0).
+#pragma once
+
+#include "constitutive.cuh"
+
+namespace rve {
+
+// Adjoints of the material parameters (order of the C ABI's param_bar rows).
+constexpr int kParamBar = 9;  // r0_ord, r0_sup, r0_twin, Q_s, Q_b, b_s, b_b, c, d
+
+template <typename T>
+struct StageVals {
+  T sg[6];
+  T ex[16];
+  T tek[16];  // slip: tau - c alpha; twins: tau
+  T ak[16];
+  T rho[16];
+  T du_s[6], du_t[6];
+  T Es, Et, ftot, wslip, fm_left, Ptw, lg_Ptw;
+  T Rb_s, Rb_t;
+};
+
+// Forward stage (the same arithmetic as rk_stage): rates k of state Y at path point s,
+// with the intermediates kept for the reverse pass.
+template <typename T, int NP>
+__device__ void stage_eval(const MatDev<T>& M, const T* e0, const T* de, T s, const MPState<T>& Y, const T* tab,
+                           StageVals<T>& V, MPState<T>& k) {
+  constexpr double kLog2e = 1.44269504088896340736;
+  T e[6];
+  for (int c = 0; c < 6; ++c) e[c] = e0[c] + s * de[c] - Y.ep[c];
+  hooke<T>(M, e, V.sg);
+  V.Es = T(0);
+  V.Et = T(0);
+  T vtw = T(0);
+  const T cb_s = -M.b_s * T(kLog2e), cb_t = -M.b_b * T(kLog2e);
+  for (int q = 0; q < 12; ++q) {
+    V.ex[q] = fast_exp2<T>(cb_s * Y.v[q]);
+    V.Es += V.ex[q];
+  }
+  for (int q = 12; q < 16; ++q) {
+    V.ex[q] = fast_exp2<T>(cb_t * Y.v[q]);
+    V.Et += V.ex[q];
+    vtw += Y.v[q];
+  }
+  V.ftot = T(1.41421356237309504880) * vtw;
+  V.wslip = T(1) - V.ftot;
+  V.fm_left = M.fm - V.ftot;
+  V.fm_left = V.fm_left > T(0) ? V.fm_left : T(0);
+  V.Ptw = (M.Kc * T(0.70710678118654752440)) * V.fm_left;
+  V.lg_Ptw = fast_log2<T>(V.Ptw > T(0) ? V.Ptw : T(1));
+  const T dq = M.h_diag - M.h_off;
+  const T Qdq_s = M.Q_s * dq, Qdq_t = M.Q_b * dq;
+  V.Rb_s = M.Q_s * (M.h_off * (T(12) - V.Es) + dq);
+  V.Rb_t = M.Q_b * (M.h_off * (T(4) - V.Et) + dq);
+  RootCoef<T> qs, qt;
+  if constexpr (NP != 0) {
+    qs = root_coef<T>(T(1), M.K, M.n, M.inv_n, M.lg_K, M.eta, M.lg_eta, T(0));
+    qt = root_coef<T>(V.Ptw, M.Kt, M.nt, M.inv_nt, M.lg_Kt, M.eta, M.lg_eta, V.lg_Ptw);
+  }
+  T ss[6];
+  for (int c = 0; c < 6; ++c) ss[c] = V.sg[c] * sys_scale<T>(0);
+  for (int c = 0; c < 6; ++c) V.du_s[c] = V.du_t[c] = T(0);
+  for (int q = 0; q < 12; ++q) {
+    V.tek[q] = schmid_sum<T>(q, ss) - M.c * Y.al[q];
+    V.ak[q] = fabs(V.tek[q]) - ((M.r0[q] + V.Rb_s) - Qdq_s * V.ex[q]);
+    V.rho[q] = stage_rate<T, NP>(M, qs, V.ak[q], T(1), false, T(0), tab);
+    const T gd = copysign(V.rho[q], V.tek[q]);
+    schmid_add<T>(q, gd, V.du_s);
+    k.v[q] = V.rho[q];
+    k.al[q] = gd - M.d * V.rho[q] * Y.al[q];
+  }
+  for (int q = 12; q < 16; ++q) {
+    V.tek[q] = sys_scale<T>(q) * schmid_sum<T>(q, V.sg);
+    V.ak[q] = V.tek[q] - ((M.r0[q] + V.Rb_t) - Qdq_t * V.ex[q]);
+    V.rho[q] = stage_rate<T, NP>(M, qt, V.ak[q], V.Ptw, true, V.lg_Ptw, tab);
+    schmid_add<T>(q, V.rho[q], V.du_t);
+    k.v[q] = V.rho[q];
+  }
+  const T fs = V.wslip * sys_scale<T>(0);
+  for (int c = 0; c < 6; ++c) {
+    const T wc = c < 3 ? T(1) : T(0.5);
+    k.ep[c] = wc * (fs * V.du_s[c] + sys_scale<T>(12) * V.du_t[c]);
+  }
+}
+
+// d rho / d a and d rho / d P at a solved root (rho, a, P; exponent n, K, eta).
+template <typename T>
+__device__ void root_partials(T rho, T a, T P, T Kn, T n, T eta, T* d_a, T* d_P) {
+  if (!(rho > T(0)) || !(P > T(0))) {
+    *d_a = T(0);
+    *d_P = T(0);
+    return;
+  }
+  const T z = (a - eta * rho) / Kn;
+  if (!(z > T(0))) {
+    *d_a = T(0);
+    *d_P = T(0);
+    return;
+  }
+  const T zn = rho / P;              // z^n
+  const T pnz = P * n * (zn / z);    // P n z^(n-1)
+  const T D = Kn + eta * pnz;
+  *d_a = pnz / D;
+  *d_P = Kn * zn / D;
+}
+
+// Reverse of stage_eval: kb = adjoint of the rates; adds the adjoints of Y, e0, de and
+// the parameters.
+template <typename T>
+__device__ void stage_vjp(const MatDev<T>& M, const T* de, T s, const MPState<T>& Y, const StageVals<T>& V,
+                          const MPState<T>& kb, MPState<T>& Yb, T* e0b, T* deb, T* pb) {
+  constexpr double kLog2e = 1.44269504088896340736;
+  (void)kLog2e;
+  (void)de;
+  const T dq = M.h_diag - M.h_off;
+  const T ssc = sys_scale<T>(0), tsc = sys_scale<T>(12);
+  // eps_p rate: k.ep[c] = wc (wslip ssc du_s[c] + tsc du_t[c])
+  T dusb[6], dutb[6];
+  T wslipb = T(0);
+  for (int c = 0; c < 6; ++c) {
+    const T wc = c < 3 ? T(1) : T(0.5);
+    dusb[c] = kb.ep[c] * wc * V.wslip * ssc;
+    dutb[c] = kb.ep[c] * wc * tsc;
+    wslipb += kb.ep[c] * wc * ssc * V.du_s[c];
+  }
+  T sgb[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+  T exb[16];
+  for (int q = 0; q < 16; ++q) exb[q] = T(0);
+  T Esb = T(0), Etb = T(0), Ptwb = T(0);
+  // slip systems
+  for (int q = 0; q < 12; ++q) {
+    const T sgn = V.tek[q] < T(0) ? T(-1) : T(1);
+    const T gd = sgn * V.rho[q];
+    // gd enters du_s (schmid_add) and k.al = gd - d rho al
+    T gdb = kb.al[q];
+    for (int c = 0; c < 6; ++c) gdb += T(schmid_k(q, c)) * dusb[c];
+    T rhob = kb.v[q] + sgn * gdb - M.d * Y.al[q] * kb.al[q];
+    Yb.al[q] += -M.d * V.rho[q] * kb.al[q];
+    pb[8] += -V.rho[q] * Y.al[q] * kb.al[q];  // d
+    (void)gd;
+    T d_a, d_P;
+    root_partials<T>(V.rho[q], V.ak[q], T(1), M.K, M.n, M.eta, &d_a, &d_P);
+    const T akb = rhob * d_a;
+    // a = |tek| - ((r0 + Rb_s) - Qdq_s ex)
+    const T tekb = akb * sgn;
+    const T rb = -akb;
+    pb[(q % 3 == 2) ? 0 : 1] += rb;  // r0: ordinary systems 2, 5, 8, 11; the rest superdislocations
+    Esb += rb * (-M.Q_s * M.h_off);
+    exb[q] += rb * (-M.Q_s * dq);
+    pb[3] += rb * ((M.h_off * (T(12) - V.Es) + dq) - dq * V.ex[q]);  // Q_s
+    // tek = ssc sum K sg - c al
+    Yb.al[q] += -M.c * tekb;
+    pb[7] += -Y.al[q] * tekb;  // c
+    for (int c = 0; c < 6; ++c) sgb[c] += ssc * T(schmid_k(q, c)) * tekb;
+  }
+  // twins
+  for (int q = 12; q < 16; ++q) {
+    T rhob = kb.v[q];
+    for (int c = 0; c < 6; ++c) rhob += T(schmid_k(q, c)) * dutb[c];
+    T d_a, d_P;
+    root_partials<T>(V.rho[q], V.ak[q], V.Ptw, M.Kt, M.nt, M.eta, &d_a, &d_P);
+    const T akb = rhob * d_a;
+    Ptwb += rhob * d_P;
+    const T rb = -akb;
+    pb[2] += rb;  // r0_twin
+    Etb += rb * (-M.Q_b * M.h_off);
+    exb[q] += rb * (-M.Q_b * dq);
+    pb[4] += rb * ((M.h_off * (T(4) - V.Et) + dq) - dq * V.ex[q]);  // Q_b
+    for (int c = 0; c < 6; ++c) sgb[c] += tsc * T(schmid_k(q, c)) * akb;
+  }
+  // Ptw = Kc/sqrt2 max(fm - ftot, 0); wslip = 1 - ftot; ftot = sqrt2 sum v_twin
+  T ftotb = -wslipb;
+  if (V.fm_left > T(0)) ftotb += Ptwb * (-(M.Kc * T(0.70710678118654752440)));
+  const T vtwb = T(1.41421356237309504880) * ftotb;
+  // ex = exp(-b v)
+  for (int q = 0; q < 12; ++q) {
+    exb[q] += Esb;
+    Yb.v[q] += exb[q] * (-M.b_s * V.ex[q]);
+    pb[5] += exb[q] * (-Y.v[q] * V.ex[q]);  // b_s
+  }
+  for (int q = 12; q < 16; ++q) {
+    exb[q] += Etb;
+    Yb.v[q] += exb[q] * (-M.b_b * V.ex[q]) + vtwb;
+    pb[6] += exb[q] * (-Y.v[q] * V.ex[q]);  // b_b
+  }
+  // sg = hooke(e), e = e0 + s de - ep
+  T eb[6];
+  eb[0] = M.C11 * sgb[0] + M.C12 * sgb[1] + M.C13 * sgb[2];
+  eb[1] = M.C12 * sgb[0] + M.C11 * sgb[1] + M.C13 * sgb[2];
+  eb[2] = M.C13 * (sgb[0] + sgb[1]) + M.C33 * sgb[2];
+  eb[3] = T(2) * M.C44 * sgb[3];
+  eb[4] = T(2) * M.C44 * sgb[4];
+  eb[5] = T(2) * M.C66 * sgb[5];
+  for (int c = 0; c < 6; ++c) {
+    e0b[c] += eb[c];
+    deb[c] += s * eb[c];
+    Yb.ep[c] -= eb[c];
+  }
+}
+
+// Symmetric 3x3 from 6 components (11 22 33 23 13 12) and back.
+template <typename T>
+__device__ __forceinline__ void sym33(const T* v, T A[3][3]) {
+  A[0][0] = v[0]; A[1][1] = v[1]; A[2][2] = v[2];
+  A[1][2] = A[2][1] = v[3];
+  A[0][2] = A[2][0] = v[4];
+  A[0][1] = A[1][0] = v[5];
+}
+// adjoint of `sym33` for a symmetric tensor adjoint G: off-diagonal components appear twice
+template <typename T>
+__device__ __forceinline__ void sym33_adj(const T G[3][3], T* vb) {
+  vb[0] = G[0][0]; vb[1] = G[1][1]; vb[2] = G[2][2];
+  vb[3] = G[1][2] + G[2][1];
+  vb[4] = G[0][2] + G[2][0];
+  vb[5] = G[0][1] + G[1][0];
+}
+// tensor adjoint of a 6-component output taken from a symmetric tensor (one entry each)
+template <typename T>
+__device__ __forceinline__ void out6_adj(const T* ob, T G[3][3]) {
+  G[0][0] = ob[0]; G[1][1] = ob[1]; G[2][2] = ob[2];
+  G[1][2] = G[2][1] = T(0.5) * ob[3];
+  G[0][2] = G[2][0] = T(0.5) * ob[4];
+  G[0][1] = G[1][0] = T(0.5) * ob[5];
+}
+
+// out = R^T E R (to_crystal): given out_b, adds E_b (6) and R_b (9).
+template <typename T>
+__device__ void to_crystal_vjp(const T* R, const T* e, const T* ob, T* eb, T* Rb) {
+  T G[3][3], E[3][3];
+  out6_adj<T>(ob, G);
+  sym33<T>(e, E);
+  // E_b = R G R^T ; R_b = 2 E R G
+  T Eb[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      T acc = T(0);
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) acc += R[i * 3 + a] * G[a][b] * R[j * 3 + b];
+      Eb[i][j] = acc;
+    }
+  T eb6[6];
+  sym33_adj<T>(Eb, eb6);
+  for (int c = 0; c < 6; ++c) eb[c] += eb6[c];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      T acc = T(0);
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) acc += E[i][a] * R[a * 3 + b] * G[b][j];
+      Rb[i * 3 + j] += T(2) * acc;
+    }
+}
+
+// out = R S R^T (to_sample): given out_b, adds S_b (6) and R_b (9).
+template <typename T>
+__device__ void to_sample_vjp(const T* R, const T* s, const T* ob, T* sb, T* Rb) {
+  T G[3][3], S[3][3];
+  out6_adj<T>(ob, G);
+  sym33<T>(s, S);
+  T Sb[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      T acc = T(0);
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) acc += R[a * 3 + i] * G[a][b] * R[b * 3 + j];
+      Sb[i][j] = acc;
+    }
+  T sb6[6];
+  sym33_adj<T>(Sb, sb6);
+  for (int c = 0; c < 6; ++c) sb[c] += sb6[c];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      T acc = T(0);
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) acc += G[i][a] * R[a * 3 + b] * S[b][j];
+      Rb[i * 3 + j] += T(2) * acc;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void state_axpy(MPState<T>& y, T w, const MPState<T>& x) {
+  for (int c = 0; c < 6; ++c) y.ep[c] += w * x.ep[c];
+  for (int c = 0; c < 16; ++c) y.v[c] += w * x.v[c];
+  for (int c = 0; c < 12; ++c) y.al[c] += w * x.al[c];
+}
+template <typename T>
+__device__ __forceinline__ void state_zero(MPState<T>& y) {
+  for (int c = 0; c < 6; ++c) y.ep[c] = T(0);
+  for (int c = 0; c < 16; ++c) y.v[c] = T(0);
+  for (int c = 0; c < 12; ++c) y.al[c] = T(0);
+}
+
+
+// Reverse of mc_voxel.  In: R, eps_n, eps, y0 (state at t_n), sigma_b (adjoint of the stress
+// at t_{n+1}), yb (adjoint of the state at t_{n+1}; overwritten with the adjoint of y0).
+// Out (added): eps_nb, epsb, Rb, pb (kParamBar).  nsub <= kMaxSubVjp.
+template <typename T, int NP>
+__device__ void mc_voxel_vjp(const MatDev<T>& M, const T* R, const T* eps_n, const T* eps, const MPState<T>& y0,
+                             T dt, int nsub, const T* sigma_b, MPState<T>& yb, T* eps_nb, T* epsb, T* Rb, T* pb,
+                             const T* tab) {
+  T e0[6], e1[6], de[6];
+  to_crystal<T>(R, eps_n, e0);
+  to_crystal<T>(R, eps, e1);
+  for (int c = 0; c < 6; ++c) de[c] = e1[c] - e0[c];
+  const bool quiet = elastic_increment<T>(M, e0, de, y0);
+  // forward: substep start states
+  MPState<T> ys[kMaxSubVjp + 1];
+  ys[0] = y0;
+  const T h = dt / T(nsub);
+  const T inv = T(1) / T(nsub);
+  StageVals<T> V;
+  if (!quiet) {
+    for (int m = 0; m < nsub; ++m) {
+      const T s0 = T(m) * inv, sh = (T(m) + T(0.5)) * inv, s1 = (T(m) + T(1)) * inv;
+      MPState<T> k1, k2, k3, k4, Y;
+      stage_eval<T, NP>(M, e0, de, s0, ys[m], tab, V, k1);
+      Y = ys[m];
+      state_axpy<T>(Y, T(0.5) * h, k1);
+      stage_eval<T, NP>(M, e0, de, sh, Y, tab, V, k2);
+      Y = ys[m];
+      state_axpy<T>(Y, T(0.5) * h, k2);
+      stage_eval<T, NP>(M, e0, de, sh, Y, tab, V, k3);
+      Y = ys[m];
+      state_axpy<T>(Y, h, k3);
+      stage_eval<T, NP>(M, e0, de, s1, Y, tab, V, k4);
+      MPState<T> acc;
+      state_zero<T>(acc);
+      state_axpy<T>(acc, T(1), k1);
+      state_axpy<T>(acc, T(2), k2);
+      state_axpy<T>(acc, T(2), k3);
+      state_axpy<T>(acc, T(1), k4);
+      ys[m + 1] = ys[m];
+      state_axpy<T>(ys[m + 1], h / T(6), acc);
+    }
+  } else {
+    ys[nsub] = y0;
+  }
+  const MPState<T>& yN = ys[nsub];
+  // stress: sc = C (e1 - ep_N); sigma = R sc R^T
+  T ee[6], sc[6];
+  for (int c = 0; c < 6; ++c) ee[c] = e1[c] - yN.ep[c];
+  hooke<T>(M, ee, sc);
+  T scb[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+  to_sample_vjp<T>(R, sc, sigma_b, scb, Rb);
+  T eeb[6];
+  eeb[0] = M.C11 * scb[0] + M.C12 * scb[1] + M.C13 * scb[2];
+  eeb[1] = M.C12 * scb[0] + M.C11 * scb[1] + M.C13 * scb[2];
+  eeb[2] = M.C13 * (scb[0] + scb[1]) + M.C33 * scb[2];
+  eeb[3] = T(2) * M.C44 * scb[3];
+  eeb[4] = T(2) * M.C44 * scb[4];
+  eeb[5] = T(2) * M.C66 * scb[5];
+  T e0b[6], e1b[6], deb[6];
+  for (int c = 0; c < 6; ++c) {
+    e1b[c] = eeb[c];
+    yb.ep[c] -= eeb[c];
+    e0b[c] = T(0);
+    deb[c] = T(0);
+  }
+  if (!quiet) {
+    for (int m = nsub - 1; m >= 0; --m) {
+      const T s0 = T(m) * inv, sh = (T(m) + T(0.5)) * inv, s1 = (T(m) + T(1)) * inv;
+      // recompute the substep's stages
+      MPState<T> k1, k2, k3, k4, Y2, Y3, Y4;
+      StageVals<T> V1, V2, V3, V4;
+      stage_eval<T, NP>(M, e0, de, s0, ys[m], tab, V1, k1);
+      Y2 = ys[m];
+      state_axpy<T>(Y2, T(0.5) * h, k1);
+      stage_eval<T, NP>(M, e0, de, sh, Y2, tab, V2, k2);
+      Y3 = ys[m];
+      state_axpy<T>(Y3, T(0.5) * h, k2);
+      stage_eval<T, NP>(M, e0, de, sh, Y3, tab, V3, k3);
+      Y4 = ys[m];
+      state_axpy<T>(Y4, h, k3);
+      stage_eval<T, NP>(M, e0, de, s1, Y4, tab, V4, k4);
+      // y' = y + h/6 (k1 + 2 k2 + 2 k3 + k4)
+      MPState<T> k1b, k2b, k3b, k4b, Yb;
+      state_zero<T>(k1b);
+      state_zero<T>(k2b);
+      state_zero<T>(k3b);
+      state_zero<T>(k4b);
+      state_axpy<T>(k1b, h / T(6), yb);
+      state_axpy<T>(k2b, h / T(3), yb);
+      state_axpy<T>(k3b, h / T(3), yb);
+      state_axpy<T>(k4b, h / T(6), yb);
+      // stage 4 at Y4 = y + h k3
+      state_zero<T>(Yb);
+      stage_vjp<T>(M, de, s1, Y4, V4, k4b, Yb, e0b, deb, pb);
+      state_axpy<T>(yb, T(1), Yb);
+      state_axpy<T>(k3b, h, Yb);
+      // stage 3 at Y3 = y + h/2 k2
+      state_zero<T>(Yb);
+      stage_vjp<T>(M, de, sh, Y3, V3, k3b, Yb, e0b, deb, pb);
+      state_axpy<T>(yb, T(1), Yb);
+      state_axpy<T>(k2b, T(0.5) * h, Yb);
+      // stage 2 at Y2 = y + h/2 k1
+      state_zero<T>(Yb);
+      stage_vjp<T>(M, de, sh, Y2, V2, k2b, Yb, e0b, deb, pb);
+      state_axpy<T>(yb, T(1), Yb);
+      state_axpy<T>(k1b, T(0.5) * h, Yb);
+      // stage 1 at y
+      state_zero<T>(Yb);
+      stage_vjp<T>(M, de, s0, ys[m], V1, k1b, Yb, e0b, deb, pb);
+      state_axpy<T>(yb, T(1), Yb);
+    }
+  }
+  // de = e1 - e0; e0 = R^T eps_n R; e1 = R^T eps R
+  for (int c = 0; c < 6; ++c) {
+    e1b[c] += deb[c];
+    e0b[c] -= deb[c];
+  }
+  to_crystal_vjp<T>(R, eps_n, e0b, eps_nb, Rb);
+  to_crystal_vjp<T>(R, eps, e1b, epsb, Rb);
+}
+
+// One thread per voxel; arrays component-major (component * nvox + voxel) as in the
+// forward material-point kernel.  state_b: in, adjoint of the state at t_{n+1}; out, adjoint
+// of the state at t_n.  R_b (9 x nvox) and param_b (kParamBar x nvox) are per voxel.
+template <typename T, int NP>
+__global__ void k_material_point_vjp(const MatDev<T> M, long long nvox, const T* __restrict__ R,
+                                     const T* __restrict__ eps_n, const T* __restrict__ eps,
+                                     const T* __restrict__ state, T dt, int nsub, const T* __restrict__ sigma_b,
+                                     T* state_b, T* eps_b, T* eps_n_b, T* R_b, T* param_b,
+                                     const T* __restrict__ root_tab) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* tab = reinterpret_cast<T*>(smem_raw);
+  if (NP != 0)
+    for (int k = threadIdx.x; k < kRootTabs; k += blockDim.x) tab[k] = root_tab[k];
+  __syncthreads();
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nvox) return;
+  const size_t n = (size_t)nvox;
+  T r[9], en[6], e[6], sb[6];
+  for (int k = 0; k < 9; ++k) r[k] = R[(size_t)i * 9 + k];
+  for (int c = 0; c < 6; ++c) {
+    en[c] = eps_n[c * n + i];
+    e[c] = eps[c * n + i];
+    sb[c] = sigma_b[c * n + i];
+  }
+  MPState<T> y, yb;
+  for (int c = 0; c < 6; ++c) {
+    y.ep[c] = state[c * n + i];
+    yb.ep[c] = state_b[c * n + i];
+  }
+  for (int c = 0; c < 16; ++c) {
+    y.v[c] = state[(6 + c) * n + i];
+    yb.v[c] = state_b[(6 + c) * n + i];
+  }
+  for (int c = 0; c < 12; ++c) {
+    y.al[c] = state[(22 + c) * n + i];
+    yb.al[c] = state_b[(22 + c) * n + i];
+  }
+  T enb[6] = {T(0), T(0), T(0), T(0), T(0), T(0)}, eb[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+  T rb[9] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
+  T pb[kParamBar];
+  for (int k = 0; k < kParamBar; ++k) pb[k] = T(0);
+  mc_voxel_vjp<T, NP>(M, r, en, e, y, dt, nsub, sb, yb, enb, eb, rb, pb, tab);
+  for (int c = 0; c < 6; ++c) {
+    state_b[c * n + i] = yb.ep[c];
+    eps_b[c * n + i] = eb[c];
+    eps_n_b[c * n + i] = enb[c];
+  }
+  for (int c = 0; c < 16; ++c) state_b[(6 + c) * n + i] = yb.v[c];
+  for (int c = 0; c < 12; ++c) state_b[(22 + c) * n + i] = yb.al[c];
+  for (int k = 0; k < 9; ++k) R_b[k * n + i] = rb[k];
+  for (int k = 0; k < kParamBar; ++k) param_b[k * n + i] = pb[k];
+}
+
+}  // namespace rve

@@ -1598,6 +1598,46 @@ rve_status rve_material_point(int precision, const rve_material* mat, long long 
   return RVE_OK;
 }
 
+rve_status rve_material_point_vjp(int precision, const rve_material* mat, long long nvox, const void* R,
+                                  const void* eps_n, const void* eps, const void* state, const void* sigma_b,
+                                  void* state_b, void* eps_b, void* eps_n_b, void* R_b, void* param_b, double dt,
+                                  int n_sub, void* stream) {
+  if (!mat || nvox < 0 || (nvox > 0 && (!R || !eps_n || !eps || !state || !sigma_b || !state_b || !eps_b ||
+                                        !eps_n_b || !R_b || !param_b)) ||
+      !(dt > 0) || n_sub < 1 || n_sub > kMaxSubVjp)
+    return fail(nullptr, RVE_ERR_INVALID_ARG, "bad material-point adjoint arguments (n_sub must be 1..16)");
+  rve_s tmp;
+  tmp.mat = *mat;
+  rve_status s = check_material(&tmp, *mat);
+  if (s) return fail(nullptr, s, tmp.err);
+  reference_medium(tmp.mat, &tmp.lam0, &tmp.mu0);
+  if (precision != RVE_FP64 && precision != RVE_FP32) return fail(nullptr, RVE_ERR_INVALID_ARG, "bad precision");
+  cudaStream_t st = stream ? (cudaStream_t)stream : cudaStreamPerThread;
+  tmp.stream = st;
+  const int np = rate_variant(mat->eta, is_small_int(mat->n), is_small_int(mat->nt));
+  s = precision == RVE_FP64 ? upload_root_tab<double>(&tmp) : upload_root_tab<float>(&tmp);
+  if (s) {
+    release(&tmp);
+    return fail(nullptr, s, tmp.err);
+  }
+  cudaError_t e;
+  if (precision == RVE_FP64)
+    e = launch_material_point_vjp<double>(make_mat<double>(&tmp), np, nvox, (const double*)R, (const double*)eps_n,
+                                          (const double*)eps, (const double*)state, dt, n_sub,
+                                          (const double*)sigma_b, (double*)state_b, (double*)eps_b,
+                                          (double*)eps_n_b, (double*)R_b, (double*)param_b,
+                                          (const double*)tmp.root_tab, st);
+  else
+    e = launch_material_point_vjp<float>(make_mat<float>(&tmp), np, nvox, (const float*)R, (const float*)eps_n,
+                                         (const float*)eps, (const float*)state, (float)dt, n_sub,
+                                         (const float*)sigma_b, (float*)state_b, (float*)eps_b, (float*)eps_n_b,
+                                         (float*)R_b, (float*)param_b, (const float*)tmp.root_tab, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  release(&tmp);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "material_point_vjp");
+  return RVE_OK;
+}
+
 }  // extern "C"
 
 template <typename T>

@@ -3,6 +3,7 @@
 // constitutive kernels, one rate-solve variant per translation unit).
 #pragma once
 
+#include "adjoint.cuh"
 #include "launch.h"
 #include "solver_kernels.cuh"
 
@@ -44,10 +45,28 @@ cudaError_t launch_material_point_np(const MatDev<T>& M, long long nvox, const T
   return cudaGetLastError();
 }
 
+template <typename T, int NP>
+cudaError_t launch_material_point_vjp_np(const MatDev<T>& M, long long nvox, const T* R, const T* eps_n, const T* eps,
+                                         const T* state, T dt, int nsub, const T* sigma_b, T* state_b, T* eps_b,
+                                         T* eps_n_b, T* R_b, T* param_b, const T* root_tab, cudaStream_t s) {
+  if (nvox <= 0) return cudaSuccess;
+  const int thr = 64;
+  const long long grid = (nvox + thr - 1) / thr;
+  const size_t smem = (size_t)kRootTabs * sizeof(T);
+  cudaError_t e = set_smem<T>((const void*)k_material_point_vjp<T, NP>, smem);
+  if (e != cudaSuccess) return e;
+  k_material_point_vjp<T, NP><<<(unsigned)grid, thr, smem, s>>>(M, nvox, R, eps_n, eps, state, dt, nsub, sigma_b,
+                                                                state_b, eps_b, eps_n_b, R_b, param_b, root_tab);
+  return cudaGetLastError();
+}
+
 #define RVE_INSTANTIATE_X(T, NP)                                                                                \
   template cudaError_t launch_xpass_np<T, NP>(const XArgs<T>&, bool, int, size_t, cudaStream_t);              \
   template cudaError_t launch_material_point_np<T, NP>(const MatDev<T>&, long long, const T*, const T*, const T*, \
-                                                       T*, T*, T, int, const T*, cudaStream_t);
+                                                       T*, T*, T, int, const T*, cudaStream_t);              \
+  template cudaError_t launch_material_point_vjp_np<T, NP>(const MatDev<T>&, long long, const T*, const T*,      \
+                                                           const T*, const T*, T, int, const T*, T*, T*, T*, T*, \
+                                                           T*, const T*, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_line(const LineArgs<T>& a, int sign, dim3 grid, size_t smem, cudaStream_t s) {

@@ -27,6 +27,25 @@ template <typename T, int NP>
 cudaError_t launch_material_point_np(const MatDev<T>& M, long long nvox, const T* R, const T* eps_n, const T* eps,
                                      T* state, T* sigma, T dt, int nsub, const T* root_tab, cudaStream_t s);
 
+template <typename T, int NP>
+cudaError_t launch_material_point_vjp_np(const MatDev<T>& M, long long nvox, const T* R, const T* eps_n, const T* eps,
+                                         const T* state, T dt, int nsub, const T* sigma_b, T* state_b, T* eps_b,
+                                         T* eps_n_b, T* R_b, T* param_b, const T* root_tab, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_material_point_vjp(const MatDev<T>& M, int np, long long nvox, const T* R, const T* eps_n,
+                                      const T* eps, const T* state, T dt, int nsub, const T* sigma_b, T* state_b,
+                                      T* eps_b, T* eps_n_b, T* R_b, T* param_b, const T* root_tab, cudaStream_t s) {
+  if (np == 10)
+    return launch_material_point_vjp_np<T, 10>(M, nvox, R, eps_n, eps, state, dt, nsub, sigma_b, state_b, eps_b,
+                                               eps_n_b, R_b, param_b, root_tab, s);
+  if (np < 0)
+    return launch_material_point_vjp_np<T, -1>(M, nvox, R, eps_n, eps, state, dt, nsub, sigma_b, state_b, eps_b,
+                                               eps_n_b, R_b, param_b, root_tab, s);
+  return launch_material_point_vjp_np<T, 0>(M, nvox, R, eps_n, eps, state, dt, nsub, sigma_b, state_b, eps_b,
+                                            eps_n_b, R_b, param_b, root_tab, s);
+}
+
 template <typename T>
 cudaError_t launch_xpass(const XArgs<T>& a, int np, bool commit, int grid, size_t smem, cudaStream_t s) {
   if (np == 10) return launch_xpass_np<T, 10>(a, commit, grid, smem, s);

@@ -99,4 +99,7 @@ constexpr double kRootPerUnit = kRootIv / (2.0 * kRootSpan);
 constexpr int kRootTabLen = 2 * kRootIv;  // values per table
 constexpr int kRootTabs = 2 * kRootTabLen;  // slip systems' table, then the twin exponent's
 
+// RK4 substeps whose start states the constitutive reverse pass (adjoint.cuh) keeps.
+constexpr int kMaxSubVjp = 16;
+
 }  // namespace rve

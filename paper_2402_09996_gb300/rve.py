@@ -117,7 +117,7 @@ EXPORTED = [
     "rve_set_mixed_load", "rve_step", "rve_get_effective", "rve_get_fields", "rve_save_state",
     "rve_load_state", "rve_last_error", "rve_destroy", "rve_material_point", "rve_fft_r2c",
     "rve_fft_c2r", "rve_label_voronoi", "rve_kernel_times", "rve_get_residuals", "rve_label_voronoi_noalloc",
-    "rve_step_batch",
+    "rve_step_batch", "rve_material_point_vjp",
 ]
 NOALLOC_MAX_PARENTS = 4096  # RVE_NOALLOC_MAX_PARENTS of include/rve.h
 
@@ -154,6 +154,8 @@ def load_library(path: str | os.PathLike | None = None):
     lib.rve_get_residuals.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double), i, C.POINTER(i)]
     lib.rve_label_voronoi_noalloc.argtypes = [i, i, i, i, vp, vp, vp, vp, vp]
     lib.rve_step_batch.argtypes = [C.POINTER(vp), i, i, C.POINTER(C.c_longlong), C.POINTER(i)]
+    lib.rve_material_point_vjp.argtypes = [i, C.POINTER(Material), C.c_longlong, vp, vp, vp, vp, vp, vp, vp, vp, vp,
+                                           vp, d, i, vp]
     for name in EXPORTED:
         getattr(lib, name).restype = C.c_int
     lib.rve_options_default.restype = None
@@ -400,6 +402,31 @@ def material_point(R, eps_n, eps, state, dt, n_sub, precision=FP64, **material):
                                 _ptr(sigma), float(dt), int(n_sub), _torch_stream())
     _check(st, None)
     return sigma
+
+
+def material_point_vjp(R, eps_n, eps, state, sigma_b, state_b, dt, n_sub, precision=FP64, **material):
+    """Reverse pass of `material_point` on CUDA tensors (rve_material_point_vjp).
+
+    state (34, nvox) is the state at t_n (unchanged); state_b (34, nvox) holds the adjoint of
+    the state at t_{n+1} and is overwritten with the adjoint of the state at t_n.  Returns
+    (eps_b, eps_n_b, R_b (9, nvox), param_b (9, nvox)); param_b rows: r0_ord, r0_sup,
+    r0_twin, Q_s, Q_b, b_s, b_b, c, d (per voxel)."""
+    import torch
+
+    lib = load_library()
+    m = default_material()
+    for k, v in material.items():
+        setattr(m, k, float(v))
+    nvox = eps.shape[1]
+    eps_b = torch.empty_like(eps)
+    eps_n_b = torch.empty_like(eps)
+    R_b = torch.empty((9, nvox), dtype=eps.dtype, device=eps.device)
+    param_b = torch.empty((9, nvox), dtype=eps.dtype, device=eps.device)
+    st = lib.rve_material_point_vjp(precision, C.byref(m), nvox, _ptr(R), _ptr(eps_n), _ptr(eps), _ptr(state),
+                                    _ptr(sigma_b), _ptr(state_b), _ptr(eps_b), _ptr(eps_n_b), _ptr(R_b),
+                                    _ptr(param_b), float(dt), int(n_sub), _torch_stream())
+    _check(st, None)
+    return eps_b, eps_n_b, R_b, param_b
 
 
 def fft_r2c(real, precision=FP64):

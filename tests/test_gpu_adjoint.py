@@ -1,0 +1,96 @@
+"""Reverse pass of the per-voxel constitutive update (rve_material_point_vjp) against
+central finite differences of the FP64 oracle's material-point update (Sec. 3 law, Sec. 4
+regularised rates, RK4): directional derivatives of J = sum(sigma_b . sigma) +
+sum(state_b . state) with respect to every input and each material parameter."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from helpers import six_to_tensor, tensor_to_six
+from oracle import rve_oracle as orc
+
+pytestmark = pytest.mark.gpu
+
+PARAMS = ["r0_ord", "r0_sup", "r0_twin", "Q_s", "Q_b", "b_s", "b_b", "c", "d"]
+PAPER = dict(C33=183000.0, r0_ord=130.0, r0_sup=200.0, r0_twin=130.0, K=104.0, Kt=104.0, n=6.42, nt=6.42,
+             Q_s=9.57, Q_b=10.5, Kc=1.45, fm=0.8, eta=1.0e4, c=5000.0, d=300.0)
+
+
+def _points(n, seed, scale):
+    rng = np.random.default_rng(seed)
+    e = rng.uniform(0, 2 * np.pi, size=(n, 3))
+    e[:, 1] = np.arccos(rng.uniform(-1, 1, size=n))
+    R = orc.bunge_rotation(e)
+    sym = lambda a: 0.5 * (a + a.transpose(0, 2, 1))  # noqa: E731
+    eps_n = sym(rng.normal(scale=1.5e-3 * scale, size=(n, 3, 3)))
+    eps = eps_n + sym(rng.normal(scale=1.0e-3 * scale, size=(n, 3, 3)))
+    quiet = rng.uniform(size=n) < 0.25
+    eps_n[quiet] *= 0.1
+    eps[quiet] *= 0.1
+    ep = sym(rng.normal(scale=3e-4, size=(n, 3, 3)))
+    ep -= np.trace(ep, axis1=1, axis2=2)[:, None, None] * np.eye(3) / 3
+    v = rng.uniform(0, 2e-3, size=(n, 16))
+    v[:, 12:] *= 0.1
+    al = rng.uniform(-1e-3, 1e-3, size=(n, 12))
+    return R, tensor_to_six(eps_n), tensor_to_six(eps), tensor_to_six(ep), v, al
+
+
+def _J(mat, R, en6, e6, ep6, v, al, sb, yb, dt, nsub):
+    sig, ep1, v1, al1 = orc.material_point_increment(mat, R, six_to_tensor(en6), six_to_tensor(e6),
+                                                     six_to_tensor(ep6), v, al, dt, nsub)
+    y = np.concatenate([tensor_to_six(ep1), v1.T, al1.T], axis=0)
+    return float(np.sum(sb * tensor_to_six(sig)) + np.sum(yb * y))
+
+
+@pytest.mark.parametrize("which", ["workload", "paper"])
+def test_material_point_vjp_matches_oracle_finite_differences(lib, cuda, which):
+    import torch
+
+    from paper_2402_09996_gb300 import rve
+
+    kw = {} if which == "workload" else PAPER
+    mat = dataclasses.replace(orc.Material(), **kw)
+    n, dt = 40, 0.5
+    nsub = orc.default_n_sub(dt)
+    R, en6, e6, ep6, v, al = _points(n, 5 if which == "workload" else 6, 1.0 if which == "workload" else 3.0)
+    rng = np.random.default_rng(77)
+    sb = rng.normal(size=(6, n)) * 1e-2
+    yb = rng.normal(size=(34, n)) * 10.0
+    to = lambda a: torch.tensor(np.ascontiguousarray(a), device=cuda, dtype=torch.float64)  # noqa: E731
+    state = np.concatenate([ep6, v.T, al.T], axis=0)
+    st_b = to(yb)
+    eps_b, eps_n_b, R_b, p_b = rve.material_point_vjp(to(R.reshape(n, 9)), to(en6), to(e6), to(state), to(sb), st_b,
+                                                      dt, nsub, rve.FP64, **kw)
+    eps_b, eps_n_b, R_b, p_b, y0_b = (t.cpu().numpy() for t in (eps_b, eps_n_b, R_b, p_b, st_b))
+    J = lambda **ch: _J(ch.get("mat", mat), ch.get("R", R), ch.get("en6", en6), ch.get("e6", e6),  # noqa: E731
+                        ch.get("ep6", ep6), ch.get("v", v), ch.get("al", al), sb, yb, dt, nsub)
+
+    def fd(name, base, grad, scale):
+        d = np.random.default_rng(sum(map(ord, name))).normal(size=base.shape) * scale
+        h = 1e-5
+        jp = J(**{name: base + h * d})
+        jm = J(**{name: base - h * d})
+        num = (jp - jm) / (2 * h)
+        ana = float(np.sum(grad * d))
+        assert abs(num - ana) <= 2e-6 * max(abs(num), abs(ana)) + 1e-10, (name, num, ana)
+
+    fd("e6", e6, eps_b, 1e-3)
+    fd("en6", en6, eps_n_b, 1e-3)
+    fd("ep6", ep6, y0_b[:6], 3e-4)
+    fd("v", v, y0_b[6:22].T, 1e-3)
+    fd("al", al, y0_b[22:].T, 1e-3)
+    fd("R", R, R_b.T.reshape(n, 3, 3), 1e-2)
+    # parameters: one at a time
+    for k, name in enumerate(PARAMS):
+        p0 = getattr(mat, name)
+        h = 1e-6 * max(abs(p0), 1.0)
+        num = (J(mat=dataclasses.replace(mat, **{name: p0 + h})) - J(mat=dataclasses.replace(mat, **{name: p0 - h}))) / (
+            2 * h)
+        ana = float(np.sum(p_b[k]))
+        assert abs(num - ana) <= 2e-5 * max(abs(num), abs(ana)) + 1e-8, (name, num, ana)
+    # the sample mixes elastic and plastic points
+    _, _, v1, _ = orc.material_point_increment(mat, R, six_to_tensor(en6), six_to_tensor(e6), six_to_tensor(ep6), v,
+                                               al, dt, nsub)
+    active = np.any(v1 > v, axis=1)
+    assert 0.2 < active.mean() < 0.95

@@ -193,6 +193,30 @@ rve_status rve_step(rve_t h, int n_increments, long long* iterations_out);
  * include the time its kernels shared the GPU with the other handles'. */
 rve_status rve_step_batch(rve_t* hs, int n, int n_increments, long long* iterations_out, int* failed_out);
 
+/* Adjoint of one converged load increment n (t_{n-1} -> t_n) of a history objective J
+ * (the paper defines no adjoint; this extends its method to gradients).  The increment's
+ * converged strain solves the Green-operator fixed point (Sec. 4) with the mixed load; the
+ * adjoint solves the transposed linearised problem (the same fixed point with the
+ * transposed algorithmic tangent and the derivative of J as a source) and runs the
+ * reverse pass of the constitutive update (rve_material_point_vjp) on every voxel.
+ *   eps_prev, eps_cur  6*nvox committed strain at t_{n-1} and t_n (device, double);
+ *   state_prev         34*nvox state at t_{n-1} (device, double; rve_get_fields layout:
+ *                      eps_p 6, v 16, alpha 12, component-major);
+ *   dS[6]              dJ / d<sigma>_n (host);
+ *   dt                 the increment's length;
+ *   state_b   34*nvox  in: dJ/d(state at t_n); out: dJ/d(state at t_{n-1}) (device, double);
+ *   eps_b     6*nvox   in: dJ/d(strain at t_n) through later increments; out: the same at
+ *                      t_{n-1} (device, double);
+ *   param_grad[9]      accumulated dJ/d(r0_ord, r0_sup, r0_twin, Q_s, Q_b, b_s, b_b, c, d);
+ *   euler_grad         n_grains*3, accumulated dJ/d(phi1, Phi, phi2) per grain (host);
+ *   iterations_out     adds the adjoint fixed-point iterations (may be NULL).
+ * The handle supplies the material, the load (its strain-controlled components and dt
+ * must be those of the increment) and the solver options.  The call reuses the handle's
+ * spectra: its forward state is lost (keep a copy with rve_save_state).  Needs n_sub <= 16. */
+rve_status rve_adjoint_increment(rve_t h, const double* eps_prev, const double* eps_cur, const double* state_prev,
+                                 const double dS[6], double dt, double* state_b, double* eps_b, double* param_grad,
+                                 double* euler_grad, long long* iterations_out);
+
 /* Effective results.  last (may be NULL) receives the most recent record;
  * hist (may be NULL) receives up to cap records, oldest first; n_hist (may be
  * NULL) receives the number of records held. */

@@ -120,6 +120,23 @@ void bunge(const double* e, double R[9]) {
   R[8] = c;
 }
 
+// d R / d (phi1, Phi, phi2) of `bunge`, entry-wise (dR[k][i] = d R[i] / d e[k]).
+void bunge_grad(const double* e, double dR[3][9]) {
+  const double c1 = std::cos(e[0]), s1 = std::sin(e[0]);
+  const double c = std::cos(e[1]), s = std::sin(e[1]);
+  const double c2 = std::cos(e[2]), s2 = std::sin(e[2]);
+  const double d1[9] = {-s1 * c2 - c1 * c * s2, s1 * s2 - c1 * c * c2, c1 * s, c1 * c2 - s1 * c * s2,
+                        -c1 * s2 - s1 * c * c2, s1 * s, 0.0, 0.0, 0.0};
+  const double d2[9] = {s1 * s * s2, s1 * s * c2, s1 * c, -c1 * s * s2, -c1 * s * c2, -c1 * c, c * s2, c * c2, -s};
+  const double d3[9] = {-c1 * s2 - s1 * c * c2, -c1 * c2 + s1 * c * s2, 0.0, -s1 * s2 + c1 * c * c2,
+                        -s1 * c2 - c1 * c * s2, 0.0, s * c2, -s * s2, 0.0};
+  for (int i = 0; i < 9; ++i) {
+    dR[0][i] = d1[i];
+    dR[1][i] = d2[i];
+    dR[2][i] = d3[i];
+  }
+}
+
 // Isotropic reference medium: 3 k0 = 2 mu0 = (min + max Mandel eigenvalue of C) / 2.
 void reference_medium(const rve_material& m, double* lam0, double* mu0) {
   double A[36] = {0};
@@ -241,6 +258,14 @@ struct rve_s {
   cudaGraph_t graph[3] = {nullptr, nullptr, nullptr};
   cudaGraphExec_t gexec[3] = {nullptr, nullptr, nullptr};
   cudaStream_t cap[2] = {nullptr, nullptr};  // capture streams
+  // adjoint of an increment (rve_adjoint_increment): host grain map, scratch, and the
+  // x pass's linear-law mode (s = B eps - g) used by the adjoint fixed point
+  std::vector<uint32_t> gid_host;
+  void* adj = nullptr;  // one block of per-voxel scratch arrays, type by precision
+  bool lin_mode = false;
+  const void* lin_B = nullptr;
+  const void* lin_g = nullptr;
+  void* lin_mu = nullptr;
   // FFT tile autotuner (opt.autotune): runs once, before the first increment
   bool tuned = false;
   IterStatus* st_tune = nullptr;  // scratch status and history for timing the z pass
@@ -599,6 +624,11 @@ XArgs<T> x_args(rve_s* h, const void* in, void* out, int it) {
   a.Rg = (const T*)h->Rg;
   a.root_tab = (const T*)h->root_tab;
   a.M = make_mat<T>(h);
+  if (h->lin_mode) {
+    a.lin_B = (const T*)h->lin_B;
+    a.lin_g = (const T*)h->lin_g;
+    if (!out) a.eps_n = (T*)h->lin_mu;  // the linear-law commit writes the solution field here
+  }
   // mixed load
   double M0[36];
   c0_mandel(h->lam0, h->mu0, M0);
@@ -606,7 +636,7 @@ XArgs<T> x_args(rve_s* h, const void* in, void* out, int it) {
   int fi[6], nf = 0;
   for (int c = 0; c < 6; ++c) {
     a.ld.free_mask[c] = h->ctrl[c] ? 0 : 1;
-    a.ld.Sigma_m[c] = h->Sigma[c] * kMw[c];
+    a.ld.Sigma_m[c] = h->lin_mode ? 0.0 : h->Sigma[c] * kMw[c];
     if (!h->ctrl[c]) fi[nf++] = c;
   }
   a.ld.any_free = nf > 0;
@@ -728,7 +758,9 @@ struct Rotation {
 
 int max_iter_of(const rve_s* h) { return h->opt.max_iter > 0 ? h->opt.max_iter : 1000; }
 
-int np_of(const rve_s* h) { return rate_variant(h->mat.eta, is_small_int(h->mat.n), is_small_int(h->mat.nt)); }
+int np_of(const rve_s* h) {
+  return h->lin_mode ? kLinearLaw : rate_variant(h->mat.eta, is_small_int(h->mat.n), is_small_int(h->mat.nt));
+}
 
 // One fixed-point iteration (x pass, forward y, z + Green, inverse y) on stream s:
 // strain spectrum si -> so, tau_hat spectra pi -> po.  it < 0: the kernels take the
@@ -1136,6 +1168,158 @@ rve_status step_one(rve_s* h, long long* iters) {
   return st;
 }
 
+// ---------------------------------------------------------------- adjoint ------------
+// Per-voxel scratch of the adjoint of one increment, in units of T per voxel.
+enum AdjSlot {
+  kAdjRvox = 0,                     // 9  rotations per voxel
+  kAdjB = kAdjRvox + 9,             // 36 B of the linear law s = B mu - g
+  kAdjG = kAdjB + 36,               // 6  g
+  kAdjMu = kAdjG + 6,               // 6  adjoint solution mu
+  kAdjSigB = kAdjMu + 6,            // 6  stress adjoint fed to the reverse pass
+  kAdjStB = kAdjSigB + 6,           // 34 state adjoint (direct part)
+  kAdjStZ = kAdjStB + 34,           // 34 state adjoint (constraint part / zero input)
+  kAdjEbA = kAdjStZ + 34,           // 6  d/d eps, direct part
+  kAdjEnA = kAdjEbA + 6,            // 6  d/d eps_prev, direct part
+  kAdjEnB = kAdjEnA + 6,            // 6  d/d eps_prev, constraint part
+  kAdjRbA = kAdjEnB + 6,            // 9
+  kAdjRbB = kAdjRbA + 9,            // 9
+  kAdjPbA = kAdjRbB + 9,            // 9
+  kAdjPbB = kAdjPbA + 9,            // 9
+  kAdjEpsP = kAdjPbB + 9,           // 6  strain at t_{n-1}
+  kAdjEpsC = kAdjEpsP + 6,          // 6  strain at t_n
+  kAdjStP = kAdjEpsC + 6,           // 34 state at t_{n-1}
+  kAdjEbIn = kAdjStP + 34,          // 6  adjoint of the strain at t_n from the next increment
+  kAdjJ = kAdjEbIn + 6,             // 36 tangent rows
+  kAdjDummy = kAdjJ + 36,           // 30 unused outputs (eps_b 6, eps_n_b 6, R_b 9, param_b 9)
+  kAdjTotal = kAdjDummy + 30
+};
+
+template <typename T>
+rve_status adjoint_increment(rve_s* h, const double* eps_prev, const double* eps_cur, const double* state_prev,
+                             const double dS[6], double dt_n, double* state_b, double* eps_b, double* pgrad,
+                             double* egrad, long long* iters) {
+  cudaStream_t s = h->stream;
+  const long long n = h->nvox;
+  const size_t N = (size_t)n;
+  if (!h->adj) {
+    rve_status st = dalloc(h, &h->adj, (size_t)kAdjTotal * N * sizeof(T));
+    if (st) return st;
+  }
+  T* A = (T*)h->adj;
+  auto at = [&](int slot) { return A + (size_t)slot * N; };
+  const MatDev<T> M = make_mat<T>(h);
+  const int np = rate_variant(h->mat.eta, is_small_int(h->mat.n), is_small_int(h->mat.nt));
+  const int nsub = h->opt.n_sub > 0 ? h->opt.n_sub : default_nsub(dt_n);
+  if (nsub > kMaxSubVjp) return fail(h, RVE_ERR_UNSUPPORTED, "adjoint: more than 16 RK4 substeps per increment");
+  const T dt = (T)dt_n;
+  const T* tab = (const T*)h->root_tab;
+  // inputs in the working precision
+  RVE_CUDA(h, launch_adj<T>(4, 6 * n, s, eps_prev, nullptr, nullptr, at(kAdjEpsP), nullptr, nullptr));
+  RVE_CUDA(h, launch_adj<T>(4, 6 * n, s, eps_cur, nullptr, nullptr, at(kAdjEpsC), nullptr, nullptr));
+  RVE_CUDA(h, launch_adj<T>(4, 34 * n, s, state_prev, nullptr, nullptr, at(kAdjStP), nullptr, nullptr));
+  RVE_CUDA(h, launch_adj<T>(4, 34 * n, s, state_b, nullptr, nullptr, at(kAdjStB), nullptr, nullptr));
+  RVE_CUDA(h, launch_adj<T>(4, 6 * n, s, eps_b, nullptr, nullptr, at(kAdjEbIn), nullptr, nullptr));
+  RVE_CUDA(h, launch_adj<T>(0, n, s, h->grain, h->Rg, nullptr, at(kAdjRvox), nullptr, nullptr));
+  // direct part: stress adjoint dS / N everywhere and the state adjoint from later increments
+  double v6[6];
+  for (int c = 0; c < 6; ++c) v6[c] = dS[c] / (double)n;
+  RVE_CUDA(h, launch_adj<T>(1, n, s, nullptr, nullptr, nullptr, at(kAdjSigB), nullptr, v6));
+  RVE_CUDA(h, launch_material_point_vjp<T>(M, np, n, at(kAdjRvox), at(kAdjEpsP), at(kAdjEpsC), at(kAdjStP), dt, nsub,
+                                           at(kAdjSigB), at(kAdjStB), at(kAdjEbA), at(kAdjEnA), at(kAdjRbA),
+                                           at(kAdjPbA), tab, s));
+  // tangent rows d sigma_k / d eps
+  for (int k = 0; k < 6; ++k) {
+    double e6[6] = {0, 0, 0, 0, 0, 0};
+    e6[k] = 1.0;
+    RVE_CUDA(h, launch_adj<T>(1, n, s, nullptr, nullptr, nullptr, at(kAdjSigB), nullptr, e6));
+    RVE_CUDA(h, cudaMemsetAsync(at(kAdjStZ), 0, 34 * N * sizeof(T), s));
+    RVE_CUDA(h, launch_material_point_vjp<T>(M, np, n, at(kAdjRvox), at(kAdjEpsP), at(kAdjEpsC), at(kAdjStP), dt,
+                                             nsub, at(kAdjSigB), at(kAdjStZ), at(kAdjJ) + (size_t)k * 6 * N,
+                                             at(kAdjDummy), at(kAdjDummy) + 6 * N, at(kAdjDummy) + 15 * N, tab, s));
+  }
+  RVE_CUDA(h, launch_adj<T>(2, n, s, at(kAdjJ), at(kAdjEbA), at(kAdjEbIn), at(kAdjB), at(kAdjG), nullptr));
+  // adjoint fixed point: mu compatible with zero controlled macro components, s = B mu - g
+  // equilibrated with zero mean on the free components (the forward iteration, linear law)
+  {
+    const Rotation r(h);
+    const size_t spec_bytes = (size_t)6 * h->NL * h->H * 2 * sizeof(T);
+    RVE_CUDA(h, cudaMemsetAsync(h->spec[r.s0], 0, spec_bytes, s));
+    RVE_CUDA(h, cudaMemsetAsync(h->P[r.p0], 0, spec_bytes, s));
+    std::memset(h->st_host->E[0], 0, sizeof(h->st_host->E[0]));
+    RVE_CUDA(h, cudaMemcpyAsync(h->st->E[0], h->st_host->E[0], 6 * sizeof(double), cudaMemcpyHostToDevice, s));
+    RVE_CUDA(h, cudaMemsetAsync(&h->st->nan_flag, 0, 5 * sizeof(int), s));
+    h->lin_mode = true;
+    h->lin_B = at(kAdjB);
+    h->lin_g = at(kAdjG);
+    h->lin_mu = at(kAdjMu);
+    const int max_iter = max_iter_of(h);
+    int done = 0, last = 0;
+    rve_status st = RVE_OK;
+    for (h->inc_it0 = 0; h->inc_it0 < max_iter && !done; h->inc_it0 += h->inc_nb) {
+      if ((st = enqueue_iterations<T>(h))) break;
+      cudaError_t e = cudaEventSynchronize(h->ev_sync);
+      if (e != cudaSuccess) {
+        st = cuda_fail(h, e, "adjoint iterations");
+        break;
+      }
+      tcollect(h, h->inc_nb);
+      done = h->st_host->done;
+      last = h->st_host->done_it;
+    }
+    if (st == RVE_OK && done == 1) {
+      XArgs<T> ca = x_args<T>(h, h->spec[r.s_in(last)], nullptr, last);
+      cudaError_t e = launch_xpass<T>(ca, kLinearLaw, true, h->xgrid, xsmem_total(h), s);
+      if (e != cudaSuccess) st = cuda_fail(h, e, "adjoint commit");
+    } else if (st == RVE_OK) {
+      st = fail(h, done == 2 ? RVE_ERR_NAN : RVE_ERR_NOT_CONVERGED, "adjoint fixed point did not converge");
+    }
+    h->lin_mode = false;
+    h->lin_B = h->lin_g = nullptr;
+    h->lin_mu = nullptr;
+    if (st) return st;
+    if (iters) *iters += last + 1;
+  }
+  // constraint part: stress adjoint -w mu, no state adjoint
+  RVE_CUDA(h, launch_adj<T>(3, n, s, at(kAdjMu), nullptr, nullptr, at(kAdjSigB), nullptr, nullptr));
+  RVE_CUDA(h, cudaMemsetAsync(at(kAdjStZ), 0, 34 * N * sizeof(T), s));
+  RVE_CUDA(h, launch_material_point_vjp<T>(M, np, n, at(kAdjRvox), at(kAdjEpsP), at(kAdjEpsC), at(kAdjStP), dt, nsub,
+                                           at(kAdjSigB), at(kAdjStZ), at(kAdjDummy), at(kAdjEnB), at(kAdjRbB),
+                                           at(kAdjPbB), tab, s));
+  // outputs: state and strain adjoints at t_{n-1} (double, device)
+  RVE_CUDA(h, launch_adj<T>(5, 34 * n, s, at(kAdjStB), at(kAdjStZ), nullptr, state_b, nullptr, nullptr));
+  RVE_CUDA(h, launch_adj<T>(5, 6 * n, s, at(kAdjEnA), at(kAdjEnB), nullptr, eps_b, nullptr, nullptr));
+  // parameter and rotation adjoints: per-voxel values summed on the host
+  std::vector<T> hb(9 * N);
+  std::vector<double> pv(9, 0.0);
+  for (int part = 0; part < 2; ++part) {
+    RVE_CUDA(h, cudaMemcpyAsync(hb.data(), at(part ? kAdjPbB : kAdjPbA), 9 * N * sizeof(T), cudaMemcpyDeviceToHost, s));
+    RVE_CUDA(h, cudaStreamSynchronize(s));
+    for (int k = 0; k < 9; ++k) {
+      double acc = 0.0;
+      for (size_t i = 0; i < N; ++i) acc += (double)hb[k * N + i];
+      pv[k] += acc;
+    }
+  }
+  for (int k = 0; k < 9; ++k) pgrad[k] += pv[k];
+  std::vector<double> Rb((size_t)h->n_grains * 9, 0.0);
+  for (int part = 0; part < 2; ++part) {
+    RVE_CUDA(h, cudaMemcpyAsync(hb.data(), at(part ? kAdjRbB : kAdjRbA), 9 * N * sizeof(T), cudaMemcpyDeviceToHost, s));
+    RVE_CUDA(h, cudaStreamSynchronize(s));
+    for (int k = 0; k < 9; ++k)
+      for (size_t i = 0; i < N; ++i) Rb[(size_t)h->gid_host[i] * 9 + k] += (double)hb[k * N + i];
+  }
+  for (int g = 0; g < h->n_grains; ++g) {
+    double dR[3][9];
+    bunge_grad(&h->euler[3 * g], dR);
+    for (int k = 0; k < 3; ++k) {
+      double acc = 0.0;
+      for (int i = 0; i < 9; ++i) acc += Rb[(size_t)g * 9 + i] * dR[k][i];
+      egrad[3 * g + k] += acc;
+    }
+  }
+  return RVE_OK;
+}
+
 bool valid_len(int n) {
   FftDim d;
   return n >= 1 && factor_radices(n, &d);
@@ -1276,6 +1460,7 @@ rve_status rve_create(rve_t* out, int nx, int ny, int nz, const uint32_t* grain_
   }
   for (uint32_t g : gid)
     if (g >= (uint32_t)n_grains) { s = fail(h, RVE_ERR_INVALID_ARG, "grain id >= n_grains"); rve_destroy(h); return s; }
+  h->gid_host = gid;
   if ((s = dalloc(h, (void**)&h->grain, gid.size() * 4))) { rve_destroy(h); return s; }
   e = cudaMemcpyAsync(h->grain, gid.data(), gid.size() * 4, cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -1433,6 +1618,23 @@ rve_status rve_step_batch(rve_t* hs, int n, int n_increments, long long* iters, 
   if (failed) *failed = first_i;
   if (first != RVE_OK) g_err = "handle " + std::to_string(first_i) + ": " + hs[first_i]->err;
   return first;
+}
+
+rve_status rve_adjoint_increment(rve_t h, const double* eps_prev, const double* eps_cur, const double* state_prev,
+                                 const double dS[6], double dt, double* state_b, double* eps_b, double* param_grad,
+                                 double* euler_grad, long long* iterations_out) {
+  if (!h) return fail(h, RVE_ERR_INVALID_ARG, "NULL handle");
+  if (!eps_prev || !eps_cur || !state_prev || !dS || !state_b || !eps_b || !param_grad || !euler_grad ||
+      !(dt > 0))
+    return fail(h, RVE_ERR_INVALID_ARG, "bad adjoint arguments");
+  cudaError_t e = cudaSetDevice(h->opt.device);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+  drop_graphs(h);  // the adjoint solve reuses the spectra; the forward state is not kept
+  return h->opt.precision == RVE_FP64
+             ? adjoint_increment<double>(h, eps_prev, eps_cur, state_prev, dS, dt, state_b, eps_b, param_grad,
+                                         euler_grad, iterations_out)
+             : adjoint_increment<float>(h, eps_prev, eps_cur, state_prev, dS, dt, state_b, eps_b, param_grad,
+                                        euler_grad, iterations_out);
 }
 
 rve_status rve_get_effective(rve_t h, rve_effective* last, rve_effective* hist, int cap, int* n_hist) {

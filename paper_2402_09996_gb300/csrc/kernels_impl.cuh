@@ -60,6 +60,10 @@ cudaError_t launch_material_point_vjp_np(const MatDev<T>& M, long long nvox, con
   return cudaGetLastError();
 }
 
+// the linear-law x pass alone (no material-point kernels)
+#define RVE_INSTANTIATE_XLIN(T) \
+  template cudaError_t launch_xpass_np<T, kLinearLaw>(const XArgs<T>&, bool, int, size_t, cudaStream_t);
+
 #define RVE_INSTANTIATE_X(T, NP)                                                                                \
   template cudaError_t launch_xpass_np<T, NP>(const XArgs<T>&, bool, int, size_t, cudaStream_t);              \
   template cudaError_t launch_material_point_np<T, NP>(const MatDev<T>&, long long, const T*, const T*, const T*, \
@@ -170,6 +174,84 @@ cudaError_t launch_von_mises(const T* sig6, double* dst, long long nvox, cudaStr
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- adjoint helpers ----
+template <typename T>
+__global__ void k_adj_gather_R(const uint32_t* __restrict__ grain, const T* __restrict__ Rg, T* __restrict__ Rvox,
+                               long long nvox) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nvox) return;
+  const uint32_t g = grain[i];
+  for (int k = 0; k < 9; ++k) Rvox[(size_t)i * 9 + k] = Rg[(size_t)g * 9 + k];
+}
+
+// out[c * nvox + i] = v[c] for all voxels (a uniform 6-vector field)
+template <typename T>
+__global__ void k_adj_fill6(T* out, double v0, double v1, double v2, double v3, double v4, double v5, long long nvox) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nvox) return;
+  const double v[6] = {v0, v1, v2, v3, v4, v5};
+  for (int c = 0; c < 6; ++c) out[c * (size_t)nvox + i] = (T)v[c];
+}
+
+// Mandel-free pairing weights of the six components: the double contraction a : b of two
+// symmetric tensors in (11 22 33 23 13 12) storage is sum_c w_c a_c b_c, w = (1 1 1 2 2 2).
+__device__ __forceinline__ double adj_w(int c) { return c < 3 ? 1.0 : 2.0; }
+
+// B(r, c) = J(c, r) w_c / w_r from the tangent rows J(k, .) = d sigma_k / d eps (the
+// transposed tangent acting on tensors, in 6-component storage); g(r) = (e_a(r) + e_b(r)) / w_r.
+template <typename T>
+__global__ void k_adj_build(const T* __restrict__ Jrows, const T* __restrict__ ea, const T* __restrict__ eb,
+                            T* __restrict__ B, T* __restrict__ g, long long nvox) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nvox) return;
+  const size_t n = (size_t)nvox;
+  for (int r = 0; r < 6; ++r) {
+    for (int c = 0; c < 6; ++c)
+      B[(r * 6 + c) * n + i] = (T)((double)Jrows[(c * 6 + r) * n + i] * adj_w(c) / adj_w(r));
+    g[r * n + i] = (T)(((double)ea[r * n + i] + (double)eb[r * n + i]) / adj_w(r));
+  }
+}
+
+// sigma_b = -w mu (the stress adjoint of the equilibrium constraint)
+template <typename T>
+__global__ void k_adj_neg_w(const T* __restrict__ mu, T* __restrict__ sb, long long nvox) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nvox) return;
+  for (int c = 0; c < 6; ++c) sb[c * (size_t)nvox + i] = (T)(-adj_w(c) * (double)mu[c * (size_t)nvox + i]);
+}
+
+template <typename T>
+__global__ void k_adj_from_double(const double* __restrict__ src, T* __restrict__ dst, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = (T)src[i];
+}
+
+// dst = (double)(a + b)
+template <typename T>
+__global__ void k_adj_sum_to_double(const T* __restrict__ a, const T* __restrict__ b, double* __restrict__ dst,
+                                    long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = (double)a[i] + (double)b[i];
+}
+
+template <typename T>
+cudaError_t launch_adj(int which, long long n, cudaStream_t s, const void* p0, const void* p1, const void* p2,
+                       void* q0, void* q1, const double* v) {
+  const int thr = 256;
+  const unsigned grid = (unsigned)((n + thr - 1) / thr);
+  if (n <= 0) return cudaSuccess;
+  switch (which) {
+    case 0: k_adj_gather_R<T><<<grid, thr, 0, s>>>((const uint32_t*)p0, (const T*)p1, (T*)q0, n); break;
+    case 1: k_adj_fill6<T><<<grid, thr, 0, s>>>((T*)q0, v[0], v[1], v[2], v[3], v[4], v[5], n); break;
+    case 2: k_adj_build<T><<<grid, thr, 0, s>>>((const T*)p0, (const T*)p1, (const T*)p2, (T*)q0, (T*)q1, n); break;
+    case 3: k_adj_neg_w<T><<<grid, thr, 0, s>>>((const T*)p0, (T*)q0, n); break;
+    case 4: k_adj_from_double<T><<<grid, thr, 0, s>>>((const double*)p0, (T*)q0, n); break;
+    case 5: k_adj_sum_to_double<T><<<grid, thr, 0, s>>>((const T*)p0, (const T*)p1, (double*)q0, n); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 #define RVE_INSTANTIATE(T)                                                                                         \
   template cudaError_t launch_line<T>(const LineArgs<T>&, int, dim3, size_t, cudaStream_t);                       \
   template cudaError_t launch_zgreen<T>(const ZArgs<T>&, dim3, size_t, cudaStream_t);                             \
@@ -177,6 +259,8 @@ cudaError_t launch_von_mises(const T* sig6, double* dst, long long nvox, cudaStr
   template cudaError_t launch_xfft<T>(const XFftArgs<T>&, int, dim3, size_t, cudaStream_t);                       \
   template cudaError_t launch_to_double<T>(const T*, double*, long long, cudaStream_t);                           \
   template cudaError_t launch_von_mises<T>(const T*, double*, long long, cudaStream_t);                          \
-  template cudaError_t launch_loop_guard<T>(IterStatus*, int, cudaGraphConditionalHandle, cudaStream_t);
+  template cudaError_t launch_loop_guard<T>(IterStatus*, int, cudaGraphConditionalHandle, cudaStream_t);           \
+  template cudaError_t launch_adj<T>(int, long long, cudaStream_t, const void*, const void*, const void*, void*,   \
+                                     void*, const double*);
 
 }  // namespace rve

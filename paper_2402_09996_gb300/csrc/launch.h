@@ -49,6 +49,7 @@ cudaError_t launch_material_point_vjp(const MatDev<T>& M, int np, long long nvox
 template <typename T>
 cudaError_t launch_xpass(const XArgs<T>& a, int np, bool commit, int grid, size_t smem, cudaStream_t s) {
   if (np == 10) return launch_xpass_np<T, 10>(a, commit, grid, smem, s);
+  if (np == kLinearLaw) return launch_xpass_np<T, kLinearLaw>(a, commit, grid, smem, s);
   if (np < 0) return launch_xpass_np<T, -1>(a, commit, grid, smem, s);
   return launch_xpass_np<T, 0>(a, commit, grid, smem, s);
 }
@@ -75,6 +76,11 @@ template <typename T>
 cudaError_t launch_von_mises(const T* sig6, double* dst, long long nvox, cudaStream_t s);
 template <typename T>
 cudaError_t launch_loop_guard(IterStatus* st, int limit, cudaGraphConditionalHandle cond, cudaStream_t s);
+// adjoint helpers (kernels_impl.cuh): 0 gather per-voxel R, 1 fill a uniform 6-vector field,
+// 2 build B and g, 3 sigma_b = -w mu, 4 double -> T copy, 5 T + T -> double sum
+template <typename T>
+cudaError_t launch_adj(int which, long long n, cudaStream_t s, const void* p0, const void* p1, const void* p2,
+                       void* q0, void* q1, const double* v);
 
 int x_threads();
 int line_threads();

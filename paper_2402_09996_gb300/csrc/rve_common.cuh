@@ -99,6 +99,9 @@ constexpr double kRootPerUnit = kRootIv / (2.0 * kRootSpan);
 constexpr int kRootTabLen = 2 * kRootIv;  // values per table
 constexpr int kRootTabs = 2 * kRootTabLen;  // slip systems' table, then the twin exponent's
 
+// Template value of the x pass's linear-law mode (the adjoint solve): s = B eps - g per voxel.
+constexpr int kLinearLaw = 1;
+
 // RK4 substeps whose start states the constitutive reverse pass (adjoint.cuh) keeps.
 constexpr int kMaxSubVjp = 16;
 

@@ -110,6 +110,10 @@ struct XArgs {
   // of the converged iteration it* (cand[0] for it* = 0, cand[1] for odd, cand[2] for even)
   int pick;
   const C2<T>* cand[3];
+  // linear-law mode (NP == kLinearLaw, the adjoint solve): s = B eps - g per voxel,
+  // B 36 x nvox (entry (r, c) at (r * 6 + c) * nvox + voxel), g 6 x nvox
+  const T* lin_B;
+  const T* lin_g;
 };
 
 constexpr int kXThreads = 128;
@@ -144,7 +148,7 @@ __global__ void __launch_bounds__(kXThreads, XMinBlocks<T>::value) k_xpass(const
   }
 
   for (int i = tid; i < nx; i += nthr) tw[i] = a.tw[i];
-  if (NP != 0)
+  if (NP != 0 && NP != kLinearLaw)
     for (int i = tid; i < kRootTabs; i += nthr) tab[i] = a.root_tab[i];
   // pack component pairs (2p, 2p+1) of each line as one complex Hermitian-extended
   // sequence Z = A + iB, so one complex inverse FFT yields both real lines
@@ -183,40 +187,61 @@ __global__ void __launch_bounds__(kXThreads, XMinBlocks<T>::value) k_xpass(const
       eps[2 * p] = z.x;
       eps[2 * p + 1] = z.y;
     }
+    if constexpr (NP == kLinearLaw) {
+      (void)epsn;
+      (void)R;
 #pragma unroll
-    for (int c = 0; c < 6; ++c) epsn[c] = a.eps_n[c * nvox + vox];
-    MPState<T> y;
+      for (int r = 0; r < 6; ++r) {
+        T sr = -a.lin_g[r * nvox + vox];
 #pragma unroll
-    for (int c = 0; c < 6; ++c) y.ep[c] = a.ep[c * nvox + vox];
-#pragma unroll
-    for (int c = 0; c < 16; ++c) y.v[c] = a.v[c * nvox + vox];
-#pragma unroll
-    for (int c = 0; c < 12; ++c) y.al[c] = a.al[c * nvox + vox];
-    const uint32_t g = a.grain[vox];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) R[i] = a.Rg[(size_t)g * 9 + i];
-    mc_voxel<T, NP>(a.M, R, epsn, eps, y, a.dt, a.nsub, sig, tab);
-#pragma unroll
-    for (int c = 0; c < 6; ++c) acc[c] += (double)sig[c];
-    if (COMMIT) {
-#pragma unroll
-      for (int c = 0; c < 6; ++c) a.ep[c * nvox + vox] = y.ep[c];
-#pragma unroll
-      for (int c = 0; c < 16; ++c) a.v[c * nvox + vox] = y.v[c];
-#pragma unroll
-      for (int c = 0; c < 12; ++c) a.al[c * nvox + vox] = y.al[c];
-#pragma unroll
-      for (int c = 0; c < 6; ++c) {
-        a.eps_n[c * nvox + vox] = eps[c];
-        a.sig_n[c * nvox + vox] = sig[c];
+        for (int c = 0; c < 6; ++c) sr += a.lin_B[(r * 6 + c) * nvox + vox] * eps[c];
+        sig[r] = sr;
       }
-      acc[6] += (double)von_mises6<T>(sig);
-      acc[7] += 1.41421356237309504880 * ((double)y.v[12] + (double)y.v[13] + (double)y.v[14] + (double)y.v[15]);
-      double vs = 0.0;
 #pragma unroll
-      for (int c = 0; c < 12; ++c) vs += (double)y.v[c];
-      acc[8] += vs;
+      for (int c = 0; c < 6; ++c) acc[c] += (double)sig[c];
+      if (COMMIT) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) a.eps_n[c * nvox + vox] = eps[c];
+        continue;
+      }
     } else {
+  #pragma unroll
+      for (int c = 0; c < 6; ++c) epsn[c] = a.eps_n[c * nvox + vox];
+      MPState<T> y;
+  #pragma unroll
+      for (int c = 0; c < 6; ++c) y.ep[c] = a.ep[c * nvox + vox];
+  #pragma unroll
+      for (int c = 0; c < 16; ++c) y.v[c] = a.v[c * nvox + vox];
+  #pragma unroll
+      for (int c = 0; c < 12; ++c) y.al[c] = a.al[c * nvox + vox];
+      const uint32_t g = a.grain[vox];
+  #pragma unroll
+      for (int i = 0; i < 9; ++i) R[i] = a.Rg[(size_t)g * 9 + i];
+      mc_voxel<T, NP>(a.M, R, epsn, eps, y, a.dt, a.nsub, sig, tab);
+  #pragma unroll
+      for (int c = 0; c < 6; ++c) acc[c] += (double)sig[c];
+      if (COMMIT) {
+  #pragma unroll
+        for (int c = 0; c < 6; ++c) a.ep[c * nvox + vox] = y.ep[c];
+  #pragma unroll
+        for (int c = 0; c < 16; ++c) a.v[c * nvox + vox] = y.v[c];
+  #pragma unroll
+        for (int c = 0; c < 12; ++c) a.al[c * nvox + vox] = y.al[c];
+  #pragma unroll
+        for (int c = 0; c < 6; ++c) {
+          a.eps_n[c * nvox + vox] = eps[c];
+          a.sig_n[c * nvox + vox] = sig[c];
+        }
+        acc[6] += (double)von_mises6<T>(sig);
+        acc[7] += 1.41421356237309504880 * ((double)y.v[12] + (double)y.v[13] + (double)y.v[14] + (double)y.v[15]);
+        double vs = 0.0;
+  #pragma unroll
+        for (int c = 0; c < 12; ++c) vs += (double)y.v[c];
+        acc[8] += vs;
+        continue;
+      }
+    }
+    {
       const T tr = a.M.lam0 * (eps[0] + eps[1] + eps[2]);
       const T m2 = T(2) * a.M.mu0;
       T tau[6];

@@ -117,7 +117,7 @@ EXPORTED = [
     "rve_set_mixed_load", "rve_step", "rve_get_effective", "rve_get_fields", "rve_save_state",
     "rve_load_state", "rve_last_error", "rve_destroy", "rve_material_point", "rve_fft_r2c",
     "rve_fft_c2r", "rve_label_voronoi", "rve_kernel_times", "rve_get_residuals", "rve_label_voronoi_noalloc",
-    "rve_step_batch", "rve_material_point_vjp",
+    "rve_step_batch", "rve_material_point_vjp", "rve_adjoint_increment",
 ]
 NOALLOC_MAX_PARENTS = 4096  # RVE_NOALLOC_MAX_PARENTS of include/rve.h
 
@@ -156,6 +156,8 @@ def load_library(path: str | os.PathLike | None = None):
     lib.rve_step_batch.argtypes = [C.POINTER(vp), i, i, C.POINTER(C.c_longlong), C.POINTER(i)]
     lib.rve_material_point_vjp.argtypes = [i, C.POINTER(Material), C.c_longlong, vp, vp, vp, vp, vp, vp, vp, vp, vp,
                                            vp, d, i, vp]
+    lib.rve_adjoint_increment.argtypes = [vp, vp, vp, vp, C.POINTER(C.c_double), d, vp, vp, C.POINTER(C.c_double),
+                                          C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
     for name in EXPORTED:
         getattr(lib, name).restype = C.c_int
     lib.rve_options_default.restype = None
@@ -427,6 +429,115 @@ def material_point_vjp(R, eps_n, eps, state, sigma_b, state_b, dt, n_sub, precis
                                     _ptr(param_b), float(dt), int(n_sub), _torch_stream())
     _check(st, None)
     return eps_b, eps_n_b, R_b, param_b
+
+
+PARAM_NAMES = ["r0_ord", "r0_sup", "r0_twin", "Q_s", "Q_b", "b_s", "b_b", "c", "d"]
+
+
+def history_gradient(grain_id, euler, n_increments, dt, target, weights=None, precision=FP64, material=None,
+                     Edot=(0, 0, 1e-3, 0, 0, 0), checkpoint_every=5, **options):
+    """Misfit J = sum_n w_n (<sigma_zz>_n - target_n)^2 of a load history and its gradient
+    with respect to the parameters PARAM_NAMES and every grain's Bunge angles, by the
+    adjoint of the history (rve_adjoint_increment), with the state checkpointed every
+    `checkpoint_every` increments and replayed segment by segment in the reverse pass.
+    Returns (J, dJ/dparams (9,), dJ/deuler (n_grains, 3), info)."""
+    import torch
+
+    lib = load_library()
+    material = dict(material or {})
+    euler = np.ascontiguousarray(np.asarray(euler, dtype=np.float64))
+    target = np.asarray(target, dtype=np.float64)
+    w = np.ones(n_increments) if weights is None else np.asarray(weights, dtype=np.float64)
+
+    def make():
+        s = RVE(grain_id, euler, precision=precision, **options)
+        if material:
+            s.set_material(**material)
+        s.set_mixed_load(Edot=Edot, dt=dt)
+        return s
+
+    fwd = make()
+    nvox = fwd.nvox
+    ckpt = {0: fwd.save_state()}
+    S = []
+    for k in range(1, n_increments + 1):
+        fwd.step(1)
+        S.append(fwd.history()[-1]["S"].copy())
+        if k % checkpoint_every == 0 and k < n_increments:
+            ckpt[k] = fwd.save_state()
+    fwd.close()
+    S = np.array(S)
+    J = float(np.sum(w * (S[:, 2] - target) ** 2))
+    dS = np.zeros((n_increments, 6))
+    dS[:, 2] = 2.0 * w * (S[:, 2] - target)
+    dev = torch.device("cuda", options.get("device", 0))
+    state_b = torch.zeros((34, nvox), dtype=torch.float64, device=dev)
+    eps_b = torch.zeros((6, nvox), dtype=torch.float64, device=dev)
+    pgrad = (C.c_double * 9)()
+    egrad = (C.c_double * euler.size)()
+    adj_iters = C.c_longlong(0)
+    adj = make()
+    rep = make()
+    starts = sorted(ckpt)
+    for seg, k0 in reversed(list(enumerate(starts))):
+        k1 = starts[seg + 1] if seg + 1 < len(starts) else n_increments
+        # replay the segment from its checkpoint, keeping strain and state at k0 .. k1
+        rep.load_state(ckpt[k0])
+        fields = []
+        for k in range(k0, k1 + 1):
+            if k > k0:
+                rep.step(1)
+            eps = rep.field(FIELD_STRAIN, out=torch.empty((6,) + rep.shape, dtype=torch.float64, device=dev))
+            st = torch.cat([rep.field(f, out=torch.empty((FIELD_COMPONENTS[f],) + rep.shape, dtype=torch.float64,
+                                                         device=dev)).reshape(-1, nvox)
+                            for f in (FIELD_EPS_P, FIELD_V, FIELD_ALPHA)]).contiguous()
+            fields.append((eps.reshape(6, nvox).contiguous(), st))
+        for k in range(k1, k0, -1):
+            e_prev, s_prev = fields[k - 1 - k0]
+            e_cur, _ = fields[k - k0]
+            d6 = (C.c_double * 6)(*dS[k - 1])
+            _check(lib.rve_adjoint_increment(adj.h, _ptr(e_prev), _ptr(e_cur), _ptr(s_prev), d6, float(dt),
+                                             _ptr(state_b), _ptr(eps_b), pgrad, egrad, C.byref(adj_iters)), adj.h)
+    adj.close()
+    rep.close()
+    info = {"S": S, "adjoint_iterations": int(adj_iters.value), "checkpoints": starts}
+    return J, np.array(pgrad[:]), np.array(egrad[:]).reshape(euler.shape), info
+
+
+class HistoryMisfit:
+    """torch.autograd.Function for the load-history misfit: apply(params (9,), euler
+    (n_grains, 3), config dict) -> J, with the adjoint gradient in backward.  `config`
+    holds grain_id, n_increments, dt, target and optional weights, precision, material,
+    Edot, checkpoint_every and solver options."""
+
+    @staticmethod
+    def _fn():
+        import torch
+
+        class _F(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, params, euler, config):
+                mat = dict(config.get("material", {}))
+                mat.update({k: float(v) for k, v in zip(PARAM_NAMES, params.detach().cpu().tolist())})
+                cfg = {k: v for k, v in config.items() if k not in ("grain_id", "n_increments", "dt", "target",
+                                                                   "material")}
+                J, gp, ge, _ = history_gradient(config["grain_id"], euler.detach().cpu().numpy(),
+                                                config["n_increments"], config["dt"], config["target"],
+                                                material=mat, **cfg)
+                ctx.save_for_backward(torch.as_tensor(gp, dtype=params.dtype),
+                                      torch.as_tensor(ge, dtype=euler.dtype))
+                return torch.tensor(J, dtype=params.dtype)
+
+            @staticmethod
+            def backward(ctx, g):
+                gp, ge = ctx.saved_tensors
+                return g * gp, g * ge, None
+
+        return _F
+
+    @classmethod
+    def apply(cls, params, euler, config):
+        return cls._fn().apply(params, euler, config)
 
 
 def fft_r2c(real, precision=FP64):

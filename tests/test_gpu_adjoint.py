@@ -94,3 +94,52 @@ def test_material_point_vjp_matches_oracle_finite_differences(lib, cuda, which):
                                                al, dt, nsub)
     active = np.any(v1 > v, axis=1)
     assert 0.2 < active.mean() < 0.95
+
+
+def _history_J(gid, euler, mat, target, n_inc, dt, **opts):
+    from paper_2402_09996_gb300 import rve
+
+    with rve.RVE(gid, euler, precision=rve.FP64, **opts) as s:
+        if mat:
+            s.set_material(**mat)
+        s.set_mixed_load(dt=dt)
+        s.step(n_inc)
+        S33 = np.array([h["S"][2] for h in s.history()])
+    return float(np.sum((S33 - target) ** 2)), S33
+
+
+def test_load_history_gradient_matches_finite_differences(lib, cuda):
+    """Adjoint of a 4-increment history (checkpoints every 2 increments, replayed) for
+    J = sum_n (<sigma_zz>_n - target_n)^2: gradient in the 9 material parameters and the
+    Bunge angles of two grains against central differences of the forward solve."""
+    from oracle.voronoi import label_rve
+
+    from paper_2402_09996_gb300 import inputs, rve
+
+    inp = inputs.make_inputs((8, 10, 12), 4, 0.0, seed=21)
+    gid = label_rve(inp)
+    euler = inp.euler[:4].copy()
+    n_inc, dt = 4, 0.5
+    opts = dict(tol=1e-12, max_iter=3000)
+    _, S0 = _history_J(gid, euler, {}, np.zeros(n_inc), n_inc, dt, **opts)
+    target = 0.97 * S0
+    J, gp, ge, info = rve.history_gradient(gid, euler, n_inc, dt, target, checkpoint_every=2, **opts)
+    assert abs(J - float(np.sum((S0 - target) ** 2))) < 1e-9 * J
+    assert info["checkpoints"] == [0, 2]
+    base = orc.Material()
+    for k, name in enumerate(rve.PARAM_NAMES):
+        p0 = getattr(base, name)
+        h = 1e-5 * abs(p0)
+        jp, _ = _history_J(gid, euler, {name: p0 + h}, target, n_inc, dt, **opts)
+        jm, _ = _history_J(gid, euler, {name: p0 - h}, target, n_inc, dt, **opts)
+        num = (jp - jm) / (2 * h)
+        assert abs(num - gp[k]) <= 1e-4 * max(abs(num), abs(gp[k])) + 1e-9 * J / abs(p0), (name, num, gp[k])
+    for g in (0, 1):
+        for a in range(3):
+            h = 1e-5
+            ep, em = euler.copy(), euler.copy()
+            ep[g, a] += h
+            em[g, a] -= h
+            num = (_history_J(gid, ep, {}, target, n_inc, dt, **opts)[0] -
+                   _history_J(gid, em, {}, target, n_inc, dt, **opts)[0]) / (2 * h)
+            assert abs(num - ge[g, a]) <= 1e-4 * max(abs(num), abs(ge[g, a])) + 1e-9 * J, (g, a, num, ge[g, a])

@@ -542,6 +542,60 @@ def run_eta_sweep(args):
     print(json.dumps({"metric": "single-crystal response vs eta (Sec. 4)", "rows": rows}))
 
 
+def run_adjoint(args):
+    """Adjoint calibration workload: 96^3 RVE, 300 Voronoi grains twinned with p = 0.5, FP32
+    forward and adjoint, --steps increments of 0.5 s (30 = 1.5 % strain), checkpoints every 5
+    increments.  The target sigma_zz curve comes from the same RVE with r0 raised by 10 %;
+    J = sum_n (<sigma_zz>_n - target_n)^2.  Prints the forward time, the gradient time
+    (forward with checkpoints + segment replays + adjoint) and their ratio, J and the
+    parameter gradient."""
+    import torch
+
+    from paper_2402_09996_gb300 import build_lib, inputs, rve
+
+    build_lib.build()
+    inp = inputs.make_inputs((96, 96, 96), 300, 0.5, seed=1000 * 4 + 0)
+    gid = rve.label_voronoi(inp)
+    n_inc, dt = args.steps, 0.5
+    base = rve.default_material().as_dict()
+    perturbed = {k: 1.1 * base[k] for k in ("r0_ord", "r0_sup", "r0_twin")}
+
+    def forward(mat):
+        with rve.RVE(gid, inp.euler, precision=rve.FP32) as s:
+            if mat:
+                s.set_material(**mat)
+            s.set_mixed_load(dt=dt)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            its = s.step(n_inc)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            return np.array([h["S"][2] for h in s.history()]), t1 - t0, its
+
+    target, _, _ = forward(perturbed)
+    S, t_fwd, its = forward({})
+    torch.cuda.synchronize()
+    g0 = time.perf_counter()
+    J, gp, ge, info = rve.history_gradient(gid, inp.euler, n_inc, dt, target, precision=rve.FP32,
+                                           checkpoint_every=5)
+    torch.cuda.synchronize()
+    t_grad = time.perf_counter() - g0
+    line = {
+        "metric": "adjoint/forward time",
+        "value": t_grad / t_fwd,
+        "unit": "ratio",
+        "higher_is_better": False,
+        "workload": "twinned RVE 96^3, 300 Voronoi grains (p_twin 0.5), FP32 forward and adjoint, "
+                    f"{n_inc} increments of 0.5 s, checkpoints every 5; target from r0 + 10 %",
+        "seconds": {"forward": t_fwd, "gradient": t_grad},
+        "forward_iterations": its, "adjoint_iterations": info["adjoint_iterations"],
+        "J": J, "dJ_dparams": dict(zip(rve.PARAM_NAMES, gp.tolist())),
+        "dJ_deuler_norm": float(np.linalg.norm(ge)),
+        "S33_final": {"model": float(S[-1]), "target": float(target[-1])},
+    }
+    print(json.dumps(line))
+
+
 def run_profile_case(args):
     """A small case for `ncu --profile-from-start off`: the kernels of --steps increments in
     the plastic regime, on inputs of a few hundred MB, after --warmup untimed increments."""
@@ -574,7 +628,7 @@ def main_args(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="twinned128",
-                    choices=["twinned128", "ensemble", "precision256", "paper", "eta"],
+                    choices=["twinned128", "ensemble", "precision256", "paper", "eta", "adjoint"],
                     help="ensemble: the 16-RVE batched workload; precision256: FP32 vs FP64 on the 256^3 RVE "
                          "over --steps increments (each prints its own JSON line)")
     ap.add_argument("--twins", default="neigh", choices=["neigh", "incl", "none"],
@@ -605,6 +659,8 @@ def main():
         run_paper(args)
     elif args.workload == "eta":
         run_eta_sweep(args)
+    elif args.workload == "adjoint":
+        run_adjoint(args)
     else:
         run_gpu(args)
 

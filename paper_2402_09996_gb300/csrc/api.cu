@@ -266,6 +266,7 @@ struct rve_s {
   const void* lin_B = nullptr;
   const void* lin_g = nullptr;
   void* lin_mu = nullptr;
+  double lin_sref = 0.0;  // source scale of the adjoint fixed point (floor of the error norms)
   // FFT tile autotuner (opt.autotune): runs once, before the first increment
   bool tuned = false;
   IterStatus* st_tune = nullptr;  // scratch status and history for timing the z pass
@@ -640,6 +641,7 @@ XArgs<T> x_args(rve_s* h, const void* in, void* out, int it) {
     if (!h->ctrl[c]) fi[nf++] = c;
   }
   a.ld.any_free = nf > 0;
+  a.ld.s_ref = h->lin_mode ? h->lin_sref : 0.0;
   if (nf > 0) {
     std::vector<double> Mff(nf * nf);
     for (int i = 0; i < nf; ++i)
@@ -698,6 +700,7 @@ ZArgs<T> z_args(rve_s* h, void* spec, const void* Pp, void* Po, int it) {
   a.conv.fixed_iters = h->opt.fixed_iters;
   a.conv.max_iter = h->opt.max_iter > 0 ? h->opt.max_iter : 1000;
   a.conv.hist = h->dhist;
+  a.conv.s_ref = h->lin_mode ? h->lin_sref : 0.0;
   a.done = &h->st->done;
   a.partial = h->partial;
   a.counter = h->counter;
@@ -1238,9 +1241,28 @@ rve_status adjoint_increment(rve_s* h, const double* eps_prev, const double* eps
                                              at(kAdjDummy), at(kAdjDummy) + 6 * N, at(kAdjDummy) + 15 * N, tab, s));
   }
   RVE_CUDA(h, launch_adj<T>(2, n, s, at(kAdjJ), at(kAdjEbA), at(kAdjEbIn), at(kAdjB), at(kAdjG), nullptr));
-  // adjoint fixed point: mu compatible with zero controlled macro components, s = B mu - g
-  // equilibrated with zero mean on the free components (the forward iteration, linear law)
+  // source scale |g|_rms = sqrt(<g : g>): per-block partial sums (into the unused-output
+  // slot, free until the constraint part) added on the host in a fixed order
+  double g_rms = 0.0;
   {
+    const size_t nb = (N + 255) / 256;
+    std::vector<double> part(nb);
+    RVE_CUDA(h, launch_adj<T>(6, n, s, at(kAdjG), nullptr, nullptr, at(kAdjDummy), nullptr, nullptr));
+    RVE_CUDA(h, cudaMemcpyAsync(part.data(), at(kAdjDummy), nb * sizeof(double), cudaMemcpyDeviceToHost, s));
+    RVE_CUDA(h, cudaStreamSynchronize(s));
+    double q = 0.0;
+    for (double x : part) q += x;
+    if (!std::isfinite(q)) return fail(h, RVE_ERR_NAN, "adjoint: non-finite source");
+    g_rms = std::sqrt(q / (double)n);
+  }
+  // adjoint fixed point: mu compatible with zero controlled macro components, s = B mu - g
+  // equilibrated with zero mean on the free components (the forward iteration, linear law).
+  // Its relative errors are taken against max(|<s>|, |g|_rms): the mean of s alone can
+  // vanish (it does exactly when g = 0, e.g. an elastic increment without misfit).  With
+  // g = 0 the solution is mu = 0 and no iteration runs.
+  if (g_rms == 0.0) {
+    RVE_CUDA(h, cudaMemsetAsync(at(kAdjMu), 0, 6 * N * sizeof(T), s));
+  } else {
     const Rotation r(h);
     const size_t spec_bytes = (size_t)6 * h->NL * h->H * 2 * sizeof(T);
     RVE_CUDA(h, cudaMemsetAsync(h->spec[r.s0], 0, spec_bytes, s));
@@ -1249,6 +1271,7 @@ rve_status adjoint_increment(rve_s* h, const double* eps_prev, const double* eps
     RVE_CUDA(h, cudaMemcpyAsync(h->st->E[0], h->st_host->E[0], 6 * sizeof(double), cudaMemcpyHostToDevice, s));
     RVE_CUDA(h, cudaMemsetAsync(&h->st->nan_flag, 0, 5 * sizeof(int), s));
     h->lin_mode = true;
+    h->lin_sref = g_rms;
     h->lin_B = at(kAdjB);
     h->lin_g = at(kAdjG);
     h->lin_mu = at(kAdjMu);
@@ -1276,6 +1299,7 @@ rve_status adjoint_increment(rve_s* h, const double* eps_prev, const double* eps
     h->lin_mode = false;
     h->lin_B = h->lin_g = nullptr;
     h->lin_mu = nullptr;
+    h->lin_sref = 0.0;
     if (st) return st;
     if (iters) *iters += last + 1;
   }

@@ -234,6 +234,28 @@ __global__ void k_adj_sum_to_double(const T* __restrict__ a, const T* __restrict
   if (i < n) dst[i] = (double)a[i] + (double)b[i];
 }
 
+// Per-block partial sums of the tensor norm^2 of a 6-component field,
+// sum_i f_c(i)^2 w_c (w = 1 1 1 2 2 2), in double and a fixed order: out[blockIdx.x].
+template <typename T>
+__global__ void k_adj_norm2(const T* __restrict__ f, double* __restrict__ out, long long nvox) {
+  __shared__ double red[256 / 32];
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double q = 0.0;
+  if (i < nvox)
+    for (int c = 0; c < 6; ++c) {
+      const double x = (double)f[c * (size_t)nvox + i];
+      q += adj_w(c) * x * x;
+    }
+  for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = q;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    out[blockIdx.x] = t;
+  }
+}
+
 template <typename T>
 cudaError_t launch_adj(int which, long long n, cudaStream_t s, const void* p0, const void* p1, const void* p2,
                        void* q0, void* q1, const double* v) {
@@ -247,6 +269,7 @@ cudaError_t launch_adj(int which, long long n, cudaStream_t s, const void* p0, c
     case 3: k_adj_neg_w<T><<<grid, thr, 0, s>>>((const T*)p0, (T*)q0, n); break;
     case 4: k_adj_from_double<T><<<grid, thr, 0, s>>>((const double*)p0, (T*)q0, n); break;
     case 5: k_adj_sum_to_double<T><<<grid, thr, 0, s>>>((const T*)p0, (const T*)p1, (double*)q0, n); break;
+    case 6: k_adj_norm2<T><<<grid, thr, 0, s>>>((const T*)p0, (double*)q0, n); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -61,6 +61,7 @@ struct LoadDev {
   double Sigma_m[6];  // target mean stress, Mandel
   int free_mask[6];   // 1 = stress-controlled
   int any_free;
+  double s_ref;       // floor of the mean-stress norm in the relative errors (0: none)
 };
 
 // Per-iteration device record, written by the last CTA of each reduction.
@@ -85,6 +86,7 @@ struct ConvDev {
   int fixed_iters;  // > 0: stop after exactly this many iterations
   int max_iter;
   double* hist;     // 2 * max_iter: (e_eq, c_F) of every iteration of the increment
+  double s_ref;     // floor of the mean-stress norm in the relative errors (0: none)
 };
 
 constexpr int kNumRed = 9;  // reduction slots per CTA

@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(kXThreads, XMinBlocks<T>::value) k_xpass(const
           nm += miss[c] * miss[c];
           ns += sm * sm;
         }
-        st->cF = ld.any_free ? sqrt(nm) / sqrt(ns) : 0.0;
+        st->cF = ld.any_free ? sqrt(nm) / fmax(sqrt(ns), ld.s_ref) : 0.0;
         const double* Ec = st->E[it & 1];
         double* En = st->E[(it + 1) & 1];
         for (int c = 0; c < 6; ++c) {
@@ -592,7 +592,9 @@ __global__ void __launch_bounds__(kZThreads) k_zgreen(const ZArgs<T> a) {
     if (tid == 0) {
       IterStatus* st = a.st;
       const double* S = st->sig_mean;
-      const double nrm = sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2] + 2.0 * (S[3] * S[3] + S[4] * S[4] + S[5] * S[5]));
+      const double nrm =
+          fmax(sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2] + 2.0 * (S[3] * S[3] + S[4] * S[4] + S[5] * S[5])),
+               a.conv.s_ref);
       st->res_sum = v[0];
       st->e_eq = nrm > 0.0 ? sqrt(v[0]) / ((double)a.nvox * nrm) : 0.0;
       st->nan_flag |= !isfinite(v[0]) ? 2 : 0;

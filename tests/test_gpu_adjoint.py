@@ -143,3 +143,42 @@ def test_load_history_gradient_matches_finite_differences(lib, cuda):
             num = (_history_J(gid, ep, {}, target, n_inc, dt, **opts)[0] -
                    _history_J(gid, em, {}, target, n_inc, dt, **opts)[0]) / (2 * h)
             assert abs(num - ge[g, a]) <= 1e-4 * max(abs(num), abs(ge[g, a])) + 1e-9 * J, (g, a, num, ge[g, a])
+
+
+def _history_S33(gid, euler, n_inc, dt, precision):
+    from paper_2402_09996_gb300 import rve
+
+    with rve.RVE(gid, euler, precision=precision) as s:
+        s.set_mixed_load(dt=dt)
+        s.step(n_inc)
+        return np.array([h["S"][2] for h in s.history()])
+
+
+def test_history_gradient_zero_misfit_and_fp32(lib, cuda):
+    """A target equal to the model's own curve gives J = 0 and an exactly zero gradient (every
+    increment's adjoint source vanishes, so no adjoint iteration runs).  A target that differs
+    only in the last two increments leaves the first increments without a direct source; the
+    FP32 adjoint then agrees with the FP64 one to the FP32 solve's accuracy."""
+    from oracle.voronoi import label_rve
+
+    from paper_2402_09996_gb300 import inputs, rve
+
+    inp = inputs.make_inputs((12, 10, 16), 6, 0.5, seed=33)
+    gid = label_rve(inp)
+    n_inc, dt = 5, 0.5
+    S32 = _history_S33(gid, inp.euler, n_inc, dt, rve.FP32)
+    J, gp, ge, info = rve.history_gradient(gid, inp.euler, n_inc, dt, S32, precision=rve.FP32, checkpoint_every=2)
+    assert J == 0.0
+    assert np.all(gp == 0.0) and np.all(ge == 0.0)
+    assert info["adjoint_iterations"] == 0
+    S64 = _history_S33(gid, inp.euler, n_inc, dt, rve.FP64)
+    target = S64.copy()
+    target[-2:] *= 0.98
+    J64, gp64, ge64, _ = rve.history_gradient(gid, inp.euler, n_inc, dt, target, precision=rve.FP64,
+                                              checkpoint_every=2)
+    J32, gp32, ge32, info32 = rve.history_gradient(gid, inp.euler, n_inc, dt, target, precision=rve.FP32,
+                                                   checkpoint_every=2)
+    assert info32["adjoint_iterations"] > 0
+    assert abs(J32 - J64) < 1e-3 * J64
+    assert np.max(np.abs(gp32 - gp64)) < 2e-3 * np.max(np.abs(gp64)), (gp32, gp64)
+    assert np.max(np.abs(ge32 - ge64)) < 2e-3 * np.max(np.abs(ge64)), (ge32, ge64)

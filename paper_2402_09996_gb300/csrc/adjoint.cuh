@@ -32,22 +32,28 @@ struct StageVals {
 };
 
 // Forward stage (the same arithmetic as rk_stage): rates k of state Y at path point s,
-// with the intermediates kept for the reverse pass.
-template <typename T, int NP>
-__device__ void stage_eval(const MatDev<T>& M, const T* e0, const T* de, T s, const MPState<T>& Y, const T* tab,
-                           StageVals<T>& V, MPState<T>& k) {
+// with the intermediates kept for the reverse pass.  SOLVE = false takes the rates rho of
+// the 16 systems from rho_in (a stage evaluated before with the same Y and s) instead of
+// solving for them, and rebuilds everything else.
+template <typename T, int NP, bool SOLVE = true>
+__device__ __forceinline__ void stage_eval(const MatDev<T>& M, const T* e0, const T* de, T s, const MPState<T>& Y,
+                                           const T* tab, StageVals<T>& V, MPState<T>& k,
+                                           const T* rho_in = nullptr) {
   constexpr double kLog2e = 1.44269504088896340736;
   T e[6];
+  #pragma unroll
   for (int c = 0; c < 6; ++c) e[c] = e0[c] + s * de[c] - Y.ep[c];
   hooke<T>(M, e, V.sg);
   V.Es = T(0);
   V.Et = T(0);
   T vtw = T(0);
   const T cb_s = -M.b_s * T(kLog2e), cb_t = -M.b_b * T(kLog2e);
+  #pragma unroll
   for (int q = 0; q < 12; ++q) {
     V.ex[q] = fast_exp2<T>(cb_s * Y.v[q]);
     V.Es += V.ex[q];
   }
+  #pragma unroll
   for (int q = 12; q < 16; ++q) {
     V.ex[q] = fast_exp2<T>(cb_t * Y.v[q]);
     V.Et += V.ex[q];
@@ -64,30 +70,37 @@ __device__ void stage_eval(const MatDev<T>& M, const T* e0, const T* de, T s, co
   V.Rb_s = M.Q_s * (M.h_off * (T(12) - V.Es) + dq);
   V.Rb_t = M.Q_b * (M.h_off * (T(4) - V.Et) + dq);
   RootCoef<T> qs, qt;
-  if constexpr (NP != 0) {
+  if constexpr (NP != 0 && SOLVE) {
     qs = root_coef<T>(T(1), M.K, M.n, M.inv_n, M.lg_K, M.eta, M.lg_eta, T(0));
     qt = root_coef<T>(V.Ptw, M.Kt, M.nt, M.inv_nt, M.lg_Kt, M.eta, M.lg_eta, V.lg_Ptw);
   }
   T ss[6];
+  #pragma unroll
   for (int c = 0; c < 6; ++c) ss[c] = V.sg[c] * sys_scale<T>(0);
+  #pragma unroll
   for (int c = 0; c < 6; ++c) V.du_s[c] = V.du_t[c] = T(0);
+  #pragma unroll
   for (int q = 0; q < 12; ++q) {
     V.tek[q] = schmid_sum<T>(q, ss) - M.c * Y.al[q];
     V.ak[q] = fabs(V.tek[q]) - ((M.r0[q] + V.Rb_s) - Qdq_s * V.ex[q]);
-    V.rho[q] = stage_rate<T, NP>(M, qs, V.ak[q], T(1), false, T(0), tab);
+    if constexpr (SOLVE) V.rho[q] = stage_rate<T, NP>(M, qs, V.ak[q], T(1), false, T(0), tab);
+    else V.rho[q] = rho_in[q];
     const T gd = copysign(V.rho[q], V.tek[q]);
     schmid_add<T>(q, gd, V.du_s);
     k.v[q] = V.rho[q];
     k.al[q] = gd - M.d * V.rho[q] * Y.al[q];
   }
+  #pragma unroll
   for (int q = 12; q < 16; ++q) {
     V.tek[q] = sys_scale<T>(q) * schmid_sum<T>(q, V.sg);
     V.ak[q] = V.tek[q] - ((M.r0[q] + V.Rb_t) - Qdq_t * V.ex[q]);
-    V.rho[q] = stage_rate<T, NP>(M, qt, V.ak[q], V.Ptw, true, V.lg_Ptw, tab);
+    if constexpr (SOLVE) V.rho[q] = stage_rate<T, NP>(M, qt, V.ak[q], V.Ptw, true, V.lg_Ptw, tab);
+    else V.rho[q] = rho_in[q];
     schmid_add<T>(q, V.rho[q], V.du_t);
     k.v[q] = V.rho[q];
   }
   const T fs = V.wslip * sys_scale<T>(0);
+  #pragma unroll
   for (int c = 0; c < 6; ++c) {
     const T wc = c < 3 ? T(1) : T(0.5);
     k.ep[c] = wc * (fs * V.du_s[c] + sys_scale<T>(12) * V.du_t[c]);
@@ -128,6 +141,7 @@ __device__ void stage_vjp(const MatDev<T>& M, const T* de, T s, const MPState<T>
   // eps_p rate: k.ep[c] = wc (wslip ssc du_s[c] + tsc du_t[c])
   T dusb[6], dutb[6];
   T wslipb = T(0);
+  #pragma unroll
   for (int c = 0; c < 6; ++c) {
     const T wc = c < 3 ? T(1) : T(0.5);
     dusb[c] = kb.ep[c] * wc * V.wslip * ssc;
@@ -136,14 +150,17 @@ __device__ void stage_vjp(const MatDev<T>& M, const T* de, T s, const MPState<T>
   }
   T sgb[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
   T exb[16];
+  #pragma unroll
   for (int q = 0; q < 16; ++q) exb[q] = T(0);
   T Esb = T(0), Etb = T(0), Ptwb = T(0);
   // slip systems
+  #pragma unroll
   for (int q = 0; q < 12; ++q) {
     const T sgn = V.tek[q] < T(0) ? T(-1) : T(1);
     const T gd = sgn * V.rho[q];
     // gd enters du_s (schmid_add) and k.al = gd - d rho al
     T gdb = kb.al[q];
+    #pragma unroll
     for (int c = 0; c < 6; ++c) gdb += T(schmid_k(q, c)) * dusb[c];
     T rhob = kb.v[q] + sgn * gdb - M.d * Y.al[q] * kb.al[q];
     Yb.al[q] += -M.d * V.rho[q] * kb.al[q];
@@ -162,11 +179,14 @@ __device__ void stage_vjp(const MatDev<T>& M, const T* de, T s, const MPState<T>
     // tek = ssc sum K sg - c al
     Yb.al[q] += -M.c * tekb;
     pb[7] += -Y.al[q] * tekb;  // c
+    #pragma unroll
     for (int c = 0; c < 6; ++c) sgb[c] += ssc * T(schmid_k(q, c)) * tekb;
   }
   // twins
+  #pragma unroll
   for (int q = 12; q < 16; ++q) {
     T rhob = kb.v[q];
+    #pragma unroll
     for (int c = 0; c < 6; ++c) rhob += T(schmid_k(q, c)) * dutb[c];
     T d_a, d_P;
     root_partials<T>(V.rho[q], V.ak[q], V.Ptw, M.Kt, M.nt, M.eta, &d_a, &d_P);
@@ -177,6 +197,7 @@ __device__ void stage_vjp(const MatDev<T>& M, const T* de, T s, const MPState<T>
     Etb += rb * (-M.Q_b * M.h_off);
     exb[q] += rb * (-M.Q_b * dq);
     pb[4] += rb * ((M.h_off * (T(4) - V.Et) + dq) - dq * V.ex[q]);  // Q_b
+    #pragma unroll
     for (int c = 0; c < 6; ++c) sgb[c] += tsc * T(schmid_k(q, c)) * akb;
   }
   // Ptw = Kc/sqrt2 max(fm - ftot, 0); wslip = 1 - ftot; ftot = sqrt2 sum v_twin
@@ -184,11 +205,13 @@ __device__ void stage_vjp(const MatDev<T>& M, const T* de, T s, const MPState<T>
   if (V.fm_left > T(0)) ftotb += Ptwb * (-(M.Kc * T(0.70710678118654752440)));
   const T vtwb = T(1.41421356237309504880) * ftotb;
   // ex = exp(-b v)
+  #pragma unroll
   for (int q = 0; q < 12; ++q) {
     exb[q] += Esb;
     Yb.v[q] += exb[q] * (-M.b_s * V.ex[q]);
     pb[5] += exb[q] * (-Y.v[q] * V.ex[q]);  // b_s
   }
+  #pragma unroll
   for (int q = 12; q < 16; ++q) {
     exb[q] += Etb;
     Yb.v[q] += exb[q] * (-M.b_b * V.ex[q]) + vtwb;
@@ -202,6 +225,7 @@ __device__ void stage_vjp(const MatDev<T>& M, const T* de, T s, const MPState<T>
   eb[3] = T(2) * M.C44 * sgb[3];
   eb[4] = T(2) * M.C44 * sgb[4];
   eb[5] = T(2) * M.C66 * sgb[5];
+  #pragma unroll
   for (int c = 0; c < 6; ++c) {
     e0b[c] += eb[c];
     deb[c] += s * eb[c];
@@ -242,20 +266,29 @@ __device__ void to_crystal_vjp(const T* R, const T* e, const T* ob, T* eb, T* Rb
   sym33<T>(e, E);
   // E_b = R G R^T ; R_b = 2 E R G
   T Eb[3][3];
+  #pragma unroll
   for (int i = 0; i < 3; ++i)
+    #pragma unroll
     for (int j = 0; j < 3; ++j) {
       T acc = T(0);
+      #pragma unroll
       for (int a = 0; a < 3; ++a)
+        #pragma unroll
         for (int b = 0; b < 3; ++b) acc += R[i * 3 + a] * G[a][b] * R[j * 3 + b];
       Eb[i][j] = acc;
     }
   T eb6[6];
   sym33_adj<T>(Eb, eb6);
+  #pragma unroll
   for (int c = 0; c < 6; ++c) eb[c] += eb6[c];
+  #pragma unroll
   for (int i = 0; i < 3; ++i)
+    #pragma unroll
     for (int j = 0; j < 3; ++j) {
       T acc = T(0);
+      #pragma unroll
       for (int a = 0; a < 3; ++a)
+        #pragma unroll
         for (int b = 0; b < 3; ++b) acc += E[i][a] * R[a * 3 + b] * G[b][j];
       Rb[i * 3 + j] += T(2) * acc;
     }
@@ -268,20 +301,29 @@ __device__ void to_sample_vjp(const T* R, const T* s, const T* ob, T* sb, T* Rb)
   out6_adj<T>(ob, G);
   sym33<T>(s, S);
   T Sb[3][3];
+  #pragma unroll
   for (int i = 0; i < 3; ++i)
+    #pragma unroll
     for (int j = 0; j < 3; ++j) {
       T acc = T(0);
+      #pragma unroll
       for (int a = 0; a < 3; ++a)
+        #pragma unroll
         for (int b = 0; b < 3; ++b) acc += R[a * 3 + i] * G[a][b] * R[b * 3 + j];
       Sb[i][j] = acc;
     }
   T sb6[6];
   sym33_adj<T>(Sb, sb6);
+  #pragma unroll
   for (int c = 0; c < 6; ++c) sb[c] += sb6[c];
+  #pragma unroll
   for (int i = 0; i < 3; ++i)
+    #pragma unroll
     for (int j = 0; j < 3; ++j) {
       T acc = T(0);
+      #pragma unroll
       for (int a = 0; a < 3; ++a)
+        #pragma unroll
         for (int b = 0; b < 3; ++b) acc += G[i][a] * R[a * 3 + b] * S[b][j];
       Rb[i * 3 + j] += T(2) * acc;
     }
@@ -289,65 +331,78 @@ __device__ void to_sample_vjp(const T* R, const T* s, const T* ob, T* sb, T* Rb)
 
 template <typename T>
 __device__ __forceinline__ void state_axpy(MPState<T>& y, T w, const MPState<T>& x) {
+  #pragma unroll
   for (int c = 0; c < 6; ++c) y.ep[c] += w * x.ep[c];
+  #pragma unroll
   for (int c = 0; c < 16; ++c) y.v[c] += w * x.v[c];
+  #pragma unroll
   for (int c = 0; c < 12; ++c) y.al[c] += w * x.al[c];
 }
 template <typename T>
 __device__ __forceinline__ void state_zero(MPState<T>& y) {
+  #pragma unroll
   for (int c = 0; c < 6; ++c) y.ep[c] = T(0);
+  #pragma unroll
   for (int c = 0; c < 16; ++c) y.v[c] = T(0);
+  #pragma unroll
   for (int c = 0; c < 12; ++c) y.al[c] = T(0);
 }
 
 
-// Reverse of mc_voxel.  In: R, eps_n, eps, y0 (state at t_n), sigma_b (adjoint of the stress
-// at t_{n+1}), yb (adjoint of the state at t_{n+1}; overwritten with the adjoint of y0).
-// Out (added): eps_nb, epsb, Rb, pb (kParamBar).  nsub <= kMaxSubVjp.
+// Forward pass of mc_voxel that keeps what the reverse sweeps need: the start state of
+// every RK4 substep (ys[0..nsub]) and the rates of its four stages (ks[4 m + j]).  The
+// update arithmetic is the primal's (classical RK4, weights 1 2 2 1, stage inputs
+// y + h/2 k1, y + h/2 k2, y + h k3).
 template <typename T, int NP>
-__device__ void mc_voxel_vjp(const MatDev<T>& M, const T* R, const T* eps_n, const T* eps, const MPState<T>& y0,
-                             T dt, int nsub, const T* sigma_b, MPState<T>& yb, T* eps_nb, T* epsb, T* Rb, T* pb,
-                             const T* tab) {
-  T e0[6], e1[6], de[6];
-  to_crystal<T>(R, eps_n, e0);
-  to_crystal<T>(R, eps, e1);
-  for (int c = 0; c < 6; ++c) de[c] = e1[c] - e0[c];
-  const bool quiet = elastic_increment<T>(M, e0, de, y0);
-  // forward: substep start states
-  MPState<T> ys[kMaxSubVjp + 1];
-  ys[0] = y0;
+__device__ __forceinline__ void mc_forward_store(const MatDev<T>& M, const T* e0, const T* de, T dt, int nsub,
+                                                 const T* tab, MPState<T>* ys, MPState<T>* ks) {
   const T h = dt / T(nsub);
   const T inv = T(1) / T(nsub);
   StageVals<T> V;
-  if (!quiet) {
-    for (int m = 0; m < nsub; ++m) {
-      const T s0 = T(m) * inv, sh = (T(m) + T(0.5)) * inv, s1 = (T(m) + T(1)) * inv;
-      MPState<T> k1, k2, k3, k4, Y;
-      stage_eval<T, NP>(M, e0, de, s0, ys[m], tab, V, k1);
-      Y = ys[m];
-      state_axpy<T>(Y, T(0.5) * h, k1);
-      stage_eval<T, NP>(M, e0, de, sh, Y, tab, V, k2);
-      Y = ys[m];
-      state_axpy<T>(Y, T(0.5) * h, k2);
-      stage_eval<T, NP>(M, e0, de, sh, Y, tab, V, k3);
-      Y = ys[m];
-      state_axpy<T>(Y, h, k3);
-      stage_eval<T, NP>(M, e0, de, s1, Y, tab, V, k4);
-      MPState<T> acc;
-      state_zero<T>(acc);
-      state_axpy<T>(acc, T(1), k1);
-      state_axpy<T>(acc, T(2), k2);
-      state_axpy<T>(acc, T(2), k3);
-      state_axpy<T>(acc, T(1), k4);
-      ys[m + 1] = ys[m];
-      state_axpy<T>(ys[m + 1], h / T(6), acc);
-    }
-  } else {
-    ys[nsub] = y0;
+#pragma unroll 1
+  for (int m = 0; m < nsub; ++m) {
+    const T s0 = T(m) * inv, sh = (T(m) + T(0.5)) * inv, s1 = (T(m) + T(1)) * inv;
+    MPState<T> k, Y, acc;
+    state_zero<T>(acc);
+    stage_eval<T, NP>(M, e0, de, s0, ys[m], tab, V, k);
+    ks[4 * m] = k;
+    state_axpy<T>(acc, T(1), k);
+    Y = ys[m];
+    state_axpy<T>(Y, T(0.5) * h, k);
+    stage_eval<T, NP>(M, e0, de, sh, Y, tab, V, k);
+    ks[4 * m + 1] = k;
+    state_axpy<T>(acc, T(2), k);
+    Y = ys[m];
+    state_axpy<T>(Y, T(0.5) * h, k);
+    stage_eval<T, NP>(M, e0, de, sh, Y, tab, V, k);
+    ks[4 * m + 2] = k;
+    state_axpy<T>(acc, T(2), k);
+    Y = ys[m];
+    state_axpy<T>(Y, h, k);
+    stage_eval<T, NP>(M, e0, de, s1, Y, tab, V, k);
+    ks[4 * m + 3] = k;
+    state_axpy<T>(acc, T(1), k);
+    Y = ys[m];
+    state_axpy<T>(Y, h / T(6), acc);
+    ys[m + 1] = Y;
   }
-  const MPState<T>& yN = ys[nsub];
+}
+
+// Reverse sweep of mc_voxel over a stored forward pass (mc_forward_store; quiet: the
+// increment was elastic, ys[nsub] = ys[0]).  In: sigma_b (adjoint of the stress at t_{n+1}),
+// yb (adjoint of the state at t_{n+1}; overwritten with the adjoint of the state at t_n).
+// Out (added): eps_nb, epsb, Rb, pb (kParamBar).  Each stage is rebuilt from its stored
+// input state and rates (no rate solve) just before it is reversed.
+template <typename T, int NP>
+__device__ __forceinline__ void mc_reverse(const MatDev<T>& M, const T* R, const T* eps_n, const T* eps,
+                                           const T* e0, const T* e1, const T* de, bool quiet,
+                                           const MPState<T>* ys, const MPState<T>* ks, T dt, int nsub,
+                                           const T* sigma_b, MPState<T>& yb, T* eps_nb, T* epsb, T* Rb, T* pb,
+                                           const T* tab) {
+  const MPState<T>& yN = ys[quiet ? 0 : nsub];
   // stress: sc = C (e1 - ep_N); sigma = R sc R^T
   T ee[6], sc[6];
+#pragma unroll
   for (int c = 0; c < 6; ++c) ee[c] = e1[c] - yN.ep[c];
   hooke<T>(M, ee, sc);
   T scb[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
@@ -360,6 +415,7 @@ __device__ void mc_voxel_vjp(const MatDev<T>& M, const T* R, const T* eps_n, con
   eeb[4] = T(2) * M.C44 * scb[4];
   eeb[5] = T(2) * M.C66 * scb[5];
   T e0b[6], e1b[6], deb[6];
+#pragma unroll
   for (int c = 0; c < 6; ++c) {
     e1b[c] = eeb[c];
     yb.ep[c] -= eeb[c];
@@ -367,59 +423,119 @@ __device__ void mc_voxel_vjp(const MatDev<T>& M, const T* R, const T* eps_n, con
     deb[c] = T(0);
   }
   if (!quiet) {
+    const T h = dt / T(nsub);
+    const T inv = T(1) / T(nsub);
+#pragma unroll 1
     for (int m = nsub - 1; m >= 0; --m) {
       const T s0 = T(m) * inv, sh = (T(m) + T(0.5)) * inv, s1 = (T(m) + T(1)) * inv;
-      // recompute the substep's stages
-      MPState<T> k1, k2, k3, k4, Y2, Y3, Y4;
-      StageVals<T> V1, V2, V3, V4;
-      stage_eval<T, NP>(M, e0, de, s0, ys[m], tab, V1, k1);
-      Y2 = ys[m];
-      state_axpy<T>(Y2, T(0.5) * h, k1);
-      stage_eval<T, NP>(M, e0, de, sh, Y2, tab, V2, k2);
-      Y3 = ys[m];
-      state_axpy<T>(Y3, T(0.5) * h, k2);
-      stage_eval<T, NP>(M, e0, de, sh, Y3, tab, V3, k3);
-      Y4 = ys[m];
-      state_axpy<T>(Y4, h, k3);
-      stage_eval<T, NP>(M, e0, de, s1, Y4, tab, V4, k4);
-      // y' = y + h/6 (k1 + 2 k2 + 2 k3 + k4)
-      MPState<T> k1b, k2b, k3b, k4b, Yb;
-      state_zero<T>(k1b);
-      state_zero<T>(k2b);
-      state_zero<T>(k3b);
-      state_zero<T>(k4b);
-      state_axpy<T>(k1b, h / T(6), yb);
-      state_axpy<T>(k2b, h / T(3), yb);
-      state_axpy<T>(k3b, h / T(3), yb);
-      state_axpy<T>(k4b, h / T(6), yb);
+      // y' = y + h/6 (k1 + 2 k2 + 2 k3 + k4); yend = adjoint of y'
+      const MPState<T> yend = yb;
+      MPState<T> Y, kb, Yb, kdum;
+      StageVals<T> V;
       // stage 4 at Y4 = y + h k3
+      Y = ys[m];
+      state_axpy<T>(Y, h, ks[4 * m + 2]);
+      stage_eval<T, NP, false>(M, e0, de, s1, Y, tab, V, kdum, ks[4 * m + 3].v);
+      state_zero<T>(kb);
+      state_axpy<T>(kb, h / T(6), yend);
       state_zero<T>(Yb);
-      stage_vjp<T>(M, de, s1, Y4, V4, k4b, Yb, e0b, deb, pb);
+      stage_vjp<T>(M, de, s1, Y, V, kb, Yb, e0b, deb, pb);
       state_axpy<T>(yb, T(1), Yb);
-      state_axpy<T>(k3b, h, Yb);
-      // stage 3 at Y3 = y + h/2 k2
+      // stage 3 at Y3 = y + h/2 k2; k3 feeds y' and Y4
+      state_zero<T>(kb);
+      state_axpy<T>(kb, h / T(3), yend);
+      state_axpy<T>(kb, h, Yb);
+      Y = ys[m];
+      state_axpy<T>(Y, T(0.5) * h, ks[4 * m + 1]);
+      stage_eval<T, NP, false>(M, e0, de, sh, Y, tab, V, kdum, ks[4 * m + 2].v);
       state_zero<T>(Yb);
-      stage_vjp<T>(M, de, sh, Y3, V3, k3b, Yb, e0b, deb, pb);
+      stage_vjp<T>(M, de, sh, Y, V, kb, Yb, e0b, deb, pb);
       state_axpy<T>(yb, T(1), Yb);
-      state_axpy<T>(k2b, T(0.5) * h, Yb);
-      // stage 2 at Y2 = y + h/2 k1
+      // stage 2 at Y2 = y + h/2 k1; k2 feeds y' and Y3
+      state_zero<T>(kb);
+      state_axpy<T>(kb, h / T(3), yend);
+      state_axpy<T>(kb, T(0.5) * h, Yb);
+      Y = ys[m];
+      state_axpy<T>(Y, T(0.5) * h, ks[4 * m]);
+      stage_eval<T, NP, false>(M, e0, de, sh, Y, tab, V, kdum, ks[4 * m + 1].v);
       state_zero<T>(Yb);
-      stage_vjp<T>(M, de, sh, Y2, V2, k2b, Yb, e0b, deb, pb);
+      stage_vjp<T>(M, de, sh, Y, V, kb, Yb, e0b, deb, pb);
       state_axpy<T>(yb, T(1), Yb);
-      state_axpy<T>(k1b, T(0.5) * h, Yb);
-      // stage 1 at y
+      // stage 1 at y; k1 feeds y' and Y2
+      state_zero<T>(kb);
+      state_axpy<T>(kb, h / T(6), yend);
+      state_axpy<T>(kb, T(0.5) * h, Yb);
+      stage_eval<T, NP, false>(M, e0, de, s0, ys[m], tab, V, kdum, ks[4 * m].v);
       state_zero<T>(Yb);
-      stage_vjp<T>(M, de, s0, ys[m], V1, k1b, Yb, e0b, deb, pb);
+      stage_vjp<T>(M, de, s0, ys[m], V, kb, Yb, e0b, deb, pb);
       state_axpy<T>(yb, T(1), Yb);
     }
   }
   // de = e1 - e0; e0 = R^T eps_n R; e1 = R^T eps R
+#pragma unroll
   for (int c = 0; c < 6; ++c) {
     e1b[c] += deb[c];
     e0b[c] -= deb[c];
   }
   to_crystal_vjp<T>(R, eps_n, e0b, eps_nb, Rb);
   to_crystal_vjp<T>(R, eps, e1b, epsb, Rb);
+}
+
+// Per-voxel inputs of the reverse kernels: rotation, strains (sample frame), state at t_n,
+// and the stored forward pass.
+template <typename T>
+struct VjpVoxel {
+  T r[9], en[6], e[6], e0[6], e1[6], de[6];
+  MPState<T> ys[kMaxSubVjp + 1];
+  MPState<T> ks[4 * kMaxSubVjp];
+  bool quiet;
+};
+
+template <typename T, int NP>
+__device__ __forceinline__ void vjp_prepare(const MatDev<T>& M, long long i, size_t n, const T* __restrict__ R,
+                                            const T* __restrict__ eps_n, const T* __restrict__ eps,
+                                            const T* __restrict__ state, T dt, int nsub, const T* tab,
+                                            VjpVoxel<T>& P) {
+#pragma unroll
+  for (int k = 0; k < 9; ++k) P.r[k] = R[(size_t)i * 9 + k];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    P.en[c] = eps_n[c * n + i];
+    P.e[c] = eps[c * n + i];
+  }
+  MPState<T> y;
+#pragma unroll
+  for (int c = 0; c < 6; ++c) y.ep[c] = state[c * n + i];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) y.v[c] = state[(6 + c) * n + i];
+#pragma unroll
+  for (int c = 0; c < 12; ++c) y.al[c] = state[(22 + c) * n + i];
+  to_crystal<T>(P.r, P.en, P.e0);
+  to_crystal<T>(P.r, P.e, P.e1);
+#pragma unroll
+  for (int c = 0; c < 6; ++c) P.de[c] = P.e1[c] - P.e0[c];
+  P.quiet = elastic_increment<T>(M, P.e0, P.de, y);
+  P.ys[0] = y;
+  if (!P.quiet) mc_forward_store<T, NP>(M, P.e0, P.de, dt, nsub, tab, P.ys, P.ks);
+}
+
+template <typename T>
+__device__ __forceinline__ void load_state34(const T* __restrict__ src, long long i, size_t n, MPState<T>& y) {
+#pragma unroll
+  for (int c = 0; c < 6; ++c) y.ep[c] = src[c * n + i];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) y.v[c] = src[(6 + c) * n + i];
+#pragma unroll
+  for (int c = 0; c < 12; ++c) y.al[c] = src[(22 + c) * n + i];
+}
+template <typename T>
+__device__ __forceinline__ void store_state34(T* __restrict__ dst, long long i, size_t n, const MPState<T>& y) {
+#pragma unroll
+  for (int c = 0; c < 6; ++c) dst[c * n + i] = y.ep[c];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) dst[(6 + c) * n + i] = y.v[c];
+#pragma unroll
+  for (int c = 0; c < 12; ++c) dst[(22 + c) * n + i] = y.al[c];
 }
 
 // One thread per voxel; arrays component-major (component * nvox + voxel) as in the
@@ -439,40 +555,88 @@ __global__ void k_material_point_vjp(const MatDev<T> M, long long nvox, const T*
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nvox) return;
   const size_t n = (size_t)nvox;
-  T r[9], en[6], e[6], sb[6];
-  for (int k = 0; k < 9; ++k) r[k] = R[(size_t)i * 9 + k];
-  for (int c = 0; c < 6; ++c) {
-    en[c] = eps_n[c * n + i];
-    e[c] = eps[c * n + i];
-    sb[c] = sigma_b[c * n + i];
-  }
-  MPState<T> y, yb;
-  for (int c = 0; c < 6; ++c) {
-    y.ep[c] = state[c * n + i];
-    yb.ep[c] = state_b[c * n + i];
-  }
-  for (int c = 0; c < 16; ++c) {
-    y.v[c] = state[(6 + c) * n + i];
-    yb.v[c] = state_b[(6 + c) * n + i];
-  }
-  for (int c = 0; c < 12; ++c) {
-    y.al[c] = state[(22 + c) * n + i];
-    yb.al[c] = state_b[(22 + c) * n + i];
-  }
+  VjpVoxel<T> P;
+  vjp_prepare<T, NP>(M, i, n, R, eps_n, eps, state, dt, nsub, tab, P);
+  T sb[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) sb[c] = sigma_b[c * n + i];
+  MPState<T> yb;
+  load_state34<T>(state_b, i, n, yb);
   T enb[6] = {T(0), T(0), T(0), T(0), T(0), T(0)}, eb[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
   T rb[9] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
   T pb[kParamBar];
+#pragma unroll
   for (int k = 0; k < kParamBar; ++k) pb[k] = T(0);
-  mc_voxel_vjp<T, NP>(M, r, en, e, y, dt, nsub, sb, yb, enb, eb, rb, pb, tab);
+  mc_reverse<T, NP>(M, P.r, P.en, P.e, P.e0, P.e1, P.de, P.quiet, P.ys, P.ks, dt, nsub, sb, yb, enb, eb, rb, pb, tab);
+  store_state34<T>(state_b, i, n, yb);
+#pragma unroll
   for (int c = 0; c < 6; ++c) {
-    state_b[c * n + i] = yb.ep[c];
     eps_b[c * n + i] = eb[c];
     eps_n_b[c * n + i] = enb[c];
   }
-  for (int c = 0; c < 16; ++c) state_b[(6 + c) * n + i] = yb.v[c];
-  for (int c = 0; c < 12; ++c) state_b[(22 + c) * n + i] = yb.al[c];
+#pragma unroll
   for (int k = 0; k < 9; ++k) R_b[k * n + i] = rb[k];
+#pragma unroll
   for (int k = 0; k < kParamBar; ++k) param_b[k * n + i] = pb[k];
+}
+
+// The reverse work of one increment of the history adjoint before its fixed point, over one
+// stored forward pass per voxel: the six rows J(k, .) = d sigma_k / d eps of the algorithmic
+// tangent (unit stress adjoints, no state adjoint; written to J at (k * 6 + c) * nvox + voxel)
+// and the direct part (uniform stress adjoint sd, state adjoint state_b at t_{n+1}, which is
+// overwritten with the adjoint at t_n), whose eps, eps_n, rotation and parameter adjoints go
+// to eps_b, eps_n_b, R_b and param_b.
+template <typename T, int NP>
+__global__ void k_adj_tangent(const MatDev<T> M, long long nvox, const T* __restrict__ R,
+                              const T* __restrict__ eps_n, const T* __restrict__ eps,
+                              const T* __restrict__ state, T dt, int nsub, T sd0, T sd1, T sd2, T sd3, T sd4, T sd5,
+                              T* state_b, T* J, T* eps_b, T* eps_n_b, T* R_b, T* param_b,
+                              const T* __restrict__ root_tab) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* tab = reinterpret_cast<T*>(smem_raw);
+  if (NP != 0)
+    for (int k = threadIdx.x; k < kRootTabs; k += blockDim.x) tab[k] = root_tab[k];
+  __syncthreads();
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nvox) return;
+  const size_t n = (size_t)nvox;
+  VjpVoxel<T> P;
+  vjp_prepare<T, NP>(M, i, n, R, eps_n, eps, state, dt, nsub, tab, P);
+#pragma unroll 1
+  for (int row = 0; row < 7; ++row) {
+    T sb[6];
+    MPState<T> yb;
+    if (row < 6) {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) sb[c] = c == row ? T(1) : T(0);
+      state_zero<T>(yb);
+    } else {
+      sb[0] = sd0; sb[1] = sd1; sb[2] = sd2; sb[3] = sd3; sb[4] = sd4; sb[5] = sd5;
+      load_state34<T>(state_b, i, n, yb);
+    }
+    T enb[6] = {T(0), T(0), T(0), T(0), T(0), T(0)}, eb[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+    T rb[9] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
+    T pb[kParamBar];
+#pragma unroll
+    for (int k = 0; k < kParamBar; ++k) pb[k] = T(0);
+    mc_reverse<T, NP>(M, P.r, P.en, P.e, P.e0, P.e1, P.de, P.quiet, P.ys, P.ks, dt, nsub, sb, yb, enb, eb, rb, pb,
+                      tab);
+    if (row < 6) {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) J[((size_t)row * 6 + c) * n + i] = eb[c];
+    } else {
+      store_state34<T>(state_b, i, n, yb);
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        eps_b[c * n + i] = eb[c];
+        eps_n_b[c * n + i] = enb[c];
+      }
+#pragma unroll
+      for (int k = 0; k < 9; ++k) R_b[k * n + i] = rb[k];
+#pragma unroll
+      for (int k = 0; k < kParamBar; ++k) param_b[k * n + i] = pb[k];
+    }
+  }
 }
 
 }  // namespace rve

@@ -262,6 +262,8 @@ struct rve_s {
   // x pass's linear-law mode (s = B eps - g) used by the adjoint fixed point
   std::vector<uint32_t> gid_host;
   void* adj = nullptr;  // one block of per-voxel scratch arrays, type by precision
+  void* adj_perm = nullptr;  // voxel indices sorted by grain (increasing within a grain)
+  void* adj_goff = nullptr;  // n_grains + 1 offsets into adj_perm
   bool lin_mode = false;
   const void* lin_B = nullptr;
   const void* lin_g = nullptr;
@@ -1223,23 +1225,14 @@ rve_status adjoint_increment(rve_s* h, const double* eps_prev, const double* eps
   RVE_CUDA(h, launch_adj<T>(4, 34 * n, s, state_b, nullptr, nullptr, at(kAdjStB), nullptr, nullptr));
   RVE_CUDA(h, launch_adj<T>(4, 6 * n, s, eps_b, nullptr, nullptr, at(kAdjEbIn), nullptr, nullptr));
   RVE_CUDA(h, launch_adj<T>(0, n, s, h->grain, h->Rg, nullptr, at(kAdjRvox), nullptr, nullptr));
-  // direct part: stress adjoint dS / N everywhere and the state adjoint from later increments
+  // one stored forward pass per voxel, then the reverse sweeps: the tangent rows
+  // d sigma_k / d eps and the direct part (stress adjoint dS / N everywhere, the state
+  // adjoint from later increments)
   double v6[6];
   for (int c = 0; c < 6; ++c) v6[c] = dS[c] / (double)n;
-  RVE_CUDA(h, launch_adj<T>(1, n, s, nullptr, nullptr, nullptr, at(kAdjSigB), nullptr, v6));
-  RVE_CUDA(h, launch_material_point_vjp<T>(M, np, n, at(kAdjRvox), at(kAdjEpsP), at(kAdjEpsC), at(kAdjStP), dt, nsub,
-                                           at(kAdjSigB), at(kAdjStB), at(kAdjEbA), at(kAdjEnA), at(kAdjRbA),
-                                           at(kAdjPbA), tab, s));
-  // tangent rows d sigma_k / d eps
-  for (int k = 0; k < 6; ++k) {
-    double e6[6] = {0, 0, 0, 0, 0, 0};
-    e6[k] = 1.0;
-    RVE_CUDA(h, launch_adj<T>(1, n, s, nullptr, nullptr, nullptr, at(kAdjSigB), nullptr, e6));
-    RVE_CUDA(h, cudaMemsetAsync(at(kAdjStZ), 0, 34 * N * sizeof(T), s));
-    RVE_CUDA(h, launch_material_point_vjp<T>(M, np, n, at(kAdjRvox), at(kAdjEpsP), at(kAdjEpsC), at(kAdjStP), dt,
-                                             nsub, at(kAdjSigB), at(kAdjStZ), at(kAdjJ) + (size_t)k * 6 * N,
-                                             at(kAdjDummy), at(kAdjDummy) + 6 * N, at(kAdjDummy) + 15 * N, tab, s));
-  }
+  RVE_CUDA(h, launch_adj_tangent<T>(M, np, n, at(kAdjRvox), at(kAdjEpsP), at(kAdjEpsC), at(kAdjStP), dt, nsub, v6,
+                                    at(kAdjStB), at(kAdjJ), at(kAdjEbA), at(kAdjEnA), at(kAdjRbA), at(kAdjPbA), tab,
+                                    s));
   RVE_CUDA(h, launch_adj<T>(2, n, s, at(kAdjJ), at(kAdjEbA), at(kAdjEbIn), at(kAdjB), at(kAdjG), nullptr));
   // source scale |g|_rms = sqrt(<g : g>): per-block partial sums (into the unused-output
   // slot, free until the constraint part) added on the host in a fixed order
@@ -1312,25 +1305,39 @@ rve_status adjoint_increment(rve_s* h, const double* eps_prev, const double* eps
   // outputs: state and strain adjoints at t_{n-1} (double, device)
   RVE_CUDA(h, launch_adj<T>(5, 34 * n, s, at(kAdjStB), at(kAdjStZ), nullptr, state_b, nullptr, nullptr));
   RVE_CUDA(h, launch_adj<T>(5, 6 * n, s, at(kAdjEnA), at(kAdjEnB), nullptr, eps_b, nullptr, nullptr));
-  // parameter and rotation adjoints: per-voxel values summed on the host
-  std::vector<T> hb(9 * N);
-  std::vector<double> pv(9, 0.0);
-  for (int part = 0; part < 2; ++part) {
-    RVE_CUDA(h, cudaMemcpyAsync(hb.data(), at(part ? kAdjPbB : kAdjPbA), 9 * N * sizeof(T), cudaMemcpyDeviceToHost, s));
+  // parameter and rotation adjoints: per-voxel values summed on the device in a fixed order
+  // (parameters: block partials, added here; rotations: per grain over the grain-sorted
+  // voxel list), into the unused-output slot
+  if (!h->adj_perm) {
+    std::vector<int> goff((size_t)h->n_grains + 1, 0);
+    for (size_t i = 0; i < N; ++i) ++goff[(size_t)h->gid_host[i] + 1];
+    for (int g = 0; g < h->n_grains; ++g) goff[g + 1] += goff[g];
+    std::vector<uint32_t> perm(N);
+    std::vector<int> fill(goff.begin(), goff.end() - 1);
+    for (size_t i = 0; i < N; ++i) perm[(size_t)fill[h->gid_host[i]]++] = (uint32_t)i;
+    rve_status st = dalloc(h, &h->adj_perm, N * sizeof(uint32_t));
+    if (st) return st;
+    st = dalloc(h, &h->adj_goff, goff.size() * sizeof(int));
+    if (st) return st;
+    RVE_CUDA(h, cudaMemcpyAsync(h->adj_perm, perm.data(), N * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+    RVE_CUDA(h, cudaMemcpyAsync(h->adj_goff, goff.data(), goff.size() * sizeof(int), cudaMemcpyHostToDevice, s));
     RVE_CUDA(h, cudaStreamSynchronize(s));
-    for (int k = 0; k < 9; ++k) {
-      double acc = 0.0;
-      for (size_t i = 0; i < N; ++i) acc += (double)hb[k * N + i];
-      pv[k] += acc;
-    }
   }
-  for (int k = 0; k < 9; ++k) pgrad[k] += pv[k];
-  std::vector<double> Rb((size_t)h->n_grains * 9, 0.0);
-  for (int part = 0; part < 2; ++part) {
-    RVE_CUDA(h, cudaMemcpyAsync(hb.data(), at(part ? kAdjRbB : kAdjRbA), 9 * N * sizeof(T), cudaMemcpyDeviceToHost, s));
-    RVE_CUDA(h, cudaStreamSynchronize(s));
-    for (int k = 0; k < 9; ++k)
-      for (size_t i = 0; i < N; ++i) Rb[(size_t)h->gid_host[i] * 9 + k] += (double)hb[k * N + i];
+  const size_t nb = (N + 255) / 256;
+  if ((nb + (size_t)h->n_grains) * 9 * sizeof(double) > (size_t)30 * N * sizeof(T))
+    return fail(h, RVE_ERR_UNSUPPORTED, "adjoint: more grains than the gradient scratch holds");
+  double* param_part = (double*)at(kAdjDummy);
+  double* grain_out = param_part + nb * 9;
+  RVE_CUDA(h, launch_adj_sums<T>(at(kAdjPbA), at(kAdjPbB), at(kAdjRbA), at(kAdjRbB), (const uint32_t*)h->adj_perm,
+                                 (const int*)h->adj_goff, h->n_grains, n, param_part, grain_out, s));
+  std::vector<double> hp(nb * 9), Rb((size_t)h->n_grains * 9);
+  RVE_CUDA(h, cudaMemcpyAsync(hp.data(), param_part, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  RVE_CUDA(h, cudaMemcpyAsync(Rb.data(), grain_out, Rb.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  RVE_CUDA(h, cudaStreamSynchronize(s));
+  for (int k = 0; k < 9; ++k) {
+    double acc = 0.0;
+    for (size_t b = 0; b < nb; ++b) acc += hp[b * 9 + k];
+    pgrad[k] += acc;
   }
   for (int g = 0; g < h->n_grains; ++g) {
     double dR[3][9];

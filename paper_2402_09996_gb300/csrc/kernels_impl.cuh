@@ -60,6 +60,22 @@ cudaError_t launch_material_point_vjp_np(const MatDev<T>& M, long long nvox, con
   return cudaGetLastError();
 }
 
+template <typename T, int NP>
+cudaError_t launch_adj_tangent_np(const MatDev<T>& M, long long nvox, const T* R, const T* eps_n, const T* eps,
+                                  const T* state, T dt, int nsub, const double* sd, T* state_b, T* J, T* eps_b,
+                                  T* eps_n_b, T* R_b, T* param_b, const T* root_tab, cudaStream_t s) {
+  if (nvox <= 0) return cudaSuccess;
+  const int thr = 64;
+  const long long grid = (nvox + thr - 1) / thr;
+  const size_t smem = (size_t)kRootTabs * sizeof(T);
+  cudaError_t e = set_smem<T>((const void*)k_adj_tangent<T, NP>, smem);
+  if (e != cudaSuccess) return e;
+  k_adj_tangent<T, NP><<<(unsigned)grid, thr, smem, s>>>(M, nvox, R, eps_n, eps, state, dt, nsub, (T)sd[0], (T)sd[1],
+                                                         (T)sd[2], (T)sd[3], (T)sd[4], (T)sd[5], state_b, J, eps_b,
+                                                         eps_n_b, R_b, param_b, root_tab);
+  return cudaGetLastError();
+}
+
 // the linear-law x pass alone (no material-point kernels)
 #define RVE_INSTANTIATE_XLIN(T) \
   template cudaError_t launch_xpass_np<T, kLinearLaw>(const XArgs<T>&, bool, int, size_t, cudaStream_t);
@@ -70,7 +86,10 @@ cudaError_t launch_material_point_vjp_np(const MatDev<T>& M, long long nvox, con
                                                        T*, T*, T, int, const T*, cudaStream_t);              \
   template cudaError_t launch_material_point_vjp_np<T, NP>(const MatDev<T>&, long long, const T*, const T*,      \
                                                            const T*, const T*, T, int, const T*, T*, T*, T*, T*, \
-                                                           T*, const T*, cudaStream_t);
+                                                           T*, const T*, cudaStream_t);                            \
+  template cudaError_t launch_adj_tangent_np<T, NP>(const MatDev<T>&, long long, const T*, const T*, const T*,    \
+                                                    const T*, T, int, const double*, T*, T*, T*, T*, T*, T*,       \
+                                                    const T*, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_line(const LineArgs<T>& a, int sign, dim3 grid, size_t smem, cudaStream_t s) {
@@ -256,6 +275,71 @@ __global__ void k_adj_norm2(const T* __restrict__ f, double* __restrict__ out, l
   }
 }
 
+// Sum of A + B over 9 component rows (row k at k * nvox), in double: per-block partials
+// out[blockIdx.x * 9 + k] (256 threads, fixed reduction order).
+template <typename T>
+__global__ void k_adj_param_sum(const T* __restrict__ A, const T* __restrict__ B, double* __restrict__ out,
+                                long long nvox) {
+  __shared__ double red[9][8];
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double v[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    v[k] = i < nvox ? (double)A[k * (size_t)nvox + i] + (double)B[k * (size_t)nvox + i] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+  }
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int k = 0; k < 9; ++k) red[k][threadIdx.x >> 5] = v[k];
+  __syncthreads();
+  if (threadIdx.x < 9) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[threadIdx.x][w];
+    out[(size_t)blockIdx.x * 9 + threadIdx.x] = t;
+  }
+}
+
+// Per-grain sums of A + B over 9 component rows: block g adds the voxels perm[goff[g] ..
+// goff[g+1]) (one grain's voxels in increasing order) in a fixed order into out[g * 9 + k].
+template <typename T>
+__global__ void k_adj_grain_sum(const T* __restrict__ A, const T* __restrict__ B, const uint32_t* __restrict__ perm,
+                                const int* __restrict__ goff, double* __restrict__ out, long long nvox) {
+  __shared__ double red[9][8];
+  const int g = blockIdx.x;
+  double v[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) v[k] = 0.0;
+  for (int j = goff[g] + threadIdx.x; j < goff[g + 1]; j += blockDim.x) {
+    const size_t q = perm[j];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) v[k] += (double)A[k * (size_t)nvox + q] + (double)B[k * (size_t)nvox + q];
+  }
+#pragma unroll
+  for (int k = 0; k < 9; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int k = 0; k < 9; ++k) red[k][threadIdx.x >> 5] = v[k];
+  __syncthreads();
+  if (threadIdx.x < 9) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[threadIdx.x][w];
+    out[(size_t)g * 9 + threadIdx.x] = t;
+  }
+}
+
+template <typename T>
+cudaError_t launch_adj_sums(const T* pA, const T* pB, const T* rA, const T* rB, const uint32_t* perm, const int* goff,
+                            int n_grains, long long nvox, double* param_part, double* grain_out, cudaStream_t s) {
+  if (nvox <= 0) return cudaSuccess;
+  const unsigned nb = (unsigned)((nvox + 255) / 256);
+  k_adj_param_sum<T><<<nb, 256, 0, s>>>(pA, pB, param_part, nvox);
+  if (n_grains > 0) k_adj_grain_sum<T><<<(unsigned)n_grains, 256, 0, s>>>(rA, rB, perm, goff, grain_out, nvox);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_adj(int which, long long n, cudaStream_t s, const void* p0, const void* p1, const void* p2,
                        void* q0, void* q1, const double* v) {
@@ -284,6 +368,8 @@ cudaError_t launch_adj(int which, long long n, cudaStream_t s, const void* p0, c
   template cudaError_t launch_von_mises<T>(const T*, double*, long long, cudaStream_t);                          \
   template cudaError_t launch_loop_guard<T>(IterStatus*, int, cudaGraphConditionalHandle, cudaStream_t);           \
   template cudaError_t launch_adj<T>(int, long long, cudaStream_t, const void*, const void*, const void*, void*,   \
-                                     void*, const double*);
+                                     void*, const double*);                                                        \
+  template cudaError_t launch_adj_sums<T>(const T*, const T*, const T*, const T*, const uint32_t*, const int*, int, \
+                                          long long, double*, double*, cudaStream_t);
 
 }  // namespace rve

@@ -32,6 +32,26 @@ cudaError_t launch_material_point_vjp_np(const MatDev<T>& M, long long nvox, con
                                          const T* state, T dt, int nsub, const T* sigma_b, T* state_b, T* eps_b,
                                          T* eps_n_b, T* R_b, T* param_b, const T* root_tab, cudaStream_t s);
 
+template <typename T, int NP>
+cudaError_t launch_adj_tangent_np(const MatDev<T>& M, long long nvox, const T* R, const T* eps_n, const T* eps,
+                                  const T* state, T dt, int nsub, const double* sd, T* state_b, T* J, T* eps_b,
+                                  T* eps_n_b, T* R_b, T* param_b, const T* root_tab, cudaStream_t s);
+
+// tangent rows and direct part of one increment's adjoint (adjoint.cuh, k_adj_tangent)
+template <typename T>
+cudaError_t launch_adj_tangent(const MatDev<T>& M, int np, long long nvox, const T* R, const T* eps_n, const T* eps,
+                               const T* state, T dt, int nsub, const double* sd, T* state_b, T* J, T* eps_b,
+                               T* eps_n_b, T* R_b, T* param_b, const T* root_tab, cudaStream_t s) {
+  if (np == 10)
+    return launch_adj_tangent_np<T, 10>(M, nvox, R, eps_n, eps, state, dt, nsub, sd, state_b, J, eps_b, eps_n_b, R_b,
+                                        param_b, root_tab, s);
+  if (np < 0)
+    return launch_adj_tangent_np<T, -1>(M, nvox, R, eps_n, eps, state, dt, nsub, sd, state_b, J, eps_b, eps_n_b, R_b,
+                                        param_b, root_tab, s);
+  return launch_adj_tangent_np<T, 0>(M, nvox, R, eps_n, eps, state, dt, nsub, sd, state_b, J, eps_b, eps_n_b, R_b,
+                                     param_b, root_tab, s);
+}
+
 template <typename T>
 cudaError_t launch_material_point_vjp(const MatDev<T>& M, int np, long long nvox, const T* R, const T* eps_n,
                                       const T* eps, const T* state, T dt, int nsub, const T* sigma_b, T* state_b,
@@ -76,6 +96,12 @@ template <typename T>
 cudaError_t launch_von_mises(const T* sig6, double* dst, long long nvox, cudaStream_t s);
 template <typename T>
 cudaError_t launch_loop_guard(IterStatus* st, int limit, cudaGraphConditionalHandle cond, cudaStream_t s);
+// adjoint gradient sums (kernels_impl.cuh): per-block partial sums of the 9 parameter rows
+// pA + pB (param_part, 9 per block of 256 voxels) and per-grain sums of the 9 rotation rows
+// rA + rB over the grain-sorted voxel list perm / goff (grain_out, 9 per grain)
+template <typename T>
+cudaError_t launch_adj_sums(const T* pA, const T* pB, const T* rA, const T* rB, const uint32_t* perm, const int* goff,
+                            int n_grains, long long nvox, double* param_part, double* grain_out, cudaStream_t s);
 // adjoint helpers (kernels_impl.cuh): 0 gather per-voxel R, 1 fill a uniform 6-vector field,
 // 2 build B and g, 3 sigma_b = -w mu, 4 double -> T copy, 5 T + T -> double sum
 template <typename T>

@@ -435,12 +435,20 @@ PARAM_NAMES = ["r0_ord", "r0_sup", "r0_twin", "Q_s", "Q_b", "b_s", "b_b", "c", "
 
 
 def history_gradient(grain_id, euler, n_increments, dt, target, weights=None, precision=FP64, material=None,
-                     Edot=(0, 0, 1e-3, 0, 0, 0), checkpoint_every=5, **options):
+                     Edot=(0, 0, 1e-3, 0, 0, 0), checkpoint_every=5, memory_budget=None, **options):
     """Misfit J = sum_n w_n (<sigma_zz>_n - target_n)^2 of a load history and its gradient
     with respect to the parameters PARAM_NAMES and every grain's Bunge angles, by the
-    adjoint of the history (rve_adjoint_increment), with the state checkpointed every
-    `checkpoint_every` increments and replayed segment by segment in the reverse pass.
+    adjoint of the history (rve_adjoint_increment).
+
+    The reverse pass needs the strain and state of every increment.  With checkpoint_every
+    = k the forward pass saves the state every k increments and the reverse pass replays
+    each segment from its checkpoint.  With checkpoint_every = None the forward pass keeps
+    every increment's fields on the device (8 (6 + 34) bytes per voxel and increment) when
+    they fit in memory_budget bytes (default: half the free device memory), so nothing is
+    replayed; otherwise it checkpoints every ceil(sqrt(n_increments)) increments.
     Returns (J, dJ/dparams (9,), dJ/deuler (n_grains, 3), info)."""
+    import math
+
     import torch
 
     lib = load_library()
@@ -456,42 +464,58 @@ def history_gradient(grain_id, euler, n_increments, dt, target, weights=None, pr
         s.set_mixed_load(Edot=Edot, dt=dt)
         return s
 
+    dev = torch.device("cuda", options.get("device", 0))
     fwd = make()
     nvox = fwd.nvox
-    ckpt = {0: fwd.save_state()}
+
+    def fields_of(h):
+        eps = h.field(FIELD_STRAIN, out=torch.empty((6,) + h.shape, dtype=torch.float64, device=dev))
+        st = torch.cat([h.field(f, out=torch.empty((FIELD_COMPONENTS[f],) + h.shape, dtype=torch.float64,
+                                                   device=dev)).reshape(-1, nvox)
+                        for f in (FIELD_EPS_P, FIELD_V, FIELD_ALPHA)]).contiguous()
+        return eps.reshape(6, nvox).contiguous(), st
+
+    store_all = False
+    if checkpoint_every is None:
+        need = 8 * (6 + 34) * nvox * (n_increments + 1)
+        budget = memory_budget if memory_budget is not None else torch.cuda.mem_get_info(dev)[0] // 2
+        store_all = need <= budget
+        checkpoint_every = n_increments if store_all else max(1, math.isqrt(max(n_increments - 1, 0)) + 1)
+    ckpt = {0: fwd.save_state()} if not store_all else {}
+    stored = [fields_of(fwd)] if store_all else None
     S = []
     for k in range(1, n_increments + 1):
         fwd.step(1)
         S.append(fwd.history()[-1]["S"].copy())
-        if k % checkpoint_every == 0 and k < n_increments:
+        if store_all:
+            stored.append(fields_of(fwd))
+        elif k % checkpoint_every == 0 and k < n_increments:
             ckpt[k] = fwd.save_state()
     fwd.close()
     S = np.array(S)
     J = float(np.sum(w * (S[:, 2] - target) ** 2))
     dS = np.zeros((n_increments, 6))
     dS[:, 2] = 2.0 * w * (S[:, 2] - target)
-    dev = torch.device("cuda", options.get("device", 0))
     state_b = torch.zeros((34, nvox), dtype=torch.float64, device=dev)
     eps_b = torch.zeros((6, nvox), dtype=torch.float64, device=dev)
     pgrad = (C.c_double * 9)()
     egrad = (C.c_double * euler.size)()
     adj_iters = C.c_longlong(0)
     adj = make()
-    rep = make()
-    starts = sorted(ckpt)
+    rep = make() if not store_all else None
+    starts = [0] if store_all else sorted(ckpt)
     for seg, k0 in reversed(list(enumerate(starts))):
         k1 = starts[seg + 1] if seg + 1 < len(starts) else n_increments
-        # replay the segment from its checkpoint, keeping strain and state at k0 .. k1
-        rep.load_state(ckpt[k0])
-        fields = []
-        for k in range(k0, k1 + 1):
-            if k > k0:
-                rep.step(1)
-            eps = rep.field(FIELD_STRAIN, out=torch.empty((6,) + rep.shape, dtype=torch.float64, device=dev))
-            st = torch.cat([rep.field(f, out=torch.empty((FIELD_COMPONENTS[f],) + rep.shape, dtype=torch.float64,
-                                                         device=dev)).reshape(-1, nvox)
-                            for f in (FIELD_EPS_P, FIELD_V, FIELD_ALPHA)]).contiguous()
-            fields.append((eps.reshape(6, nvox).contiguous(), st))
+        if store_all:
+            fields = stored
+        else:
+            # replay the segment from its checkpoint, keeping strain and state at k0 .. k1
+            rep.load_state(ckpt[k0])
+            fields = []
+            for k in range(k0, k1 + 1):
+                if k > k0:
+                    rep.step(1)
+                fields.append(fields_of(rep))
         for k in range(k1, k0, -1):
             e_prev, s_prev = fields[k - 1 - k0]
             e_cur, _ = fields[k - k0]
@@ -499,8 +523,10 @@ def history_gradient(grain_id, euler, n_increments, dt, target, weights=None, pr
             _check(lib.rve_adjoint_increment(adj.h, _ptr(e_prev), _ptr(e_cur), _ptr(s_prev), d6, float(dt),
                                              _ptr(state_b), _ptr(eps_b), pgrad, egrad, C.byref(adj_iters)), adj.h)
     adj.close()
-    rep.close()
-    info = {"S": S, "adjoint_iterations": int(adj_iters.value), "checkpoints": starts}
+    if rep is not None:
+        rep.close()
+    info = {"S": S, "adjoint_iterations": int(adj_iters.value), "checkpoints": [] if store_all else starts,
+            "stored_fields": store_all}
     return J, np.array(pgrad[:]), np.array(egrad[:]).reshape(euler.shape), info
 
 

@@ -537,6 +537,9 @@ rve_status alloc_fields(rve_s* h) {
   if (h->opt.z_tile > 0) h->zHC = h->opt.z_tile;
   h->yHC = std::min(h->yHC, h->H);
   h->zHC = std::min(h->zHC, h->H);
+  // power-of-two lines run the register transforms at every width: clamp to their limit
+  if (pencil_max_hc(h->ny) > 0) h->yHC = std::min(h->yHC, pencil_max_hc(h->ny));
+  if (pencil_max_hc(h->nz) > 0) h->zHC = std::min(h->zHC, pencil_max_hc(h->nz));
   h->ysmem = y_smem<T>(h, h->yHC);
   h->zsmem = z_smem<T>(h, h->zHC);
   // x-pass partials per CTA; z-pass partials per (ky, kx) column
@@ -934,9 +937,12 @@ rve_status tune_tiles(rve_s* h) {
   if (ty) {
     float best = 1e30f;
     int bhc = h->yHC;
+    int prev = 0;
     for (int c : cands) {
-      if (c > h->H && c != cands[0] && std::min(c / 2, h->H) == h->H) continue;  // same as the previous width
-      const int hc = std::min(c, h->H);
+      const int pm = pencil_max_hc(h->ny);
+      const int hc = std::min(std::min(c, h->H), pm > 0 ? pm : c);
+      if (hc == prev) continue;  // same as the previous width
+      prev = hc;
       const size_t sm = y_smem<T>(h, hc);
       if (sm > (size_t)smax) continue;
       LineArgs<T> ya = y_args<T>(h, sp);
@@ -957,9 +963,12 @@ rve_status tune_tiles(rve_s* h) {
   if (e == cudaSuccess && tz) {
     float best = 1e30f;
     int bhc = h->zHC;
+    int prev = 0;
     for (int c : cands) {
-      if (c > h->H && c != cands[0] && std::min(c / 2, h->H) == h->H) continue;
-      const int hc = std::min(c, h->H);
+      const int pm = pencil_max_hc(h->nz);
+      const int hc = std::min(std::min(c, h->H), pm > 0 ? pm : c);
+      if (hc == prev) continue;
+      prev = hc;
       const size_t sm = z_smem<T>(h, hc);
       if (sm > (size_t)smax) continue;
       ZArgs<T> za = z_args<T>(h, sp, pp, po, 0);

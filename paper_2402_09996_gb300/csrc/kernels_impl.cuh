@@ -91,8 +91,33 @@ cudaError_t launch_adj_tangent_np(const MatDev<T>& M, long long nvox, const T* R
                                                     const T*, T, int, const double*, T*, T*, T*, T*, T*, T*,       \
                                                     const T*, cudaStream_t);
 
+// Threads of a pencil-pass CTA: N1 per line of the chunk, rounded up to whole warps.
+inline int pencil_threads(int n, int HC) {
+  const int n1 = n == 256 ? 16 : 8;
+  return (n1 * 6 * HC + 31) / 32 * 32;
+}
+// The pencil kernels serve the component-interleaved passes whose length has a split and
+// whose chunk fits one CTA.
+inline bool pencil_ok(int n, int HC) { return HC <= pencil_max_hc(n); }
+
+template <typename T, int SIGN, int N1, int N2>
+static cudaError_t launch_line_pencil(const LineArgs<T>& a, dim3 grid, cudaStream_t s) {
+  constexpr int N = N1 * N2;
+  const size_t smem = ((size_t)N + (size_t)6 * a.HC * (N + 1)) * sizeof(C2<T>);
+  cudaError_t e = set_smem<T>((const void*)k_line_pencil<T, SIGN, N1, N2>, smem);
+  if (e != cudaSuccess) return e;
+  k_line_pencil<T, SIGN, N1, N2><<<grid, pencil_threads(N, a.HC), smem, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_line(const LineArgs<T>& a, int sign, dim3 grid, size_t smem, cudaStream_t s) {
+  if (a.NC == 6 && a.hstride == 6 && pencil_ok(a.d.n, a.HC)) {
+    if (a.d.n == 64) return sign < 0 ? launch_line_pencil<T, -1, 8, 8>(a, grid, s) : launch_line_pencil<T, 1, 8, 8>(a, grid, s);
+    if (a.d.n == 128)
+      return sign < 0 ? launch_line_pencil<T, -1, 8, 16>(a, grid, s) : launch_line_pencil<T, 1, 8, 16>(a, grid, s);
+    return sign < 0 ? launch_line_pencil<T, -1, 16, 16>(a, grid, s) : launch_line_pencil<T, 1, 16, 16>(a, grid, s);
+  }
   if (sign < 0) {
     cudaError_t e = set_smem<T>((const void*)k_line<T, -1>, smem);
     if (e != cudaSuccess) return e;
@@ -105,11 +130,26 @@ cudaError_t launch_line(const LineArgs<T>& a, int sign, dim3 grid, size_t smem, 
   return cudaGetLastError();
 }
 
+template <typename T, int N1, int N2>
+static cudaError_t launch_zgreen_pencil(const ZArgs<T>& a, dim3 grid, cudaStream_t s) {
+  constexpr int N = N1 * N2;
+  const size_t smem = ((size_t)N + (size_t)6 * a.HC * (N + 1)) * sizeof(C2<T>) + (size_t)a.HC * N * sizeof(double);
+  cudaError_t e = set_smem<T>((const void*)k_zgreen<T, N1, N2>, smem);
+  if (e != cudaSuccess) return e;
+  k_zgreen<T, N1, N2><<<grid, pencil_threads(N, a.HC), smem, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_zgreen(const ZArgs<T>& a, dim3 grid, size_t smem, cudaStream_t s) {
-  cudaError_t e = set_smem<T>((const void*)k_zgreen<T>, smem);
+  if (pencil_ok(a.nz, a.HC)) {
+    if (a.nz == 64) return launch_zgreen_pencil<T, 8, 8>(a, grid, s);
+    if (a.nz == 128) return launch_zgreen_pencil<T, 8, 16>(a, grid, s);
+    return launch_zgreen_pencil<T, 16, 16>(a, grid, s);
+  }
+  cudaError_t e = set_smem<T>((const void*)k_zgreen<T, 0, 0>, smem);
   if (e != cudaSuccess) return e;
-  k_zgreen<T><<<grid, kZThreads, smem, s>>>(a);
+  k_zgreen<T, 0, 0><<<grid, kZThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -20,6 +20,10 @@ inline int rate_variant(double eta, int n_int, int nt_int) {
   return (n_int == 10 && nt_int == 10) ? 10 : -1;
 }
 
+// Largest kx chunk (HC) the two-step register transforms of the y and z passes take for a
+// line length n, 0 where n has no such split (those lengths run the Stockham kernels).
+inline int pencil_max_hc(int n) { return (n == 64 || n == 128) ? 8 : (n == 256 ? 4 : 0); }
+
 // Per-variant entry points (each instantiated in its own translation unit).
 template <typename T, int NP>
 cudaError_t launch_xpass_np(const XArgs<T>& a, bool commit, int grid, size_t smem, cudaStream_t s);

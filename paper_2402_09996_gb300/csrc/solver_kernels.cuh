@@ -15,6 +15,7 @@
 #pragma once
 
 #include "constitutive.cuh"
+#include "fft_reg.cuh"
 #include "fft_smem.cuh"
 #include "rve_common.cuh"
 
@@ -418,6 +419,51 @@ __global__ void __launch_bounds__(kLineThreads) k_line(const LineArgs<T> a) {
   }
 }
 
+// The y pass for a power-of-two line length N = N1 N2 (fft_reg.cuh), on the solver's
+// component-interleaved spectra (NC = hstride = 6).  CTA (kx chunk, outer index) as in
+// k_line; its S = 6 hc lines s sit contiguously in every row.  Thread t = n1 SP + s
+// (SP = 6 HC) loads column n1 of line s straight from global memory (rows n1 + N1 n2),
+// transforms it in registers and parks it in shared memory; then each column k2 of a line
+// is transformed and written back to rows k2 + N2 k1.  One barrier between the steps.
+constexpr int kPencilThreads = 384;  // at most N1 * 6 * HC threads per CTA
+
+template <typename T, int SIGN, int N1, int N2>
+__global__ void __launch_bounds__(kPencilThreads) k_line_pencil(const LineArgs<T> a) {
+  constexpr int N = N1 * N2;
+  constexpr int ps = N + 1;  // padded line stride in shared memory
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2<T>* tw = reinterpret_cast<C2<T>*>(smem_raw);
+  C2<T>* buf = tw + N;
+  if (a.done && *a.done) return;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int SP = 6 * a.HC;
+  const int h0 = blockIdx.x * a.HC;
+  const int S = 6 * min(a.HC, a.H - h0);
+  const int o = blockIdx.y;
+  C2<T>* g = a.spec + (size_t)(o / a.n_o2) * a.A + (size_t)(o % a.n_o2) * a.B + (size_t)h0 * 6;
+  const size_t gs = (size_t)a.stride;
+  const int s = tid % SP, n1 = tid / SP;
+  const bool mine = s < S && n1 < N1;  // the CTA has N1 * SP threads rounded up to warps
+  C2<T> v[N2];
+  if (mine) {
+#pragma unroll
+    for (int q = 0; q < N2; ++q) v[q] = g[(size_t)(n1 + N1 * q) * gs + s];
+  }
+  for (int i = tid; i < N; i += nthr) tw[i] = a.tw[i];
+  __syncthreads();
+  if (mine) pencil_step1<T, SIGN, N1, N2>(v, n1, buf + (size_t)s * ps, tw);
+  __syncthreads();
+  for (int col = tid; col < N2 * SP; col += nthr) {
+    const int s2 = col % SP, k2 = col / SP;
+    if (s2 < S) {
+      C2<T> w[N1];
+      pencil_step2<T, SIGN, N1, N2>(w, k2, buf + (size_t)s2 * ps);
+#pragma unroll
+      for (int q = 0; q < N1; ++q) g[(size_t)(k2 + N2 * q) * gs + s2] = w[q];
+    }
+  }
+}
+
 // ---------------------------------------------------------------- z pass + Green ----
 template <typename T>
 struct ZArgs {
@@ -445,8 +491,13 @@ struct ZArgs {
 
 constexpr int kZThreads = 256;
 
-template <typename T>
-__global__ void __launch_bounds__(kZThreads) k_zgreen(const ZArgs<T> a) {
+// N1 = N2 = 0: Stockham transforms of any supported nz in shared memory (two buffers,
+// line of component c and chunk column hh at (c hc + hh) ps); N1 N2 = nz: the two-step
+// register transforms of fft_reg.cuh (one buffer, line s = 6 hh + c at s ps, as in the
+// global rows).
+template <typename T, int N1, int N2>
+__global__ void __launch_bounds__(N1 > 0 ? kPencilThreads : kZThreads) k_zgreen(const ZArgs<T> a) {
+  constexpr bool kPencil = N1 > 0;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[32][kNumRed];
   __shared__ int s_last;
@@ -455,19 +506,61 @@ __global__ void __launch_bounds__(kZThreads) k_zgreen(const ZArgs<T> a) {
   const int ps = nz + 1;  // padded sequence stride
   C2<T>* b0 = tw + nz;
   C2<T>* b1 = b0 + (size_t)6 * a.HC * ps;
-  double* cres = reinterpret_cast<double*>(b1 + (size_t)6 * a.HC * ps);  // HC * nz residual terms
+  double* cres = reinterpret_cast<double*>((kPencil ? b0 : b1) + (size_t)6 * a.HC * ps);  // HC * nz residual terms
   const int tid = threadIdx.x, nthr = blockDim.x;
   if (a.done && *a.done) return;
   const int j = blockIdx.y;
   const int h0 = blockIdx.x * a.HC;
   const int hc = min(a.HC, a.H - h0);
   const size_t H = a.H, ny = a.ny;
-  for (int i = tid; i < nz; i += nthr) tw[i] = a.tw[i];
-  // component-interleaved spectra: for each kz the CTA's hc * 6 values are contiguous
-  tile_move<T, true>(b0, ps, a.spec + ((size_t)j * H + h0) * 6, ny * H * 6, nz, 6 * hc, 6, hc, tid, nthr);
-  __syncthreads();
-  C2<T>* res = smem_fft<T, -1>(b0, b1, a.dz, 6 * hc, ps, tw, tid, nthr);
-  C2<T>* oth = (res == b0) ? b1 : b0;
+  C2<T>* gz = a.spec + ((size_t)j * H + h0) * 6;
+  const size_t gs = ny * H * 6;
+  // line of (component c, chunk column hh) in shared memory
+  auto line = [&](int c, int hh) -> size_t { return (size_t)(kPencil ? hh * 6 + c : c * hc + hh) * ps; };
+  C2<T>* res;
+  C2<T>* oth = nullptr;
+  if constexpr (kPencil) {
+    // forward z transform: both steps, then the result in natural order in b0
+    const int SP = 6 * a.HC, S = 6 * hc;
+    const int s = tid % SP, n1 = tid / SP;
+    const bool mine = s < S && n1 < N1;  // the CTA has N1 * SP threads rounded up to warps
+    C2<T> v[N2];
+    if (mine) {
+#pragma unroll
+      for (int q = 0; q < N2; ++q) v[q] = gz[(size_t)(n1 + N1 * q) * gs + s];
+    }
+    for (int i = tid; i < nz; i += nthr) tw[i] = a.tw[i];
+    __syncthreads();
+    if (mine) pencil_step1<T, -1, N1, N2>(v, n1, b0 + (size_t)s * ps, tw);
+    __syncthreads();
+    constexpr int kCols = (N2 + N1 - 1) / N1;  // columns per thread (N2 * SP columns, N1 * SP threads)
+    C2<T> w[kCols][N1];
+#pragma unroll
+    for (int r = 0; r < kCols; ++r) {
+      const int col = tid + r * nthr;
+      const int s2 = col % SP, k2 = col / SP;
+      if (col < N2 * SP && s2 < S) pencil_step2<T, -1, N1, N2>(w[r], k2, b0 + (size_t)s2 * ps);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kCols; ++r) {
+      const int col = tid + r * nthr;
+      const int s2 = col % SP, k2 = col / SP;
+      if (col < N2 * SP && s2 < S) {
+#pragma unroll
+        for (int q = 0; q < N1; ++q) b0[(size_t)s2 * ps + k2 + N2 * q] = w[r][q];
+      }
+    }
+    __syncthreads();
+    res = b0;
+  } else {
+    for (int i = tid; i < nz; i += nthr) tw[i] = a.tw[i];
+    // component-interleaved spectra: for each kz the CTA's hc * 6 values are contiguous
+    tile_move<T, true>(b0, ps, gz, gs, nz, 6 * hc, 6, hc, tid, nthr);
+    __syncthreads();
+    res = smem_fft<T, -1>(b0, b1, a.dz, 6 * hc, ps, tw, tid, nthr);
+    oth = (res == b0) ? b1 : b0;
+  }
 
   const int it = a.it >= 0 ? a.it : a.st->it_dev;
   const double* En = a.st->E[(it + 1) & 1];
@@ -491,7 +584,7 @@ __global__ void __launch_bounds__(kZThreads) k_zgreen(const ZArgs<T> a) {
     C2<T> t[6];
     const size_t g0 = (((size_t)kz * ny + j) * H + h) * 6;
 #pragma unroll
-    for (int c = 0; c < 6; ++c) t[c] = res[(size_t)(c * hc + hh) * ps + kz];
+    for (int c = 0; c < 6; ++c) t[c] = res[line(c, hh) + kz];
     // equilibrium residual kappa . sigma_hat = kappa . (tau_hat - tau_hat_prev)
     {
       C2<T> d[6];
@@ -543,11 +636,36 @@ __global__ void __launch_bounds__(kZThreads) k_zgreen(const ZArgs<T> a) {
       }
     }
 #pragma unroll
-    for (int c = 0; c < 6; ++c) res[(size_t)(c * hc + hh) * ps + kz] = e[c];
+    for (int c = 0; c < 6; ++c) res[line(c, hh) + kz] = e[c];
   }
   __syncthreads();
-  C2<T>* out = smem_fft<T, +1>(res, oth, a.dz, 6 * hc, ps, tw, tid, nthr);
-  tile_move<T, false>(out, ps, a.spec + ((size_t)j * H + h0) * 6, ny * H * 6, nz, 6 * hc, 6, hc, tid, nthr);
+  if constexpr (kPencil) {
+    // inverse z transform: step 1 reads its column from b0 (all reads before the writes),
+    // step 2 writes the rows to global memory
+    const int SP = 6 * a.HC, S = 6 * hc;
+    const int s = tid % SP, n1 = tid / SP;
+    const bool mine = s < S && n1 < N1;
+    C2<T> v[N2];
+    if (mine) {
+#pragma unroll
+      for (int q = 0; q < N2; ++q) v[q] = b0[(size_t)s * ps + n1 + N1 * q];
+    }
+    __syncthreads();
+    if (mine) pencil_step1<T, +1, N1, N2>(v, n1, b0 + (size_t)s * ps, tw);
+    __syncthreads();
+    for (int col = tid; col < N2 * SP; col += nthr) {
+      const int s2 = col % SP, k2 = col / SP;
+      if (s2 < S) {
+        C2<T> w2[N1];
+        pencil_step2<T, +1, N1, N2>(w2, k2, b0 + (size_t)s2 * ps);
+#pragma unroll
+        for (int q = 0; q < N1; ++q) gz[(size_t)(k2 + N2 * q) * gs + s2] = w2[q];
+      }
+    }
+  } else {
+    C2<T>* out = smem_fft<T, +1>(res, oth, a.dz, 6 * hc, ps, tw, tid, nthr);
+    tile_move<T, false>(out, ps, gz, gs, nz, 6 * hc, 6, hc, tid, nthr);
+  }
   // residual: one partial per (ky, kx) column, summed over kz in a fixed order (lane l
   // takes kz = l, l + 32, ...; then a fixed shuffle tree), so the total does not depend on
   // how many kx columns a CTA holds
@@ -572,23 +690,34 @@ __global__ void __launch_bounds__(kZThreads) k_zgreen(const ZArgs<T> a) {
   __syncthreads();
   if (s_last) {
     __threadfence();
+    // the column partials summed in the order of 256 lanes (8 warps) whatever the block
+    // size: lane vl takes b = vl, vl + 256, ... with four accumulators, each warp of lanes
+    // adds by a shuffle tree, then warp 0 adds the 8 warp sums
+    constexpr int kVL = 256;
+    const size_t np = ny * H;
+    const int lane = tid & 31;
+    for (int vl = tid; vl < kVL; vl += nthr) {
+      double q0 = 0.0, q1 = 0.0, q2 = 0.0, q3 = 0.0;
+      size_t b = vl;
+      for (; b + 3 * (size_t)kVL < np; b += 4 * (size_t)kVL) {
+        q0 += __ldcg(&a.partial[b]);
+        q1 += __ldcg(&a.partial[b + kVL]);
+        q2 += __ldcg(&a.partial[b + 2 * (size_t)kVL]);
+        q3 += __ldcg(&a.partial[b + 3 * (size_t)kVL]);
+      }
+      for (; b < np; b += kVL) q0 += __ldcg(&a.partial[b]);
+      double w = (q0 + q1) + (q2 + q3);
+      warp_sum<1>(&w);
+      if (lane == 0) red[vl >> 5][0] = w;
+    }
+    __syncthreads();
     double v[kNumRed];
 #pragma unroll
     for (int i = 0; i < kNumRed; ++i) v[i] = 0.0;
-    {  // four independent accumulators keep the loads in flight; fixed order
-      const size_t np = ny * H;
-      double q0 = 0.0, q1 = 0.0, q2 = 0.0, q3 = 0.0;
-      size_t b = tid;
-      for (; b + 3 * (size_t)nthr < np; b += 4 * (size_t)nthr) {
-        q0 += __ldcg(&a.partial[b]);
-        q1 += __ldcg(&a.partial[b + nthr]);
-        q2 += __ldcg(&a.partial[b + 2 * (size_t)nthr]);
-        q3 += __ldcg(&a.partial[b + 3 * (size_t)nthr]);
-      }
-      for (; b < np; b += nthr) q0 += __ldcg(&a.partial[b]);
-      v[0] = (q0 + q1) + (q2 + q3);
+    if (tid < 32) {
+      v[0] = lane < kVL / 32 ? red[lane][0] : 0.0;
+      warp_sum<1>(v);
     }
-    block_sum<1>(v, red);
     if (tid == 0) {
       IterStatus* st = a.st;
       const double* S = st->sig_mean;

@@ -46,12 +46,15 @@ def test_two_grain_fixed_iterations_fp64(lib, cuda):
     _compare_histories(got, ref.history, 1e-9)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_ragged_voronoi_tolerance_mode(lib, cuda, prec):
-    """6 x 10 x 12 grid (radix-3/5 lengths, odd line counts), 5 twinned grains, 3 increments."""
+@pytest.mark.parametrize("shape,prec", [((12, 10, 6), "fp64"), ((12, 10, 6), "fp32"), ((64, 64, 6), "fp64"),
+                                        ((64, 64, 6), "fp32"), ((256, 8, 4), "fp64"), ((8, 256, 4), "fp32")])
+def test_ragged_voronoi_tolerance_mode(lib, cuda, shape, prec):
+    """5 twinned grains, 4 increments: a 6 x 10 x 12 grid (radix-3/5 lengths, odd line
+    counts, shared-memory Stockham transforms), and grids whose y and z lines have the
+    power-of-two lengths of the two-step register transforms (64, and 256 along z or y)."""
     from paper_2402_09996_gb300 import inputs, rve
 
-    inp = inputs.make_inputs((12, 10, 6), 5, 0.5, seed=42)
+    inp = inputs.make_inputs(shape, 5, 0.5, seed=42)
     gid = label_rve(inp)
     p = rve.FP64 if prec == "fp64" else rve.FP32
     ref = _oracle(gid, inp.euler)
@@ -215,14 +218,16 @@ def test_graph_loop_equals_host_driven_loop(lib, cuda, shape, prec, fixed):
     assert np.array_equal(s1, s0) and np.array_equal(a1, a0)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_fft_tile_widths_do_not_change_results(lib, cuda, prec):
+@pytest.mark.parametrize("shape,prec", [((20, 24, 32), "fp64"), ((20, 24, 32), "fp32"), ((64, 64, 16), "fp64"),
+                                        ((128, 64, 12), "fp32")])
+def test_fft_tile_widths_do_not_change_results(lib, cuda, shape, prec):
     """The y / z pass kx tile widths (forced to 1 or 16, or chosen by the autotuner) leave
     every result bit-identical: each sequence's FFT is the same arithmetic and the
-    residual is summed per (ky, kx) column in a fixed order."""
+    residual is summed per (ky, kx) column in a fixed order.  Power-of-two line lengths
+    (64, 128) run the two-step register transforms at every width (16 is clamped)."""
     from paper_2402_09996_gb300 import inputs, rve
 
-    inp = inputs.make_inputs((20, 24, 32), 7, 0.5, seed=99)
+    inp = inputs.make_inputs(shape, 7, 0.5, seed=99)
     gid = label_rve(inp)
     p = rve.FP64 if prec == "fp64" else rve.FP32
     out = []

@@ -594,15 +594,17 @@ __global__ void __launch_bounds__(N1 > 0 ? kPencilThreads : kZThreads) k_zgreen(
         d[c] = csub<T>(t[c], p);
         a.P_out[g0 + c] = t[c];
       }
-      // symmetric order (11,22,33,23,13,12): row i of d times kappa
-      const double r0x = (double)d[0].x * k0 + (double)d[5].x * k1 + (double)d[4].x * k2;
-      const double r0y = (double)d[0].y * k0 + (double)d[5].y * k1 + (double)d[4].y * k2;
-      const double r1x = (double)d[5].x * k0 + (double)d[1].x * k1 + (double)d[3].x * k2;
-      const double r1y = (double)d[5].y * k0 + (double)d[1].y * k1 + (double)d[3].y * k2;
-      const double r2x = (double)d[4].x * k0 + (double)d[3].x * k1 + (double)d[2].x * k2;
-      const double r2y = (double)d[4].y * k0 + (double)d[3].y * k1 + (double)d[2].y * k2;
-      const double wgt = (h == 0 || 2 * h == a.nx) ? 1.0 : 2.0;
-      cres[hh * nz + kz] = wgt * (r0x * r0x + r0y * r0y + r1x * r1x + r1y * r1y + r2x * r2x + r2y * r2y);
+      // symmetric order (11,22,33,23,13,12): row i of d times kappa.  The point's term is
+      // formed in the field precision (its rounding, relative 1e-7 in float, is far below
+      // the tolerances the error is compared with); the sums over points are FP64.
+      const T r0x = d[0].x * k0 + d[5].x * k1 + d[4].x * k2;
+      const T r0y = d[0].y * k0 + d[5].y * k1 + d[4].y * k2;
+      const T r1x = d[5].x * k0 + d[1].x * k1 + d[3].x * k2;
+      const T r1y = d[5].y * k0 + d[1].y * k1 + d[3].y * k2;
+      const T r2x = d[4].x * k0 + d[3].x * k1 + d[2].x * k2;
+      const T r2y = d[4].y * k0 + d[3].y * k1 + d[2].y * k2;
+      const T wgt = (h == 0 || 2 * h == a.nx) ? T(1) : T(2);
+      cres[hh * nz + kz] = (double)(wgt * (r0x * r0x + r0y * r0y + r1x * r1x + r1y * r1y + r2x * r2x + r2y * r2y));
     }
     const T kk = k0 * k0 + k1 * k1 + k2 * k2;
     C2<T> e[6];

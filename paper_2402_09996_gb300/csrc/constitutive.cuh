@@ -22,6 +22,8 @@
 //   NP = 0   anything else (eta = 0 or non-integer exponents): generic per-system solve.
 #pragma once
 
+#include <type_traits>
+
 #include "rve_common.cuh"
 
 namespace rve {
@@ -315,6 +317,70 @@ __device__ __forceinline__ T reg_rate_slip(T a, const RootCoef<T>& q, int n_int,
   return on ? rho : T(0);
 }
 
+// The float solves of two systems of one class at once, on packed two-lane FP32
+// arithmetic (one issue slot per pair of FMAs or products).  Each lane performs the
+// operations of reg_rate_slip / reg_rate_tab in the same order and rounding; the
+// logarithms, exponentials and reciprocals stay per lane.
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+
+template <int NP>
+__device__ __forceinline__ float2 root_zn1_2(float2 z, const RootCoef<float>& q, int n_int) {
+  if constexpr (NP > 0) {
+    // z^(NP-1) by the binary powering of cpow<NP - 1>, both lanes at once
+    float2 r = z;
+    constexpr int e = NP - 1;
+    if constexpr (e == 9) {
+      const float2 h2 = __fmul2_rn(z, z), h4 = __fmul2_rn(h2, h2), h8 = __fmul2_rn(h4, h4);
+      r = __fmul2_rn(z, h8);
+    } else {
+      r = make_float2(cpow<NP - 1, float>(z.x), cpow<NP - 1, float>(z.y));
+    }
+    return r;
+  } else {
+    const float2 l = __fmul2_rn(f2(q.nm1), make_float2(fast_log2<float>(z.x), fast_log2<float>(z.y)));
+    return make_float2(fast_exp2<float>(l.x), fast_exp2<float>(l.y));
+  }
+}
+
+template <int NP>
+__device__ __forceinline__ float2 root_newton2(float2 z, float2 aa, const RootCoef<float>& q, int n_int) {
+  const float2 zn1 = root_zn1_2<NP>(z, q, n_int);
+  const float2 phi = __ffma2_rn(z, __ffma2_rn(f2(q.c), zn1, f2(q.Kn)), make_float2(-aa.x, -aa.y));
+  const float2 den = __ffma2_rn(f2(q.c), zn1, f2(q.Kn_n));
+  const float2 r = make_float2(fast_rcp<float>(den.x), fast_rcp<float>(den.y));
+  const float2 w = __ffma2_rn(make_float2(-phi.x, -phi.y), r, z);
+  return __fmul2_rn(f2(q.Pout), __fmul2_rn(zn1, w));
+}
+
+template <int NP>
+__device__ __forceinline__ float2 reg_rate_slip2(float2 a, const RootCoef<float>& q, int n_int, const float* tab) {
+  const bool on0 = a.x > 0.f, on1 = a.y > 0.f;
+  const float2 aa = make_float2(on0 ? a.x : 1.f, on1 ? a.y : 1.f);
+  const float2 la = make_float2(fast_log2<float>(aa.x), fast_log2<float>(aa.y));
+  const float2 t = __ffma2_rn(la, f2(q.a2), f2(q.b2));
+  const float2* tb = reinterpret_cast<const float2*>(tab);
+  const float2 ab0 = tb[root_interval<float>(t.x)], ab1 = tb[root_interval<float>(t.y)];
+  const float2 ex = __ffma2_rn(make_float2(ab0.y, ab1.y), la, make_float2(ab0.x, ab1.x));
+  const float2 z = make_float2(fast_exp2<float>(ex.x), fast_exp2<float>(ex.y));
+  const float2 rho = root_newton2<NP>(z, aa, q, n_int);
+  return make_float2(on0 ? rho.x : 0.f, on1 ? rho.y : 0.f);
+}
+
+template <int NP>
+__device__ __forceinline__ float2 reg_rate_tab2(float2 a, const RootCoef<float>& q, int n_int, const float* tab) {
+  const bool on0 = a.x > 0.f, on1 = a.y > 0.f;
+  const float2 aa = make_float2(on0 ? a.x : 1.f, on1 ? a.y : 1.f);
+  const float2 la = make_float2(fast_log2<float>(aa.x), fast_log2<float>(aa.y));
+  const float2 lzB = __ffma2_rn(la, f2(q.a1), f2(q.b1));
+  const float2 t = __ffma2_rn(la, f2(q.a2), f2(q.b2));
+  const float2* tb = reinterpret_cast<const float2*>(tab);
+  const float2 ab0 = tb[root_interval<float>(t.x)], ab1 = tb[root_interval<float>(t.y)];
+  const float2 ex = __fadd2_rn(lzB, __ffma2_rn(make_float2(ab0.y, ab1.y), t, make_float2(ab0.x, ab1.x)));
+  const float2 z = make_float2(fast_exp2<float>(ex.x), fast_exp2<float>(ex.y));
+  const float2 rho = root_newton2<NP>(z, aa, q, n_int);
+  return make_float2(on0 ? rho.x : 0.f, on1 ? rho.y : 0.f);
+}
+
 // Generic solve (any eta >= 0 and exponent n >= 1): per-system branch, a smooth-minimum
 // start u0 = (1 + beta^m)^(-1/m) of the asymptotes (m makes it exact at beta = 1; within
 // 5 % for n >= 1.5) and a fixed Newton count (4 in float, 6 in double).
@@ -357,6 +423,10 @@ __device__ __forceinline__ T stage_rate(const MatDev<T>& M, const RootCoef<T>& q
                 : reg_rate<T>(a, P, M.K, M.n, M.n_int, M.inv_n, M.sm, M.lg_K, M.eta, M.lg_eta, lg_P);
   }
 }
+
+// Packed two-lane solves: float with a table-started solve.
+template <typename T, int NP>
+constexpr bool kPackedSolve = std::is_same<T, float>::value && NP != 0;
 
 // Evaluates the rates at elastic strain e0 + s*de - yt.ep and state yt, adds
 // wacc * rates to acc and overwrites yt with y0 + cnext * rates.
@@ -413,26 +483,57 @@ __device__ __forceinline__ void rk_stage(const MatDev<T>& M, const T* e0, const 
   for (int c = 0; c < 6; ++c) ss[c] = sg[c] * sys_scale<T>(0);
   T du_s[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
   T du_t[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+  // the systems in pairs: both driving forces, both rates (packed solve in float), then
+  // each system folded into acc / yt
 #pragma unroll
-  for (int k = 0; k < 12; ++k) {
-    const T tek = schmid_sum<T>(k, ss) - M.c * yt.al[k];
-    const T ak = fabs(tek) - ((M.r0[k] + Rb_s) - Qdq_s * ex[k]);
-    const T rk = stage_rate<T, NP>(M, qs, ak, T(1), false, T(0), tab);
-    const T gd = copysign(rk, tek);  // rk = 0 unless |tek| > r > 0
-    schmid_add<T>(k, gd, du_s);
-    const T ald = gd - M.d * rk * yt.al[k];
-    acc.v[k] += wacc * rk;
-    yt.v[k] = y0.v[k] + cnext * rk;
-    acc.al[k] += wacc * ald;
-    yt.al[k] = y0.al[k] + cnext * ald;
+  for (int k = 0; k < 12; k += 2) {
+    const T tek0 = schmid_sum<T>(k, ss) - M.c * yt.al[k];
+    const T tek1 = schmid_sum<T>(k + 1, ss) - M.c * yt.al[k + 1];
+    const T ak0 = fabs(tek0) - ((M.r0[k] + Rb_s) - Qdq_s * ex[k]);
+    const T ak1 = fabs(tek1) - ((M.r0[k + 1] + Rb_s) - Qdq_s * ex[k + 1]);
+    T rk2[2];
+    if constexpr (kPackedSolve<T, NP>) {
+      const float2 r = reg_rate_slip2<NP>(make_float2(ak0, ak1), qs, M.n_int, tab);
+      rk2[0] = r.x;
+      rk2[1] = r.y;
+    } else {
+      rk2[0] = stage_rate<T, NP>(M, qs, ak0, T(1), false, T(0), tab);
+      rk2[1] = stage_rate<T, NP>(M, qs, ak1, T(1), false, T(0), tab);
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int q = k + u;
+      const T rk = rk2[u];
+      const T gd = copysign(rk, u ? tek1 : tek0);  // rk = 0 unless |tek| > r > 0
+      schmid_add<T>(q, gd, du_s);
+      const T ald = gd - M.d * rk * yt.al[q];
+      acc.v[q] += wacc * rk;
+      yt.v[q] = y0.v[q] + cnext * rk;
+      acc.al[q] += wacc * ald;
+      yt.al[q] = y0.al[q] + cnext * ald;
+    }
   }
 #pragma unroll
-  for (int k = 12; k < 16; ++k) {
-    const T ak = sys_scale<T>(k) * schmid_sum<T>(k, sg) - ((M.r0[k] + Rb_t) - Qdq_t * ex[k]);
-    const T rk = stage_rate<T, NP>(M, qt, ak, Ptw, true, lg_Ptw, tab);
-    schmid_add<T>(k, rk, du_t);
-    acc.v[k] += wacc * rk;
-    yt.v[k] = y0.v[k] + cnext * rk;
+  for (int k = 12; k < 16; k += 2) {
+    const T ak0 = sys_scale<T>(k) * schmid_sum<T>(k, sg) - ((M.r0[k] + Rb_t) - Qdq_t * ex[k]);
+    const T ak1 = sys_scale<T>(k + 1) * schmid_sum<T>(k + 1, sg) - ((M.r0[k + 1] + Rb_t) - Qdq_t * ex[k + 1]);
+    T rk2[2];
+    if constexpr (kPackedSolve<T, NP>) {
+      const float2 r = reg_rate_tab2<NP>(make_float2(ak0, ak1), qt, M.nt_int, tab + kRootTabLen);
+      rk2[0] = r.x;
+      rk2[1] = r.y;
+    } else {
+      rk2[0] = stage_rate<T, NP>(M, qt, ak0, Ptw, true, lg_Ptw, tab);
+      rk2[1] = stage_rate<T, NP>(M, qt, ak1, Ptw, true, lg_Ptw, tab);
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int q = k + u;
+      const T rk = rk2[u];
+      schmid_add<T>(q, rk, du_t);
+      acc.v[q] += wacc * rk;
+      yt.v[q] = y0.v[q] + cnext * rk;
+    }
   }
   // eps_p rate = (1 - sum f) sum_s gdot_s m_s + sum_b gdot_b m_b, m = scale sym(n x l)
   const T fs = wslip * sys_scale<T>(0);

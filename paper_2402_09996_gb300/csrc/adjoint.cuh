@@ -31,7 +31,9 @@ struct StageVals {
   T Rb_s, Rb_t;
 };
 
-// Forward stage (the same arithmetic as rk_stage): rates k of state Y at path point s,
+// Forward stage (the operations of rk_stage, one system at a time; the float primal runs
+// pairs of systems on packed instructions, which may round the last bit differently):
+// rates k of state Y at path point s,
 // with the intermediates kept for the reverse pass.  SOLVE = false takes the rates rho of
 // the 16 systems from rho_in (a stage evaluated before with the same Y and s) instead of
 // solving for them, and rebuilds everything else.

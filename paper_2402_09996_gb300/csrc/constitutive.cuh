@@ -428,14 +428,40 @@ __device__ __forceinline__ T stage_rate(const MatDev<T>& M, const RootCoef<T>& q
 template <typename T, int NP>
 constexpr bool kPackedSolve = std::is_same<T, float>::value && NP != 0;
 
+// Two values of a pair of systems (or components).  Float: one packed two-lane FP32
+// instruction per operation; double: the scalar expressions.
+template <typename T> struct PairT;
+template <> struct PairT<float> { using type = float2; };
+template <> struct PairT<double> { using type = double2; };
+template <typename T> using pair_t = typename PairT<T>::type;
+
+template <typename T>
+__device__ __forceinline__ pair_t<T> pmk(T a, T b) {
+  pair_t<T> r;
+  r.x = a;
+  r.y = b;
+  return r;
+}
+template <typename T>
+__device__ __forceinline__ pair_t<T> pfma(pair_t<T> a, pair_t<T> b, pair_t<T> c) {  // a b + c
+  if constexpr (std::is_same<T, float>::value) return __ffma2_rn(a, b, c);
+  else return pmk<T>(a.x * b.x + c.x, a.y * b.y + c.y);
+}
+template <typename T>
+__device__ __forceinline__ pair_t<T> pmul(pair_t<T> a, pair_t<T> b) {
+  if constexpr (std::is_same<T, float>::value) return __fmul2_rn(a, b);
+  else return pmk<T>(a.x * b.x, a.y * b.y);
+}
+
 // Evaluates the rates at elastic strain e0 + s*de - yt.ep and state yt, adds
 // wacc * rates to acc and overwrites yt with y0 + cnext * rates.
 // tab: the rate-root tables (slip systems' at 0, twin exponent's at kRootTabLen), NP != 0 only.
-// Each system is resolved, solved and folded into acc / yt before the next one (yt.v and
-// yt.al of system k are read before they are overwritten; the hardening terms use the
-// stage's yt.v, computed first).  With NP != 0 the solves are branch-free, so the whole
-// stage is one basic block the compiler interleaves; this order keeps fewer values live
-// than solving all 16 systems first.
+// The systems go in pairs (k, k + 1): both are resolved, solved and folded into acc / yt
+// before the next pair (yt.v and yt.al of a pair are read before they are overwritten;
+// the hardening terms use the stage's yt.v, computed first).  In float the pair's
+// arithmetic runs on packed two-lane instructions.  With NP != 0 the solves are
+// branch-free, so the whole stage is one basic block the compiler interleaves; this order
+// keeps fewer values live than solving all 16 systems first.
 // Rewritten forms (same quantities): with e_k = exp(-b v_k) = 1 - g_k,
 //   r_k = r0_k + Q (h_off sum g + (h_diag - h_off) g_k) = (r0_k + Q (h_off (N - sum e) + dq)) - Q dq e_k;
 // the slip stresses share the Schmid scale 1/sqrt6 (applied once to sigma), and the
@@ -453,15 +479,22 @@ __device__ __forceinline__ void rk_stage(const MatDev<T>& M, const T* e0, const 
   T Es = T(0), Et = T(0), vtw = T(0);
   const T cb_s = -M.b_s * T(kLog2e), cb_t = -M.b_b * T(kLog2e);
 #pragma unroll
-  for (int k = 0; k < 12; ++k) {
-    ex[k] = fast_exp2<T>(cb_s * yt.v[k]);
+  for (int k = 0; k < 12; k += 2) {
+    const pair_t<T> p = pmul<T>(pmk<T>(cb_s, cb_s), pmk<T>(yt.v[k], yt.v[k + 1]));
+    ex[k] = fast_exp2<T>(p.x);
+    ex[k + 1] = fast_exp2<T>(p.y);
     Es += ex[k];
+    Es += ex[k + 1];
   }
 #pragma unroll
-  for (int k = 12; k < 16; ++k) {
-    ex[k] = fast_exp2<T>(cb_t * yt.v[k]);
+  for (int k = 12; k < 16; k += 2) {
+    const pair_t<T> p = pmul<T>(pmk<T>(cb_t, cb_t), pmk<T>(yt.v[k], yt.v[k + 1]));
+    ex[k] = fast_exp2<T>(p.x);
+    ex[k + 1] = fast_exp2<T>(p.y);
     Et += ex[k];
+    Et += ex[k + 1];
     vtw += yt.v[k];
+    vtw += yt.v[k + 1];
   }
   const T ftot = T(1.41421356237309504880) * vtw;
   const T wslip = T(1) - ftot;
@@ -487,10 +520,13 @@ __device__ __forceinline__ void rk_stage(const MatDev<T>& M, const T* e0, const 
   // each system folded into acc / yt
 #pragma unroll
   for (int k = 0; k < 12; k += 2) {
-    const T tek0 = schmid_sum<T>(k, ss) - M.c * yt.al[k];
-    const T tek1 = schmid_sum<T>(k + 1, ss) - M.c * yt.al[k + 1];
-    const T ak0 = fabs(tek0) - ((M.r0[k] + Rb_s) - Qdq_s * ex[k]);
-    const T ak1 = fabs(tek1) - ((M.r0[k + 1] + Rb_s) - Qdq_s * ex[k + 1]);
+    const pair_t<T> alk = pmk<T>(yt.al[k], yt.al[k + 1]);
+    const pair_t<T> tk = pfma<T>(pmk<T>(-M.c, -M.c), alk, pmk<T>(schmid_sum<T>(k, ss), schmid_sum<T>(k + 1, ss)));
+    const pair_t<T> rr = pfma<T>(pmk<T>(-Qdq_s, -Qdq_s), pmk<T>(ex[k], ex[k + 1]),
+                                 pmk<T>(M.r0[k] + Rb_s, M.r0[k + 1] + Rb_s));
+    const T tek0 = tk.x, tek1 = tk.y;
+    const T ak0 = fabs(tek0) - rr.x;
+    const T ak1 = fabs(tek1) - rr.y;
     T rk2[2];
     if constexpr (kPackedSolve<T, NP>) {
       const float2 r = reg_rate_slip2<NP>(make_float2(ak0, ak1), qs, M.n_int, tab);
@@ -500,23 +536,33 @@ __device__ __forceinline__ void rk_stage(const MatDev<T>& M, const T* e0, const 
       rk2[0] = stage_rate<T, NP>(M, qs, ak0, T(1), false, T(0), tab);
       rk2[1] = stage_rate<T, NP>(M, qs, ak1, T(1), false, T(0), tab);
     }
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const int q = k + u;
-      const T rk = rk2[u];
-      const T gd = copysign(rk, u ? tek1 : tek0);  // rk = 0 unless |tek| > r > 0
-      schmid_add<T>(q, gd, du_s);
-      const T ald = gd - M.d * rk * yt.al[q];
-      acc.v[q] += wacc * rk;
-      yt.v[q] = y0.v[q] + cnext * rk;
-      acc.al[q] += wacc * ald;
-      yt.al[q] = y0.al[q] + cnext * ald;
-    }
+    const T gd0 = copysign(rk2[0], tek0);  // rk = 0 unless |tek| > r > 0
+    const T gd1 = copysign(rk2[1], tek1);
+    schmid_add<T>(k, gd0, du_s);
+    schmid_add<T>(k + 1, gd1, du_s);
+    const pair_t<T> rk = pmk<T>(rk2[0], rk2[1]);
+    const pair_t<T> drk = pmul<T>(pmk<T>(-M.d, -M.d), rk);
+    const pair_t<T> ald = pfma<T>(drk, alk, pmk<T>(gd0, gd1));  // gd - d rk alpha
+    const pair_t<T> wa = pmk<T>(wacc, wacc), cn = pmk<T>(cnext, cnext);
+    const pair_t<T> av = pfma<T>(wa, rk, pmk<T>(acc.v[k], acc.v[k + 1]));
+    const pair_t<T> yv = pfma<T>(cn, rk, pmk<T>(y0.v[k], y0.v[k + 1]));
+    const pair_t<T> aa = pfma<T>(wa, ald, pmk<T>(acc.al[k], acc.al[k + 1]));
+    const pair_t<T> ya = pfma<T>(cn, ald, pmk<T>(y0.al[k], y0.al[k + 1]));
+    acc.v[k] = av.x;
+    acc.v[k + 1] = av.y;
+    yt.v[k] = yv.x;
+    yt.v[k + 1] = yv.y;
+    acc.al[k] = aa.x;
+    acc.al[k + 1] = aa.y;
+    yt.al[k] = ya.x;
+    yt.al[k + 1] = ya.y;
   }
 #pragma unroll
   for (int k = 12; k < 16; k += 2) {
-    const T ak0 = sys_scale<T>(k) * schmid_sum<T>(k, sg) - ((M.r0[k] + Rb_t) - Qdq_t * ex[k]);
-    const T ak1 = sys_scale<T>(k + 1) * schmid_sum<T>(k + 1, sg) - ((M.r0[k + 1] + Rb_t) - Qdq_t * ex[k + 1]);
+    const pair_t<T> rr = pfma<T>(pmk<T>(-Qdq_t, -Qdq_t), pmk<T>(ex[k], ex[k + 1]),
+                                 pmk<T>(M.r0[k] + Rb_t, M.r0[k + 1] + Rb_t));
+    const T ak0 = sys_scale<T>(k) * schmid_sum<T>(k, sg) - rr.x;
+    const T ak1 = sys_scale<T>(k + 1) * schmid_sum<T>(k + 1, sg) - rr.y;
     T rk2[2];
     if constexpr (kPackedSolve<T, NP>) {
       const float2 r = reg_rate_tab2<NP>(make_float2(ak0, ak1), qt, M.nt_int, tab + kRootTabLen);
@@ -526,24 +572,31 @@ __device__ __forceinline__ void rk_stage(const MatDev<T>& M, const T* e0, const 
       rk2[0] = stage_rate<T, NP>(M, qt, ak0, Ptw, true, lg_Ptw, tab);
       rk2[1] = stage_rate<T, NP>(M, qt, ak1, Ptw, true, lg_Ptw, tab);
     }
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const int q = k + u;
-      const T rk = rk2[u];
-      schmid_add<T>(q, rk, du_t);
-      acc.v[q] += wacc * rk;
-      yt.v[q] = y0.v[q] + cnext * rk;
-    }
+    schmid_add<T>(k, rk2[0], du_t);
+    schmid_add<T>(k + 1, rk2[1], du_t);
+    const pair_t<T> rk = pmk<T>(rk2[0], rk2[1]);
+    const pair_t<T> av = pfma<T>(pmk<T>(wacc, wacc), rk, pmk<T>(acc.v[k], acc.v[k + 1]));
+    const pair_t<T> yv = pfma<T>(pmk<T>(cnext, cnext), rk, pmk<T>(y0.v[k], y0.v[k + 1]));
+    acc.v[k] = av.x;
+    acc.v[k + 1] = av.y;
+    yt.v[k] = yv.x;
+    yt.v[k + 1] = yv.y;
   }
   // eps_p rate = (1 - sum f) sum_s gdot_s m_s + sum_b gdot_b m_b, m = scale sym(n x l)
   const T fs = wslip * sys_scale<T>(0);
   const T fsh = T(0.5) * fs;
+  const T tsc = sys_scale<T>(12), tsh = T(0.5) * sys_scale<T>(12);
 #pragma unroll
-  for (int c = 0; c < 6; ++c) {
-    const T dep = c < 3 ? fs * du_s[c] + sys_scale<T>(12) * du_t[c]
-                        : fsh * du_s[c] + (T(0.5) * sys_scale<T>(12)) * du_t[c];
-    acc.ep[c] += wacc * dep;
-    yt.ep[c] = y0.ep[c] + cnext * dep;
+  for (int c = 0; c < 6; c += 2) {
+    const pair_t<T> dep = pfma<T>(pmk<T>(c < 3 ? fs : fsh, c + 1 < 3 ? fs : fsh), pmk<T>(du_s[c], du_s[c + 1]),
+                                  pmul<T>(pmk<T>(c < 3 ? tsc : tsh, c + 1 < 3 ? tsc : tsh),
+                                          pmk<T>(du_t[c], du_t[c + 1])));
+    const pair_t<T> ae = pfma<T>(pmk<T>(wacc, wacc), dep, pmk<T>(acc.ep[c], acc.ep[c + 1]));
+    const pair_t<T> ye = pfma<T>(pmk<T>(cnext, cnext), dep, pmk<T>(y0.ep[c], y0.ep[c + 1]));
+    acc.ep[c] = ae.x;
+    acc.ep[c + 1] = ae.y;
+    yt.ep[c] = ye.x;
+    yt.ep[c + 1] = ye.y;
   }
 }
 

@@ -472,9 +472,29 @@ __device__ __forceinline__ void rk_stage(const MatDev<T>& M, const T* e0, const 
                                          T cnext, const T* tab) {
   constexpr double kLog2e = 1.44269504088896340736;
   T e[6], sg[6];
+  if constexpr (std::is_same<T, float>::value) {
+    // e = e0 + s de - eps_p and sigma = C : e on packed pairs
 #pragma unroll
-  for (int c = 0; c < 6; ++c) e[c] = e0[c] + s * de[c] - yt.ep[c];
-  hooke<T>(M, e, sg);
+    for (int c = 0; c < 6; c += 2) {
+      const pair_t<T> ec = pfma<T>(pmk<T>(s, s), pmk<T>(de[c], de[c + 1]), pmk<T>(e0[c], e0[c + 1]));
+      e[c] = ec.x - yt.ep[c];
+      e[c + 1] = ec.y - yt.ep[c + 1];
+    }
+    const pair_t<T> s01 = pfma<T>(pmk<T>(M.C13, M.C13), pmk<T>(e[2], e[2]),
+                                  pfma<T>(pmk<T>(M.C12, M.C11), pmk<T>(e[1], e[1]),
+                                          pmul<T>(pmk<T>(M.C11, M.C12), pmk<T>(e[0], e[0]))));
+    const pair_t<T> s45 = pmul<T>(pmk<T>(T(2) * M.C44, T(2) * M.C66), pmk<T>(e[4], e[5]));
+    sg[0] = s01.x;
+    sg[1] = s01.y;
+    sg[2] = M.C13 * (e[0] + e[1]) + M.C33 * e[2];
+    sg[3] = T(2) * M.C44 * e[3];
+    sg[4] = s45.x;
+    sg[5] = s45.y;
+  } else {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) e[c] = e0[c] + s * de[c] - yt.ep[c];
+    hooke<T>(M, e, sg);
+  }
   T ex[16];
   T Es = T(0), Et = T(0), vtw = T(0);
   const T cb_s = -M.b_s * T(kLog2e), cb_t = -M.b_b * T(kLog2e);

@@ -178,6 +178,9 @@ __global__ void __launch_bounds__(kXThreads, XMinBlocks<T>::value) k_xpass(const
   double acc[kNumRed];
 #pragma unroll
   for (int i = 0; i < kNumRed; ++i) acc[i] = 0.0;
+  // the thread's stresses are summed in the field precision over its few voxels (4 at
+  // most in float) and added to the FP64 block sum once
+  T sacc[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
   for (int t = tid; t < nl * nx; t += nthr) {
     const int l = t / nx, x = t - l * nx;
     const size_t vox = ((size_t)line0 + l) * nx + x;
@@ -220,7 +223,7 @@ __global__ void __launch_bounds__(kXThreads, XMinBlocks<T>::value) k_xpass(const
       for (int i = 0; i < 9; ++i) R[i] = a.Rg[(size_t)g * 9 + i];
       mc_voxel<T, NP>(a.M, R, epsn, eps, y, a.dt, a.nsub, sig, tab);
   #pragma unroll
-      for (int c = 0; c < 6; ++c) acc[c] += (double)sig[c];
+      for (int c = 0; c < 6; ++c) sacc[c] += sig[c];
       if (COMMIT) {
   #pragma unroll
         for (int c = 0; c < 6; ++c) a.ep[c * nvox + vox] = y.ep[c];
@@ -252,6 +255,8 @@ __global__ void __launch_bounds__(kXThreads, XMinBlocks<T>::value) k_xpass(const
       for (int p = 0; p < 3; ++p) res[(size_t)(p * nl + l) * nx + x] = mk<T>(tau[2 * p], tau[2 * p + 1]);
     }
   }
+#pragma unroll
+  for (int c = 0; c < 6; ++c) acc[c] += (double)sacc[c];
   if (!COMMIT) {
     __syncthreads();
     C2<T>* out = smem_fft<T, -1>(res, oth, a.dx, 3 * nl, nx, tw, tid, nthr);

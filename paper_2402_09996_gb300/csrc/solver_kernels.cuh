@@ -1,17 +1,18 @@
 // Kernels of one fixed-point iteration of the Green-operator solver (Sec. 3, last
 // paragraph) and of the commit of a converged increment.
 //
-// Spectral layout: S[c][kz][ky][kx], c = 6 tensor components, kx in [0, nx/2]
-// (half spectrum of the real-to-complex transform along x), complex interleaved.
+// Spectral layout: S[kz][ky][kx][c], c = 6 tensor components innermost, kx in [0, nx/2]
+// (half spectrum of the real-to-complex transform along x), complex values.
 // Between iterations S holds the strain with x still in Fourier space and y, z in
 // real space ("x-spectral" form).  One iteration:
 //   k_xpass   inverse x-FFT -> eps(x) -> per-voxel MC update -> sigma, tau = sigma - C0:eps
-//             -> forward x-FFT (out of place); FP64 block sums of sigma; the last CTA
-//             forms <sigma>, the stress-constraint error and the mixed-load update.
-//   k_line    forward y-FFT (in place)
+//             -> forward x-FFT (out of place); sums of sigma (per thread and in-warp in
+//             the field precision, across warps and CTAs in FP64); the last CTA forms
+//             <sigma>, the stress-constraint error and the mixed-load update.
+//   k_line_pencil / k_line   forward y-FFT (in place)
 //   k_zgreen  forward z-FFT -> eps_hat = -Gamma0(kappa):tau_hat / N, eps_hat(0) = E,
-//             equilibrium residual (FP64) -> inverse z-FFT (in place)
-//   k_line    inverse y-FFT (in place)
+//             equilibrium residual (FP64 sums) -> inverse z-FFT (in place)
+//   k_line_pencil / k_line   inverse y-FFT (in place)
 #pragma once
 
 #include "constitutive.cuh"
@@ -62,6 +63,42 @@ __device__ __forceinline__ bool publish_partial(double* v, double* partial, unsi
     __threadfence();
     const unsigned int prev = atomicAdd(counter, 1u);
     *s_last = (prev == block_count() - 1) ? 1 : 0;
+  }
+  __syncthreads();
+  return *s_last != 0;
+}
+
+// publish_partial for NV sums held in the field precision T: the in-warp shuffle tree runs
+// in T (in float, the adds of GB300's slow FP64 pipe are kept out of every thread), the
+// warp sums are converted and added across warps in FP64.  For T = double this is
+// publish_partial's arithmetic.
+template <typename T, int NV>
+__device__ __forceinline__ bool publish_partial_t(const T* s, double* partial, unsigned int* counter,
+                                                  double (*red)[kNumRed], int* s_last) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  T v[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) v[i] = s[i];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], off);
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) red[wid][i] = (double)v[i];
+  __syncthreads();
+  if (wid == 0) {
+    double w[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) w[i] = lane < nw ? red[lane][i] : 0.0;
+    warp_sum<NV>(w);
+    if (lane == 0) {
+#pragma unroll
+      for (int i = 0; i < NV; ++i) partial[(size_t)block_linear() * kNumRed + i] = w[i];
+      __threadfence();
+      const unsigned int prev = atomicAdd(counter, 1u);
+      *s_last = (prev == block_count() - 1) ? 1 : 0;
+    }
   }
   __syncthreads();
   return *s_last != 0;
@@ -255,8 +292,10 @@ __global__ void __launch_bounds__(kXThreads, XMinBlocks<T>::value) k_xpass(const
       for (int p = 0; p < 3; ++p) res[(size_t)(p * nl + l) * nx + x] = mk<T>(tau[2 * p], tau[2 * p + 1]);
     }
   }
+  if constexpr (COMMIT || NP == kLinearLaw) {
 #pragma unroll
-  for (int c = 0; c < 6; ++c) acc[c] += (double)sacc[c];
+    for (int c = 0; c < 6; ++c) acc[c] += (double)sacc[c];
+  }
   if (!COMMIT) {
     __syncthreads();
     C2<T>* out = smem_fft<T, -1>(res, oth, a.dx, 3 * nl, nx, tw, tid, nthr);
@@ -275,8 +314,15 @@ __global__ void __launch_bounds__(kXThreads, XMinBlocks<T>::value) k_xpass(const
       a.spec_out[e0 + 1] = B;
     }
   }
-  if (publish_partial<kNumRed>(acc, a.partial, a.counter, red, &s_last)) {
-    total_partials<kNumRed>(a.partial, acc, red);
+  // trial iterations sum the 6 stress components (in-warp in the field precision); the
+  // commit and the linear-law mode all slots in FP64
+  constexpr bool kSix = !COMMIT && NP != kLinearLaw;
+  bool last;
+  if constexpr (kSix) last = publish_partial_t<T, 6>(sacc, a.partial, a.counter, red, &s_last);
+  else last = publish_partial<kNumRed>(acc, a.partial, a.counter, red, &s_last);
+  if (last) {
+    if constexpr (kSix) total_partials<6>(a.partial, acc, red);
+    else total_partials<kNumRed>(a.partial, acc, red);
     if (tid == 0) {
       IterStatus* st = a.st;
       const double inv = 1.0 / (double)a.nvox;

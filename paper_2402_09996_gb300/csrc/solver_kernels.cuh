@@ -557,7 +557,7 @@ __global__ void __launch_bounds__(N1 > 0 ? kPencilThreads : kZThreads) k_zgreen(
   const int ps = nz + 1;  // padded sequence stride
   C2<T>* b0 = tw + nz;
   C2<T>* b1 = b0 + (size_t)6 * a.HC * ps;
-  double* cres = reinterpret_cast<double*>((kPencil ? b0 : b1) + (size_t)6 * a.HC * ps);  // HC * nz residual terms
+  T* cres = reinterpret_cast<T*>((kPencil ? b0 : b1) + (size_t)6 * a.HC * ps);  // HC * nz residual terms
   const int tid = threadIdx.x, nthr = blockDim.x;
   if (a.done && *a.done) return;
   const int j = blockIdx.y;
@@ -645,9 +645,10 @@ __global__ void __launch_bounds__(N1 > 0 ? kPencilThreads : kZThreads) k_zgreen(
         d[c] = csub<T>(t[c], p);
         a.P_out[g0 + c] = t[c];
       }
-      // symmetric order (11,22,33,23,13,12): row i of d times kappa.  The point's term is
-      // formed in the field precision (its rounding, relative 1e-7 in float, is far below
-      // the tolerances the error is compared with); the sums over points are FP64.
+      // symmetric order (11,22,33,23,13,12): row i of d times kappa.  The point's term and
+      // its column's sum over kz are formed in the field precision (relative rounding
+      // below 1e-5 in float, on an error compared with tolerances of 1e-6 and above); the
+      // sum over columns is FP64.
       const T r0x = d[0].x * k0 + d[5].x * k1 + d[4].x * k2;
       const T r0y = d[0].y * k0 + d[5].y * k1 + d[4].y * k2;
       const T r1x = d[5].x * k0 + d[1].x * k1 + d[3].x * k2;
@@ -655,7 +656,7 @@ __global__ void __launch_bounds__(N1 > 0 ? kPencilThreads : kZThreads) k_zgreen(
       const T r2x = d[4].x * k0 + d[3].x * k1 + d[2].x * k2;
       const T r2y = d[4].y * k0 + d[3].y * k1 + d[2].y * k2;
       const T wgt = (h == 0 || 2 * h == a.nx) ? T(1) : T(2);
-      cres[hh * nz + kz] = (double)(wgt * (r0x * r0x + r0y * r0y + r1x * r1x + r1y * r1y + r2x * r2x + r2y * r2y));
+      cres[hh * nz + kz] = wgt * (r0x * r0x + r0y * r0y + r1x * r1x + r1y * r1y + r2x * r2x + r2y * r2y);
     }
     const T kk = k0 * k0 + k1 * k1 + k2 * k2;
     C2<T> e[6];
@@ -725,11 +726,12 @@ __global__ void __launch_bounds__(N1 > 0 ? kPencilThreads : kZThreads) k_zgreen(
   {
     const int lane = tid & 31, wid = tid >> 5, nw = nthr >> 5;
     for (int hh = wid; hh < hc; hh += nw) {
-      double cv = 0.0;
+      T cv = T(0);
       for (int kz = lane; kz < nz; kz += 32) cv += cres[hh * nz + kz];
-      warp_sum<1>(&cv);
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) cv += __shfl_xor_sync(0xffffffffu, cv, off);
       if (lane == 0) {
-        a.partial[(size_t)j * H + h0 + hh] = cv;
+        a.partial[(size_t)j * H + h0 + hh] = (double)cv;
         __threadfence();
       }
     }

@@ -435,17 +435,18 @@ PARAM_NAMES = ["r0_ord", "r0_sup", "r0_twin", "Q_s", "Q_b", "b_s", "b_b", "c", "
 
 
 def history_gradient(grain_id, euler, n_increments, dt, target, weights=None, precision=FP64, material=None,
-                     Edot=(0, 0, 1e-3, 0, 0, 0), checkpoint_every=5, memory_budget=None, **options):
+                     Edot=(0, 0, 1e-3, 0, 0, 0), checkpoint_every=None, memory_budget=None, **options):
     """Misfit J = sum_n w_n (<sigma_zz>_n - target_n)^2 of a load history and its gradient
     with respect to the parameters PARAM_NAMES and every grain's Bunge angles, by the
     adjoint of the history (rve_adjoint_increment).
 
     The reverse pass needs the strain and state of every increment.  With checkpoint_every
-    = k the forward pass saves the state every k increments and the reverse pass replays
-    each segment from its checkpoint.  With checkpoint_every = None the forward pass keeps
-    every increment's fields on the device (8 (6 + 34) bytes per voxel and increment) when
-    they fit in memory_budget bytes (default: half the free device memory), so nothing is
-    replayed; otherwise it checkpoints every ceil(sqrt(n_increments)) increments.
+    = None (the default) the forward pass keeps every increment's fields on the device
+    (8 (6 + 34) bytes per voxel and increment) when they fit in memory_budget bytes
+    (default: half the free device memory), so nothing is replayed; otherwise it
+    checkpoints every ceil(sqrt(n_increments)) increments.  With checkpoint_every = k the
+    forward pass saves the state every k increments and the reverse pass replays each
+    segment from its checkpoint.
     Returns (J, dJ/dparams (9,), dJ/deuler (n_grains, 3), info)."""
     import math
 

@@ -204,3 +204,30 @@ def test_history_gradient_storage_modes_agree(lib, cuda):
     for other in (stored, auto_ck):
         assert other[0] == ref[0]
         assert np.array_equal(other[1], ref[1]) and np.array_equal(other[2], ref[2])
+
+
+def test_history_misfit_autograd_function(lib, cuda):
+    """rve.HistoryMisfit as a torch.autograd.Function: the forward value is the history's
+    misfit and backward hands back exactly the adjoint gradient, scaled by the incoming
+    gradient."""
+    import torch
+
+    from oracle.voronoi import label_rve
+
+    from paper_2402_09996_gb300 import inputs, rve
+
+    inp = inputs.make_inputs((8, 10, 12), 4, 0.5, seed=8)
+    gid = label_rve(inp)
+    n_inc, dt = 3, 0.5
+    target = np.array([95.0, 185.0, 245.0])
+    base = rve.default_material().as_dict()
+    p0 = np.array([base[k] for k in rve.PARAM_NAMES], dtype=np.float64)
+    J, gp, ge, _ = rve.history_gradient(gid, inp.euler, n_inc, dt, target)
+    params = torch.tensor(p0, requires_grad=True)
+    euler = torch.tensor(inp.euler, dtype=torch.float64, requires_grad=True)
+    config = {"grain_id": gid, "n_increments": n_inc, "dt": dt, "target": target}
+    out = rve.HistoryMisfit.apply(params, euler, config)
+    assert float(out) == J
+    (3.0 * out).backward()
+    assert np.array_equal(params.grad.numpy(), 3.0 * gp)
+    assert np.array_equal(euler.grad.numpy(), 3.0 * ge)

@@ -232,6 +232,7 @@ struct rve_s {
   int L = 1, xgrid = 0;
   size_t xsmem = 0, ysmem = 0, zsmem = 0;
   int yHC = 1, zHC = 1;
+  int xs = 0;  // x-pass shared-memory line stride
   double lam0 = 0, mu0 = 0;
   // host state
   double E_n[6] = {0}, E_prev[6] = {0};
@@ -527,7 +528,10 @@ rve_status alloc_fields(rve_s* h) {
     h->L = (int)std::max(fill, std::min(most, keep));
   }
   h->xgrid = (int)((h->NL + h->L - 1) / h->L);
-  h->xsmem = (size_t)(h->nx + 6 * h->L * h->nx) * 2 * sizeof(T);  // FFT buffers; + tables: xsmem_total
+  // x sequences in shared memory: odd stride nx + 1 for the register transforms of
+  // power-of-two lines (conflict-free steps), nx for the Stockham passes
+  h->xs = (h->nx == 64 || h->nx == 128 || h->nx == 256) ? h->nx + 1 : h->nx;
+  h->xsmem = (size_t)(h->nx + 6 * h->L * h->xs) * 2 * sizeof(T);  // FFT buffers; + tables: xsmem_total
   // y and z passes: tiles of HC kx values x 6 components (two buffers of padded lines);
   // default about 50 KB per CTA so that four CTAs share an SM (the autotuner may change it)
   const size_t tile_budget = 50 * 1024;
@@ -619,7 +623,7 @@ rve_status upload_root_tab(rve_s* h) {
 template <typename T>
 XArgs<T> x_args(rve_s* h, const void* in, void* out, int it) {
   XArgs<T> a{};
-  a.nx = h->nx; a.ny = h->ny; a.nz = h->nz; a.H = h->H; a.L = h->L;
+  a.nx = h->nx; a.ny = h->ny; a.nz = h->nz; a.H = h->H; a.L = h->L; a.xs = h->xs;
   a.nvox = h->nvox;
   a.dx = h->dx;
   a.tw = (const C2<T>*)h->tw_x;

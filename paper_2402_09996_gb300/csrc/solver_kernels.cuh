@@ -122,6 +122,7 @@ __device__ __forceinline__ double mandel_w(int a) { return a < 3 ? 1.0 : 1.41421
 template <typename T>
 struct XArgs {
   int nx, ny, nz, H, L;
+  int xs;  // line stride of the shared-memory x sequences: nx + 1 for power-of-two nx, else nx
   long long nvox;
   FftDim dx;
   const C2<T>* tw;
@@ -154,6 +155,51 @@ struct XArgs {
   const T* lin_g;
 };
 
+// The x transforms of a CTA's nseq packed lines (stride xs >= N + 1 in shared memory) for
+// a power-of-two length N = N1 N2: step 1 from a into b, step 2 back into a in natural
+// order.  Consecutive threads take consecutive lines, so with an odd stride both steps
+// are free of bank conflicts.  Contains barriers: every thread of the CTA calls it.
+template <typename T, int SIGN, int N1, int N2>
+__device__ __forceinline__ void xlines_pencil(C2<T>* a, C2<T>* b, int nseq, int xs, const C2<T>* tw, int tid,
+                                              int nthr) {
+  for (int w = tid; w < nseq * N1; w += nthr) {
+    const int q = w % nseq, n1 = w / nseq;
+    C2<T> v[N2];
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) v[n2] = a[(size_t)q * xs + n1 + N1 * n2];
+    pencil_step1<T, SIGN, N1, N2>(v, n1, b + (size_t)q * xs, tw);
+  }
+  __syncthreads();
+  for (int w = tid; w < nseq * N2; w += nthr) {
+    const int q = w % nseq, k2 = w / nseq;
+    C2<T> u[N1];
+    pencil_step2<T, SIGN, N1, N2>(u, k2, b + (size_t)q * xs);
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) a[(size_t)q * xs + k2 + N2 * k1] = u[k1];
+  }
+  __syncthreads();
+}
+
+// The CTA's x transforms: register two-step transforms for nx = 64, 128, 256 (result in
+// a), shared-memory Stockham passes otherwise (result in a or b, returned).
+template <typename T, int SIGN>
+__device__ __forceinline__ C2<T>* xlines_fft(C2<T>* a, C2<T>* b, const FftDim& d, int nseq, int xs, const C2<T>* tw,
+                                             int tid, int nthr) {
+  if (d.n == 128) {
+    xlines_pencil<T, SIGN, 8, 16>(a, b, nseq, xs, tw, tid, nthr);
+    return a;
+  }
+  if (d.n == 64) {
+    xlines_pencil<T, SIGN, 8, 8>(a, b, nseq, xs, tw, tid, nthr);
+    return a;
+  }
+  if (d.n == 256) {
+    xlines_pencil<T, SIGN, 16, 16>(a, b, nseq, xs, tw, tid, nthr);
+    return a;
+  }
+  return smem_fft<T, SIGN>(a, b, d, nseq, xs, tw, tid, nthr);
+}
+
 constexpr int kXThreads = 128;
 // Minimum resident x-pass CTAs per SM requested from the register allocator.  Float: 3
 // (at most 168 registers; the constitutive update is latency-bound at 2 CTAs, and 3 run
@@ -168,10 +214,10 @@ __global__ void __launch_bounds__(kXThreads, XMinBlocks<T>::value) k_xpass(const
   __shared__ int s_last;
   C2<T>* tw = reinterpret_cast<C2<T>*>(smem_raw);
   C2<T>* b0 = tw + a.nx;
-  C2<T>* b1 = b0 + 3 * a.L * a.nx;
-  T* tab = reinterpret_cast<T*>(b1 + 3 * a.L * a.nx);  // kRootTabs
+  C2<T>* b1 = b0 + 3 * a.L * a.xs;
+  T* tab = reinterpret_cast<T*>(b1 + 3 * a.L * a.xs);  // kRootTabs
   const int tid = threadIdx.x, nthr = blockDim.x;
-  const int nx = a.nx, H = a.H, half = nx / 2;
+  const int nx = a.nx, H = a.H, half = nx / 2, xs = a.xs;
   const size_t NL = (size_t)a.ny * a.nz;
   const int line0 = blockIdx.x * a.L;
   const int nl = min(a.L, (int)(NL - line0));
@@ -204,12 +250,12 @@ __global__ void __launch_bounds__(kXThreads, XMinBlocks<T>::value) k_xpass(const
       A.y = T(0);
       B.y = T(0);
     }
-    C2<T>* seq = b0 + (size_t)q * nx;
+    C2<T>* seq = b0 + (size_t)q * xs;
     seq[xi] = mk<T>(A.x - B.y, A.y + B.x);
     if (xi > 0 && xi < half) seq[nx - xi] = mk<T>(A.x + B.y, B.x - A.y);
   }
   __syncthreads();
-  C2<T>* res = smem_fft<T, +1>(b0, b1, a.dx, 3 * nl, nx, tw, tid, nthr);
+  C2<T>* res = xlines_fft<T, +1>(b0, b1, a.dx, 3 * nl, xs, tw, tid, nthr);
   C2<T>* oth = (res == b0) ? b1 : b0;
 
   double acc[kNumRed];
@@ -224,7 +270,7 @@ __global__ void __launch_bounds__(kXThreads, XMinBlocks<T>::value) k_xpass(const
     T eps[6], epsn[6], sig[6], R[9];
 #pragma unroll
     for (int p = 0; p < 3; ++p) {
-      const C2<T> z = res[(size_t)(p * nl + l) * nx + x];
+      const C2<T> z = res[(size_t)(p * nl + l) * xs + x];
       eps[2 * p] = z.x;
       eps[2 * p + 1] = z.y;
     }
@@ -289,7 +335,7 @@ __global__ void __launch_bounds__(kXThreads, XMinBlocks<T>::value) k_xpass(const
 #pragma unroll
       for (int c = 0; c < 6; ++c) tau[c] = sig[c] - m2 * eps[c] - (c < 3 ? tr : T(0));
 #pragma unroll
-      for (int p = 0; p < 3; ++p) res[(size_t)(p * nl + l) * nx + x] = mk<T>(tau[2 * p], tau[2 * p + 1]);
+      for (int p = 0; p < 3; ++p) res[(size_t)(p * nl + l) * xs + x] = mk<T>(tau[2 * p], tau[2 * p + 1]);
     }
   }
   if constexpr (COMMIT || NP == kLinearLaw) {
@@ -298,15 +344,15 @@ __global__ void __launch_bounds__(kXThreads, XMinBlocks<T>::value) k_xpass(const
   }
   if (!COMMIT) {
     __syncthreads();
-    C2<T>* out = smem_fft<T, -1>(res, oth, a.dx, 3 * nl, nx, tw, tid, nthr);
+    C2<T>* out = xlines_fft<T, -1>(res, oth, a.dx, 3 * nl, xs, tw, tid, nthr);
     // unpack: A = (Z_k + conj Z_{n-k}) / 2, B = (Z_k - conj Z_{n-k}) / (2i)
     for (int w = tid; w < 3 * nl * H; w += nthr) {
       const int p = w % 3;
       const int r = w / 3;
       const int xi = r % H, l = r / H;
       const int q = p * nl + l;
-      const C2<T> Z = out[(size_t)q * nx + xi];
-      const C2<T> Zm = out[(size_t)q * nx + (xi == 0 ? 0 : nx - xi)];
+      const C2<T> Z = out[(size_t)q * xs + xi];
+      const C2<T> Zm = out[(size_t)q * xs + (xi == 0 ? 0 : nx - xi)];
       const C2<T> A = mk<T>(T(0.5) * (Z.x + Zm.x), T(0.5) * (Z.y - Zm.y));
       const C2<T> B = mk<T>(T(0.5) * (Z.y + Zm.y), T(-0.5) * (Z.x - Zm.x));
       const size_t e0 = (((size_t)line0 + l) * H + xi) * 6 + 2 * p;

@@ -47,11 +47,12 @@ def test_two_grain_fixed_iterations_fp64(lib, cuda):
 
 
 @pytest.mark.parametrize("shape,prec", [((12, 10, 6), "fp64"), ((12, 10, 6), "fp32"), ((64, 64, 6), "fp64"),
-                                        ((64, 64, 6), "fp32"), ((256, 8, 4), "fp64"), ((8, 256, 4), "fp32")])
+                                        ((64, 64, 6), "fp32"), ((256, 8, 4), "fp64"), ((8, 256, 4), "fp32"),
+                                        ((6, 8, 64), "fp64"), ((4, 4, 128), "fp32"), ((4, 6, 256), "fp64")])
 def test_ragged_voronoi_tolerance_mode(lib, cuda, shape, prec):
     """5 twinned grains, 4 increments: a 6 x 10 x 12 grid (radix-3/5 lengths, odd line
-    counts, shared-memory Stockham transforms), and grids whose y and z lines have the
-    power-of-two lengths of the two-step register transforms (64, and 256 along z or y)."""
+    counts, shared-memory Stockham transforms), and grids whose x, y or z lines have the
+    power-of-two lengths of the two-step register transforms (64, 128, 256)."""
     from paper_2402_09996_gb300 import inputs, rve
 
     inp = inputs.make_inputs(shape, 5, 0.5, seed=42)

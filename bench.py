@@ -41,7 +41,7 @@ FP32_LANES_PER_SM, N_SM = 128, 152  # GB300
 # DRAM bytes (read + write) of one trial x-pass launch on the 128^3 FP32 workload, from ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum, mean of two launches); valid for the x-pass
 # source as profiled, to be re-taken whenever that kernel changes
-XPASS_DRAM_BYTES_128 = 436_074_624
+XPASS_DRAM_BYTES_128 = 438_034_560
 
 
 def flops_per_voxit(n_sub):

@@ -211,8 +211,13 @@ rve_status rve_step_batch(rve_t* hs, int n, int n_increments, long long* iterati
  *   euler_grad         n_grains*3, accumulated dJ/d(phi1, Phi, phi2) per grain (host);
  *   iterations_out     adds the adjoint fixed-point iterations (may be NULL).
  * The handle supplies the material, the load (its strain-controlled components and dt
- * must be those of the increment) and the solver options.  The call reuses the handle's
- * spectra: its forward state is lost (keep a copy with rve_save_state).  Needs n_sub <= 16. */
+ * must be those of the increment) and the solver options.  The adjoint fixed point stops
+ * on the forward criterion with both relative errors taken against max(|<s>|, |g|_rms)
+ * (g the adjoint source); a zero source gives the zero solution without iterating.  It
+ * returns RVE_ERR_NOT_CONVERGED after max_iter iterations and RVE_ERR_NAN on a non-finite
+ * source or iterate, the accumulated gradients then being partial.  The call reuses the
+ * handle's spectra: its forward state is lost (keep a copy with rve_save_state).  Needs
+ * n_sub <= 16. */
 rve_status rve_adjoint_increment(rve_t h, const double* eps_prev, const double* eps_cur, const double* state_prev,
                                  const double dS[6], double dt, double* state_b, double* eps_b, double* param_grad,
                                  double* euler_grad, long long* iterations_out);

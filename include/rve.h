@@ -215,7 +215,7 @@ rve_status rve_step_batch(rve_t* hs, int n, int n_increments, long long* iterati
  * on the forward criterion with both relative errors taken against max(|<s>|, |g|_rms)
  * (g the adjoint source); a zero source gives the zero solution without iterating.  It
  * returns RVE_ERR_NOT_CONVERGED after max_iter iterations and RVE_ERR_NAN on a non-finite
- * source or iterate, the accumulated gradients then being partial.  The call reuses the
+ * source or iterate, leaving state_b, eps_b and the gradients unchanged.  The call reuses the
  * handle's spectra: its forward state is lost (keep a copy with rve_save_state).  Needs
  * n_sub <= 16. */
 rve_status rve_adjoint_increment(rve_t h, const double* eps_prev, const double* eps_cur, const double* state_prev,

@@ -5,9 +5,10 @@
 // This is the constitutive building block of the adjoint of the load history; with unit
 // stress adjoints it gives the rows of the algorithmic tangent d sigma / d eps.
 //
-// The forward values are recomputed with the same code as the primal (constitutive.cuh):
-// each RK4 substep's start state is stored, and each stage is re-evaluated before it is
-// reversed.  The regularised rate rho(a, P) solving rho = P ((a - eta rho)/K)^n is
+// One forward pass per voxel, with the primal's operations (constitutive.cuh), stores each
+// RK4 substep's start state and its four stage rates; every reverse sweep rebuilds a
+// stage's intermediates from its input state and stored rates (no rate solve) just
+// before reversing it.  The regularised rate rho(a, P) solving rho = P ((a - eta rho)/K)^n is
 // differentiated implicitly: with z = (a - eta rho)/K and D = K + eta P n z^(n-1),
 //   d rho / d a = P n z^(n-1) / D,   d rho / d P = K z^n / D   (0 where rho = 0).
 #pragma once

@@ -9,6 +9,7 @@ no CPU path.
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 from pathlib import Path
 
@@ -434,6 +435,23 @@ def material_point_vjp(R, eps_n, eps, state, sigma_b, state_b, dt, n_sub, precis
 PARAM_NAMES = ["r0_ord", "r0_sup", "r0_twin", "Q_s", "Q_b", "b_s", "b_b", "c", "d"]
 
 
+def history_storage(n_increments, nvox, checkpoint_every, memory_budget):
+    """How history_gradient keeps the history: (store_all, checkpoint_every).
+
+    checkpoint_every = k (an int) is taken as given (checkpoints every k increments).  With
+    None, every increment's fields are kept on the device when (n_increments + 1) * 8 *
+    (6 + 34) * nvox bytes fit in memory_budget; otherwise checkpoints every
+    ceil(sqrt(n_increments)) increments (at least 1)."""
+    if checkpoint_every is not None:
+        if int(checkpoint_every) < 1:
+            raise ValueError("checkpoint_every must be >= 1 or None")
+        return False, int(checkpoint_every)
+    need = 8 * (6 + 34) * int(nvox) * (int(n_increments) + 1)
+    if need <= memory_budget:
+        return True, max(1, int(n_increments))
+    return False, max(1, math.isqrt(max(int(n_increments) - 1, 0)) + 1)
+
+
 def history_gradient(grain_id, euler, n_increments, dt, target, weights=None, precision=FP64, material=None,
                      Edot=(0, 0, 1e-3, 0, 0, 0), checkpoint_every=None, memory_budget=None, **options):
     """Misfit J = sum_n w_n (<sigma_zz>_n - target_n)^2 of a load history and its gradient
@@ -448,8 +466,6 @@ def history_gradient(grain_id, euler, n_increments, dt, target, weights=None, pr
     forward pass saves the state every k increments and the reverse pass replays each
     segment from its checkpoint.
     Returns (J, dJ/dparams (9,), dJ/deuler (n_grains, 3), info)."""
-    import math
-
     import torch
 
     lib = load_library()
@@ -476,12 +492,10 @@ def history_gradient(grain_id, euler, n_increments, dt, target, weights=None, pr
                         for f in (FIELD_EPS_P, FIELD_V, FIELD_ALPHA)]).contiguous()
         return eps.reshape(6, nvox).contiguous(), st
 
-    store_all = False
-    if checkpoint_every is None:
-        need = 8 * (6 + 34) * nvox * (n_increments + 1)
-        budget = memory_budget if memory_budget is not None else torch.cuda.mem_get_info(dev)[0] // 2
-        store_all = need <= budget
-        checkpoint_every = n_increments if store_all else max(1, math.isqrt(max(n_increments - 1, 0)) + 1)
+    budget = memory_budget
+    if checkpoint_every is None and budget is None:
+        budget = torch.cuda.mem_get_info(dev)[0] // 2
+    store_all, checkpoint_every = history_storage(n_increments, nvox, checkpoint_every, budget)
     ckpt = {0: fwd.save_state()} if not store_all else {}
     stored = [fields_of(fwd)] if store_all else None
     S = []

@@ -231,3 +231,29 @@ def test_history_misfit_autograd_function(lib, cuda):
     (3.0 * out).backward()
     assert np.array_equal(params.grad.numpy(), 3.0 * gp)
     assert np.array_equal(euler.grad.numpy(), 3.0 * ge)
+
+
+def test_history_gradient_register_transform_grid(lib, cuda):
+    """The adjoint on a grid whose x and y lines take the two-step register transforms
+    (8 x 64 x 64, FP64): the gradient in r0_ord and Q_s against central differences of the
+    forward solve."""
+    from oracle.voronoi import label_rve
+
+    from paper_2402_09996_gb300 import inputs, rve
+
+    inp = inputs.make_inputs((8, 64, 64), 6, 0.5, seed=64)
+    gid = label_rve(inp)
+    n_inc, dt = 3, 0.5
+    opts = dict(tol=1e-12, max_iter=3000)
+    _, S0 = _history_J(gid, inp.euler, {}, np.zeros(n_inc), n_inc, dt, **opts)
+    target = 0.97 * S0
+    J, gp, _, _ = rve.history_gradient(gid, inp.euler, n_inc, dt, target, **opts)
+    base = orc.Material()
+    for name in ("r0_ord", "Q_s"):
+        k = rve.PARAM_NAMES.index(name)
+        p0 = getattr(base, name)
+        h = 1e-5 * abs(p0)
+        jp, _ = _history_J(gid, inp.euler, {name: p0 + h}, target, n_inc, dt, **opts)
+        jm, _ = _history_J(gid, inp.euler, {name: p0 - h}, target, n_inc, dt, **opts)
+        num = (jp - jm) / (2 * h)
+        assert abs(num - gp[k]) <= 1e-4 * max(abs(num), abs(gp[k])) + 1e-9 * J / abs(p0), (name, num, gp[k])

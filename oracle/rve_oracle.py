@@ -14,10 +14,11 @@ of arXiv 2402.09996:
   slip and the unidirectional twin law with f = sqrt(2) v;
 * Table 1 for the 12 slip and 4 twin systems;
 * Sec. 4, Eq. (regu): the viscous regularisation r' = r + eta |gamma_dot|, solved at
-  the same instant as the rate (reading B of DESIGN.md);
+  the same instant as the rate (the paper leaves the instant open);
 * Sec. 3 (end): explicit RK4 integration per voxel, coupled to a Green-operator
   ("FFT") solver -- here the basic fixed-point scheme with Willot's rotated
-  discrete Green operator (reading R9) and a mixed macroscopic load (R8).
+  discrete Green operator (the paper names no discretisation) and a mixed macroscopic
+  load (strain rate on the controlled components, zero mean stress on the others).
 
 Nothing here is blocked, fused or reordered for speed.  Parity status of each
 function is stated in its docstring; all are pinned by tests/test_oracle_*.py.
@@ -33,7 +34,7 @@ SQRT2 = math.sqrt(2.0)
 
 # ----------------------------------------------------------------------------------
 # Table 1: slip planes n and directions l (crystal frame, Miller indices, c/a = 1).
-# Reading R1: system 9 is (1 -1 1)[1 1 0]; the table prints [0 1 1], a duplicate of s7.
+# System 9 is read as (1 -1 1)[1 1 0]: Table 1 prints [0 1 1], a duplicate of system 7.
 # ----------------------------------------------------------------------------------
 SLIP_TABLE = [
     # (plane, direction, kind)  kind: "s" superdislocation, "o" ordinary dislocation
@@ -62,7 +63,7 @@ N_SYS = N_SLIP + N_TWIN
 
 
 def system_vectors():
-    """Unit plane normals and slip directions of the 16 systems (Table 1, reading R2).
+    """Unit plane normals and slip directions of the 16 systems (Table 1; lattice read as pseudo-cubic, c/a = 1).
 
     Returns (n, l, kinds): arrays (16, 3) and a list of 16 kinds ("s", "o", "t").
     Parity: pinned (tests/test_oracle_tables.py: orthogonality, Schmid factors).
@@ -181,7 +182,7 @@ def mandel_matrix(C4: np.ndarray) -> np.ndarray:
 
 
 def reference_medium(mat: Material):
-    """Isotropic C0 (reading R10): 3 k0 = 2 mu0 = (lambda_min + lambda_max) / 2 of the
+    """Isotropic C0 (the paper gives none; chosen as): 3 k0 = 2 mu0 = (lambda_min + lambda_max) / 2 of the
     crystal's Mandel eigenvalues.  Returns (lam0, mu0)."""
     ev = np.linalg.eigvalsh(mandel_matrix(stiffness_tensor(mat)))
     two_mu = 0.5 * (ev[0] + ev[-1])
@@ -192,7 +193,7 @@ def reference_medium(mat: Material):
 
 
 def bunge_rotation(euler: np.ndarray) -> np.ndarray:
-    """Crystal-to-sample rotation R = Rz(phi1) Rx(Phi) Rz(phi2) (Bunge ZXZ, reading R2).
+    """Crystal-to-sample rotation R = Rz(phi1) Rx(Phi) Rz(phi2) (Bunge ZXZ, crystal to sample).
 
     euler (..., 3) rad -> (..., 3, 3); v_sample = R v_crystal.
     Parity: pinned (tests check R e_z and orthogonality against hand values).
@@ -279,7 +280,8 @@ class Constitutive:
         """Rates (ep_dot, v_dot, alpha_dot) at strain eps_c and state (ep, v, alpha).
 
         eps_c, ep: (V, 3, 3); v: (V, 16) accumulated slip, twin entries are v^beta;
-        alpha: (V, 12) kinematic variables of the slip systems (reading R6).
+        alpha: (V, 12) kinematic variables of the slip systems (back-stress x = c alpha, not in the paper's text;
+        none on the twins).
         """
         mt = self.mat
         sigma = self.stress(eps_c, ep)
@@ -295,7 +297,7 @@ class Constitutive:
         P_twin = (mt.Kc / SQRT2) * np.maximum(0.0, mt.fm - f_total)
         a_twin = tau[:, N_SLIP:] - r_twin
         gdot_twin = regularized_rate(a_twin, P_twin[:, None], mt.Kt, mt.nt, mt.eta)
-        # plastic strain rate (Sec. 3), twin-fraction weighting on slip only (R13)
+        # plastic strain rate (Sec. 3), twin-fraction weighting (1 - sum f) on the slip part only
         ep_dot = (1.0 - f_total)[:, None, None] * np.einsum("vs,sij->vij", gdot_slip, self.m[:N_SLIP])
         ep_dot = ep_dot + np.einsum("vb,bij->vij", gdot_twin, self.m[N_SLIP:])
         v_dot = np.concatenate([np.abs(gdot_slip), gdot_twin], axis=1)
@@ -304,7 +306,7 @@ class Constitutive:
 
     def integrate(self, eps_n_c, eps_c, ep, v, alpha, dt, n_sub):
         """N_sub classical RK4 steps over one increment along the linear strain path
-        eps(s) = eps_n + s (eps - eps_n), s in [0, 1] (Sec. 3 end; reading R7).
+        eps(s) = eps_n + s (eps - eps_n), s in [0, 1] (Sec. 3 end; the paper does not say how the strain varies inside an increment).
 
         Returns (sigma_c, ep, v, alpha) at the end of the increment.
         Parity: pinned (Radau reference, homogeneous and single-crystal tests).
@@ -342,7 +344,7 @@ def von_mises(sig: np.ndarray) -> np.ndarray:
 
 
 # ----------------------------------------------------------------------------------
-# Green operator (reading R9)
+# Green operator (Willot's rotated discrete scheme)
 # ----------------------------------------------------------------------------------
 def wave_vectors(shape, scheme: str = "willot"):
     """kappa(xi) on the half spectrum of numpy's rfftn over axes (z, y, x).
@@ -423,7 +425,7 @@ def apply_green(kappa, tau_hat, lam0, mu0):
 # ----------------------------------------------------------------------------------
 @dataclass
 class Load:
-    """Mixed macroscopic load (reading R8): strain rate on controlled components,
+    """Mixed macroscopic load: strain rate on controlled components,
     target mean stress on the others.  Component order (11, 22, 33, 23, 13, 12),
     tensor (not engineering) shear."""
 
@@ -434,7 +436,8 @@ class Load:
 
 
 def default_n_sub(dt: float) -> int:
-    """Reading R7: smallest power of two with substep dt/n_sub <= 1/8 s."""
+    """Substeps per increment (the paper gives no rule): the smallest power of two with
+    dt/n_sub <= 1/8 s."""
     n = 1
     while dt / n > 0.125 * (1.0 + 1e-12):
         n *= 2
@@ -542,7 +545,8 @@ class OracleRVE:
         free = ~ctrl
         M0 = self._c0_mandel()
         Mff = M0[np.ix_(free, free)]
-        # a1: macroscopic strain on controlled components, initial guess (reading R12)
+        # macroscopic strain on controlled components and the initial guess (first increment:
+        # free components from C0; later: the previous increment's step)
         dE0 = np.zeros(6)
         if self.increment == 0:
             dE0[ctrl] = np.asarray(ld.Edot, dtype=np.float64)[ctrl] * ld.dt
@@ -560,11 +564,11 @@ class OracleRVE:
         residuals = []
         it = 0
         while True:
-            # a2/a3: local constitutive update and polarisation
+            # local constitutive update and polarisation
             sig, ep_new, v_new, a_new = self.constitutive(eps)
             sig_mean = sig.mean(axis=0)
             tau = sig - np.einsum("ijkl,vkl->vij", self.C0, eps)
-            # a4: forward transforms; a7: equilibrium and stress-constraint errors (R11)
+            # forward transforms; equilibrium and stress-constraint errors
             sig_hat = self._fft(sig)
             tau_hat = self._fft(tau)
             div = np.einsum("zyxij,zyxj->zyxi", sig_hat, self.kappa)
@@ -580,17 +584,17 @@ class OracleRVE:
                 break
             if it + 1 >= op.max_iter:
                 raise NotConverged(f"increment {self.increment + 1}: {op.max_iter} iterations, e={e_eq:.3e}")
-            # a7: mixed-load update of the free macroscopic components (R8)
+            # mixed-load update of the free macroscopic components
             if np.any(free):
                 Em = E * _MANDEL_W
                 Em[free] -= np.linalg.solve(Mff, miss)
                 E = Em / _MANDEL_W
-            # a5/a6: Green operator, prescribed mean, inverse transform
+            # Green operator, prescribed mean, inverse transform
             eps_hat = apply_green(self.kappa, tau_hat, self.lam0, self.mu0)
             eps_hat[0, 0, 0] = _voigt6_to_tensor(E) * N
             eps = self._ifft(eps_hat)
             it += 1
-        # a8: commit and effective outputs
+        # commit and effective outputs
         self.E_prev = self.E.copy()
         self.E = E
         self.eps_n = eps

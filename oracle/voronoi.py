@@ -4,14 +4,14 @@ TEST INFRASTRUCTURE: used only by tests, the smoke check and the benchmark's CPU
 baseline leg; it shares no code with the library's labelling kernel.
 
 Sec. 2.1 defines the grain G_n as the set of points not farther from generator s_n
-than from any other generator, on a periodic window.  Readings:
+than from any other generator, on a periodic window.  Choices where it is silent:
 
-* R14: voxel (i, j, k) is represented by its centre ((i+1/2)/nx, (j+1/2)/ny,
+* voxel (i, j, k) is represented by its centre ((i+1/2)/nx, (j+1/2)/ny,
   (k+1/2)/nz); the squared minimum-image distance is formed in float64 as
   (dx*dx + dy*dy) + dz*dz, every product and sum rounded separately; a tie goes to
   the lowest generator index.  The minimum image folds d into [-1/2, 1/2]:
   d > 1/2 -> d - 1, d < -1/2 -> d + 1.
-* R17 (twins of the synthetic workloads): a twinned parent p is split by the plane
+* twins of the synthetic workloads: a twinned parent p is split by the plane
   through its centroid c_p with normal n_p.  The centroid is taken in voxel units as
   (centre of the voxel holding s_p) + (integer sum of minimum-image voxel offsets
   from that voxel) / count, so it is independent of summation order.  A voxel of p

@@ -724,7 +724,7 @@ double vm_of(const double* s) {
   return std::sqrt(1.5 * (a * a + b * b + c * c + 2.0 * (s[3] * s[3] + s[4] * s[4] + s[5] * s[5])));
 }
 
-// a1: macroscopic increment and initial guess (first increment: C0-consistent free
+// Macroscopic increment and initial guess (first increment: C0-consistent free
 // components; later ones: the previous increment's macroscopic step).
 void initial_increment(rve_s* h, double dE0[6]) {
   int fi[6], ci[6], nf = 0, nc = 0;
@@ -1143,7 +1143,7 @@ rve_status inc_advance(rve_s* h, bool* finished, long long* iters) {
     const IterStatus stat = *h->st_host;
     rve_status st = close_iterations<T>(h, stat);
     if (st) return st;
-    // a8: commit the converged iterate
+    // commit the converged iterate
     note_converged(h, stat);
     const int it = stat.done_it;
     XArgs<T> ca = x_args<T>(h, h->spec[r.s_in(it)], nullptr, it);

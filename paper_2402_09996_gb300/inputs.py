@@ -10,7 +10,7 @@ Generator: SplitMix64 (Steele, Lea and Flood, "Fast splittable pseudorandom
 number generators", OOPSLA 2014), uniform doubles from the top 53 bits.
 
 Microstructure recipe (paper Section 2 uses a Matern-hardcore Voronoi model; the
-synthetic workloads here use uniform seeds, as documented in the design doc):
+synthetic workloads here use uniform seeds):
 
 * seeds s_n uniform in the unit cube, one per grain (Voronoi generators, Sec. 2.1);
 * orientations Haar-uniform on SO(3) (Sec. 2.2, "uniform distribution on the

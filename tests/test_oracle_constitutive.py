@@ -99,7 +99,7 @@ def test_slip_rate_sign_and_kinematic_law():
     """Pure resolved shear on ordinary system 3 at 1.05 r0 activates that system alone:
     gamma_dot takes the sign of tau - x, v_dot = |gamma_dot|, alpha_dot = gamma_dot -
     d |gamma_dot| alpha, eps_p_dot = gamma_dot m; with twins present the weighting
-    (1 - sum f) scales the slip part only (reading R13)."""
+    (1 - sum f) scales the slip part only (as written in Sec. 3)."""
     mat = orc.Material()
     law = orc.Constitutive(mat)
     k = 2

@@ -1,4 +1,4 @@
-"""Pins of the oracle's Green operator and discrete wave vectors (reading R9)."""
+"""Pins of the oracle's Green operator and discrete wave vectors (Willot's rotated scheme)."""
 import numpy as np
 
 from oracle import rve_oracle as orc

@@ -15,7 +15,7 @@ def test_systems_orthogonal_unit_and_distinct():
     assert np.allclose(np.linalg.norm(l, axis=1), 1.0)
     assert kinds.count("o") == 4 and kinds.count("s") == 8 and kinds.count("t") == 4
     pairs = {(tuple(np.round(a, 12)), tuple(np.round(np.abs(b), 12))) for a, b in zip(n, l)}
-    assert len(pairs) == 16  # reading R1 removes the duplicate of system 7
+    assert len(pairs) == 16  # system 9 read as (1 -1 1)[1 1 0], not the printed duplicate of system 7
     # ordinary dislocations glide along 1/2<110]: no c component (c/a = 1 frame)
     for k, d in zip(kinds, l):
         if k == "o":
@@ -67,7 +67,7 @@ def test_uniaxial_moduli_closed_form():
 
 def test_reference_medium():
     """Mandel eigenvalues {105641.8, 109000, 156000, 210000, 210000, 329358.2} MPa give
-    2 mu0 = 3 k0 = 217500 MPa, so mu0 = 108750 and lam0 = 0 (reading R10)."""
+    2 mu0 = 3 k0 = 217500 MPa, so mu0 = 108750 and lam0 = 0 (the isotropic reference medium)."""
     ev = np.linalg.eigvalsh(orc.mandel_matrix(orc.stiffness_tensor(orc.Material())))
     assert np.allclose(ev, [105641.8, 109000, 156000, 210000, 210000, 329358.2], atol=0.1)
     lam0, mu0 = orc.reference_medium(orc.Material())

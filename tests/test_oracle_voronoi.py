@@ -1,4 +1,4 @@
-"""Pins of the oracle's periodic Voronoi labelling (Sec. 2.1) and twin split (R14, R17)
+"""Pins of the oracle's periodic Voronoi labelling (Sec. 2.1) and twin split
 against hand-derived partitions."""
 import numpy as np
 

@@ -45,7 +45,7 @@ typedef enum {
   RVE_ERR_NOT_CONVERGED = 4, /* fixed point hit max_iter; increment not committed */
   RVE_ERR_NAN = 5,           /* NaN/Inf in the averages; increment not committed */
   RVE_ERR_STATE = 6,         /* call not valid in the handle's state */
-  RVE_ERR_UNSUPPORTED = 7    /* grid size or option this build does not handle */
+  RVE_ERR_UNSUPPORTED = 7    /* grid size or option the library does not handle */
 } rve_status;
 
 typedef enum {

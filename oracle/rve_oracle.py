@@ -338,9 +338,27 @@ class Constitutive:
 
 
 def von_mises(sig: np.ndarray) -> np.ndarray:
-    """sqrt(3/2 s:s) with s the deviator (Sec. 5, equivalent stress)."""
+    """sqrt(3/2 s:s) with s the deviator (Sec. 5, equivalent stress).
+
+    Parity: pinned (tests/test_oracle_effective.py: uniaxial stress s gives |s|, pure
+    shear t gives sqrt(3) |t|, hydrostatic stress gives 0, rotation invariance).
+    """
     s = sig - np.trace(sig, axis1=-2, axis2=-1)[..., None, None] * np.eye(3) / 3.0
     return np.sqrt(1.5 * np.sum(s * s, axis=(-2, -1)))
+
+
+def effective_averages(v: np.ndarray):
+    """The Sec. 5 averages of the internal variables over the RVE: (<f_beta>, <v^s>).
+
+    v: (V, 16) accumulated slip of the 12 slip systems followed by the 4 twin systems.
+    <f_beta> is the mean over the 4 twin systems and all voxels of the twin volume
+    fraction f = sqrt(2) v^beta (Sec. 3); <v^s> the mean over the 12 slip systems and all
+    voxels of v^s (twins excluded).
+    Parity: pinned (tests/test_oracle_effective.py: hand-set v on a few voxels).
+    """
+    mean_f = float(np.mean(SQRT2 * v[:, N_SLIP:]))
+    mean_v = float(np.mean(v[:, :N_SLIP]))
+    return mean_f, mean_v
 
 
 # ----------------------------------------------------------------------------------
@@ -381,6 +399,39 @@ def wave_vectors(shape, scheme: str = "willot"):
     else:
         raise ValueError(scheme)
     return out
+
+
+def hermitian_weights(nx: int) -> np.ndarray:
+    """Multiplicity of each stored kx of the half spectrum of a real field: 1 for kx = 0
+    and (nx even) for the Nyquist plane kx = nx/2, whose conjugate partners are stored
+    themselves, 2 for every other kx, which also stands for its unstored partner -kx."""
+    w = np.full(nx // 2 + 1, 2.0)
+    w[0] = 1.0
+    if nx % 2 == 0:
+        w[-1] = 1.0
+    return w
+
+
+def equilibrium_error(sig_grid: np.ndarray, kappa: np.ndarray) -> float:
+    """Equilibrium error of a stress field (the fixed point's stopping test; the paper
+    gives no criterion, so the Moulinec-Suquet measure with the scheme's own wave vectors):
+
+        e = sqrt( sum over all frequencies xi of |kappa(xi) . sigma_hat(xi)|^2 ) / |sigma_hat(0)|
+
+    with the unnormalised transform sigma_hat, the Frobenius norm of the 3x3 tensor
+    sigma_hat(0) = N <sigma>, and the sum over the full spectrum taken on the half
+    spectrum with hermitian_weights.  sig_grid: (nz, ny, nx, 3, 3) real; kappa:
+    wave_vectors(shape).
+    Parity: pinned (tests/test_oracle_effective.py: single Fourier modes on the kx = 0
+    plane, an interior plane and the Nyquist plane against hand values; divergence-free
+    fields give 0).
+    """
+    nx = sig_grid.shape[2]
+    sig_hat = np.fft.rfftn(sig_grid, axes=(0, 1, 2))
+    div = np.einsum("zyxij,zyxj->zyxi", sig_hat, kappa)
+    num = np.sum(hermitian_weights(nx)[None, None, :] * np.sum(np.abs(div) ** 2, axis=-1))
+    denom = np.linalg.norm(sig_hat[0, 0, 0])
+    return math.sqrt(num) / denom if denom > 0 else 0.0
 
 
 def green_tensor(kappa, lam0, mu0):
@@ -487,12 +538,6 @@ class OracleRVE:
         self.lam0, self.mu0 = reference_medium(self.mat)
         self.C0 = isotropic_tensor(self.lam0, self.mu0)
         self.kappa = wave_vectors(self.shape, self.opts.scheme)
-        nx = self.shape[2]
-        w = np.full(nx // 2 + 1, 2.0)
-        w[0] = 1.0
-        if nx % 2 == 0:
-            w[-1] = 1.0
-        self.hermitian_w = w[None, None, :]
         V = self.N
         # committed state at t_n (sample-frame strain, crystal-frame internal variables)
         self.eps_n = np.zeros((V, 3, 3))
@@ -568,13 +613,9 @@ class OracleRVE:
             sig, ep_new, v_new, a_new = self.constitutive(eps)
             sig_mean = sig.mean(axis=0)
             tau = sig - np.einsum("ijkl,vkl->vij", self.C0, eps)
-            # forward transforms; equilibrium and stress-constraint errors
-            sig_hat = self._fft(sig)
+            # forward transform of tau; equilibrium and stress-constraint errors
             tau_hat = self._fft(tau)
-            div = np.einsum("zyxij,zyxj->zyxi", sig_hat, self.kappa)
-            num = np.sum(self.hermitian_w * np.sum(np.abs(div) ** 2, axis=-1))
-            denom = np.linalg.norm(sig_hat[0, 0, 0])
-            e_eq = math.sqrt(num) / denom if denom > 0 else 0.0
+            e_eq = equilibrium_error(self._grid(sig), self.kappa)
             sm = to_mandel(sig_mean)
             miss = (sm - Sigma_m)[free]
             c_F = float(np.linalg.norm(miss) / np.linalg.norm(sm)) if np.any(free) else 0.0
@@ -602,6 +643,7 @@ class OracleRVE:
         self.sigma_n = sig
         self.time += ld.dt
         self.increment += 1
+        mean_f, mean_v = effective_averages(self.v)
         rec = {
             "increment": self.increment,
             "time": self.time,
@@ -609,8 +651,8 @@ class OracleRVE:
             "S": _tensor_to_voigt6(sig_mean),
             "S_eq_of_mean": float(von_mises(sig_mean)),
             "mean_S_eq": float(np.mean(von_mises(sig))),
-            "mean_f": float(np.mean(SQRT2 * self.v[:, N_SLIP:])),
-            "mean_v": float(np.mean(self.v[:, :N_SLIP])),
+            "mean_f": mean_f,
+            "mean_v": mean_v,
             "iterations": it + 1,
             "residual": residuals[-1][0],
             "stress_residual": residuals[-1][1],

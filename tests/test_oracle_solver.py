@@ -38,6 +38,8 @@ def test_uniaxial_stress_modulus_single_crystal():
     rec = rve.step()
     assert abs(rec["S"][2] / rec["E"][2] - 135385.2) < 0.05
     assert np.max(np.abs(np.delete(rec["S"], 2))) < 1e-9 * rec["S"][2]
+    # uniaxial mean stress: its von Mises value is the axial stress itself (Sec. 5 measure)
+    assert abs(rec["S_eq_of_mean"] - rec["S"][2]) < 1e-9 * rec["S"][2]
 
 
 @pytest.mark.parametrize("scheme", ["willot", "ms"])

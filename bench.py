@@ -1,25 +1,41 @@
-"""Benchmark: voxel-iterations/s of the FFT Green-operator / Meric-Cailletaud fixed point.
+"""Benchmark: voxel-iterations/s of the FFT Green-operator / Meric-Cailletaud fixed point,
+FP32 batched against FP64 plain, and the adjoint/forward time.
 
-Workload (N = 1): the twinned 128^3 RVE -- 200 Voronoi grains, each split into parent
-and twin with probability 0.5 -- in FP32 fields with FP64 norms, uniaxial tension along
-z at 1e-3/s with the other mean stresses held at zero, increments of 0.5 s (the 40
-increments to 2 % of the workload description).  One benchmark step is one load
-increment (all hot-path steps: increment, fixed-point iterations of constitutive update,
-polarisation, forward FFT, Green operator, residual, inverse FFT, mixed-load update,
-commit).  Warm-up steps are the first increments of the loading path; the timed steps
-follow them.  A voxel-iteration is one voxel passing once through one fixed-point
-iteration; the rate counts committed iterations only.
+Default line (N = 1).  `value` is the batched ensemble: 16 RVE realizations (4 each of
+64^3, 96^3, 128^3 and 160^3 voxels with 50/125/241/400 Voronoi grains; two of each size
+split into parent and twin domains with probability 0.5) in FP32 fields with FP64 norms,
+all stepped together by rve_step_batch under uniaxial tension along z at 1e-3/s with the
+other mean stresses held at zero, increments of 0.5 s.  One benchmark step is one load
+increment of every member (all hot-path steps: increment, fixed-point iterations of
+constitutive update, polarisation, forward FFT, Green operator, residual, inverse FFT,
+mixed-load update, commit).  Warm-up steps are the first increments of the loading path;
+the K timed steps follow them.  A voxel-iteration is one voxel passing once through one
+fixed-point iteration; the rate counts committed iterations only.  Inputs are resident in
+HBM (the per-iteration state, ~6 GB, is far larger than L2).
 
-Multi-GPU (torchrun): replicas only -- every rank solves its own realization (seed offset
-by the rank), no data-path collective; value = all ranks' voxel-iterations / max time.
+The same line carries: the FP64 plain path (the 16^3 plain workload over its 10
+increments, and the twinned 128^3 grid on a bounded sample) and the speedup against it;
+the twinned 128^3 RVE alone in FP32 (its per-kernel CUDA-event times give the roofline of
+the dominant kernel, the x pass); the adjoint/forward time of the 96^3 calibration
+workload with checkpoints every 5 increments; cuFFT R2C + C2R of the same 6-component
+fields timed beside the solver's own transform passes (a comparison only: nothing of cuFFT
+is on the solver's path); measured ALU peaks; the end-to-end rate through the public API
+from host buffers; and the FP64 CPU oracle timed on this machine's cores.
 
---impl reference times the FP64 CPU oracle (numpy) on a bounded sample of the same
-workload (a 32^3 block of the 128^3 grain map, one fixed-point iteration per step).
+Multi-GPU (torchrun): replicas only -- every rank steps its own ensemble (seeds offset by
+the rank), no data-path collective; value = all ranks' voxel-iterations / max time; the
+side legs run on rank 0 at N = 1 only.
+
+--impl reference times the FP64 CPU oracle (numpy, unchanged) on the host cores: one
+process per core, each on a 32^3 block of an ensemble member's grain map; one step = one
+fixed-point iteration of every block.
 """
 from __future__ import annotations
 
 import argparse
 import json
+import math
+import multiprocessing as mp
 import os
 import statistics
 import subprocess
@@ -33,11 +49,18 @@ ROOT = Path(__file__).resolve().parent
 sys.path.insert(0, str(ROOT))
 
 METRIC = "voxel-iterations/s"
-WORKLOAD = "twinned RVE 128^3, 200 Voronoi grains (p_twin 0.5), FP32 fields + FP64 norms, uniaxial tension 1e-3/s, dt 0.5 s"
-# algorithmic work per voxel-iteration (per-unit figures of the design notes)
+ENSEMBLE_WORKLOAD = ("ensemble of 16 RVEs: 4 each of 64^3, 96^3, 128^3, 160^3 voxels (50/125/241/400 Voronoi "
+                     "grains), two of each size twinned (p_twin 0.5); FP32 fields + FP64 norms; uniaxial tension "
+                     "1e-3/s with the other mean stresses zero, dt 0.5 s; all members stepped together "
+                     "(rve_step_batch)")
+WORKLOAD_128 = ("twinned RVE 128^3, 200 Voronoi grains (p_twin 0.5), FP32 fields + FP64 norms, uniaxial tension "
+                "1e-3/s, dt 0.5 s")
+# algorithmic work per voxel-iteration: state in + stress out + one spectral round trip (bytes);
+# four RK stages per substep, each one right-hand side with its rate-root solves (flops)
 BYTES_PER_VOXIT_FP32 = 260          # state + strain/stress traffic of the fused iteration
 FLOPS_RHS = 1100                    # one evaluation of the constitutive right-hand side
-FP32_LANES_PER_SM, N_SM = 128, 152  # GB300
+N_SUB = 4                           # RK4 substeps at dt = 0.5 s
+DT = 0.5
 # DRAM bytes (read + write) of one trial x-pass launch on the 128^3 FP32 workload, from ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum, mean of two launches); valid for the x-pass
 # source as profiled, to be re-taken whenever that kernel changes
@@ -46,6 +69,13 @@ XPASS_DRAM_BYTES_128 = 438_034_560
 
 def flops_per_voxit(n_sub):
     return 4 * n_sub * FLOPS_RHS + 200
+
+
+def launches_per_increment(iterations):
+    """Kernel launches of one increment on the graph path: the strain shift, iteration 0
+    (4 kernels), then loop bodies of two iterations plus a guard kernel (the second
+    iteration of the last body returns at once when the first decided), and the commit."""
+    return 1 + 4 + 9 * (iterations // 2) + 1
 
 
 def aggregate_ranks(dist, work, ms, device="cpu"):
@@ -121,87 +151,484 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def measure_alu_peaks(target_ms=40.0, repeats=3):
+    """Measured ALU rates of this GPU (rve_alu_probe): FP32 and FP64 FMA (TFLOP/s, an FMA
+    counted as 2) and FP32 MUFU ex2 (Top/s).  Each probe runs 8 CTAs of 256 threads per SM,
+    its length calibrated to about target_ms; best of `repeats` launches, CUDA events on
+    the launching stream."""
+    import torch
+
+    from paper_2402_09996_gb300 import rve
+
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    blocks = props.multi_processor_count * 8
+    sink = torch.zeros(4, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed(kind, iters):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ops = rve.alu_probe(kind, blocks, iters, sink)
+        b.record(stream)
+        b.synchronize()
+        return ops, a.elapsed_time(b)
+
+    out = {"sms": props.multi_processor_count, "blocks": blocks, "threads_per_block": 256}
+    for kind, name in ((0, "fp32_fma_tflops"), (1, "fp64_fma_tflops"), (2, "fp32_ex2_tops")):
+        iters = 64
+        ops, ms = timed(kind, iters)
+        while ms < 2.0 and iters < (1 << 24):  # grow until the launch is long enough to scale from
+            iters *= 4
+            ops, ms = timed(kind, iters)
+        iters = max(1, int(iters * target_ms / ms))
+        best = 0.0
+        for _ in range(repeats):
+            ops, ms = timed(kind, iters)
+            best = max(best, ops / (ms * 1e-3) / 1e12)
+        out[name] = best
+    return out
+
+
+def _measured_peaks():
+    try:
+        return json.load(open(ROOT / "MEASURED_PEAKS.json"))
+    except (OSError, ValueError):
+        return {}
+
+
+def _measured_hbm():
+    return _measured_peaks().get("hbm_gbs")
+
+
 def make_workload(rank):
+    """The twinned 128^3 workload (realization seed 1000 + rank)."""
     from paper_2402_09996_gb300 import inputs
 
-    inp = inputs.make_inputs((128, 128, 128), 200, 0.5, seed=1000 * 1 + rank)
-    return inp
+    return inputs.make_inputs((128, 128, 128), 200, 0.5, seed=1000 * 1 + rank)
 
 
+def ensemble_members(rank=0):
+    """The 16 ensemble realizations; other ranks draw other realizations (seed offset)."""
+    from paper_2402_09996_gb300 import inputs
+
+    if rank == 0:
+        return inputs.workload_ensemble()
+    out = []
+    for r, (n, g) in enumerate((n, g) for n, g in zip(inputs.ENSEMBLE_SIZES, inputs.ENSEMBLE_GRAINS)
+                               for _ in range(4)):
+        out.append(inputs.make_inputs((n, n, n), g, 0.5 if r % 4 < 2 else 0.0, seed=1000 * 3 + 100 * rank + r))
+    return out
+
+
+def _event_pair():
+    import torch
+
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def _iterations(solvers):
+    return [sum(h["iterations"] for h in s.history()) for s in solvers]
+
+
+# ---------------------------------------------------------------- legs ------------------
+def leg_ensemble(members, warmup, steps, dist=None, clocks=None):
+    """The headline: every member stepped together; device time of the K timed increments
+    (CUDA events on the launching stream, which the batch call's private streams join)."""
+    import torch
+
+    from paper_2402_09996_gb300 import rve
+
+    solvers = []
+    for inp in members:
+        s = rve.RVE(rve.label_voronoi(inp), inp.euler, precision=rve.FP32, n_sub=0)
+        s.set_mixed_load(dt=DT)
+        solvers.append(s)
+    rve.step_batch(solvers, warmup)
+    before = _iterations(solvers)
+    stream = torch.cuda.current_stream()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+    t0, t1 = _event_pair()
+    t0.record(stream)
+    rve.step_batch(solvers, steps)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop() if clocks else None
+    ms = t0.elapsed_time(t1)
+    per_inc = [[h["iterations"] for h in s.history()[warmup:]] for s in solvers]
+    its = [a - b for a, b in zip(_iterations(solvers), before)]
+    nvox = [s.nvox for s in solvers]
+    hist_last = solvers[-1].history()[-1]
+    for s in solvers:
+        s.close()
+    voxit = float(sum(n * i for n, i in zip(nvox, its)))
+    launches = int(sum(launches_per_increment(i) for row in per_inc for i in row))
+    return {"ms": ms, "voxit": voxit, "iterations": its, "nvox": nvox, "clocks": clk, "launches": launches,
+            "last": {"E33": hist_last["E"][2], "S33": hist_last["S"][2]}}
+
+
+def leg_e2e(members, warmup, steps):
+    """The same K increments through the public API from host buffers: handles created from
+    pinned host grain maps (set-up, untimed), the W warm-up increments untimed; then, timed
+    on the host clock, every step re-states each member's load from host memory
+    (rve_set_mixed_load), runs the increment of every member (rve_step_batch, whose status
+    records come back to the host each increment) and reads each member's effective record
+    (rve_get_effective); after the last step every member's stress field is copied to host
+    memory."""
+    import torch
+
+    from paper_2402_09996_gb300 import rve
+
+    maps = []
+    for inp in members:
+        g = np.ascontiguousarray(np.asarray(rve.label_voronoi(inp), dtype=np.uint32))
+        pinned = torch.from_numpy(g.reshape(-1).view(np.int32)).pin_memory()
+        maps.append((pinned.numpy().view(np.uint32).reshape(g.shape), pinned))
+    solvers = []
+    for (g, _), inp in zip(maps, members):
+        s = rve.RVE(g, inp.euler, precision=rve.FP32, n_sub=0)
+        s.set_mixed_load(dt=DT)
+        solvers.append(s)
+    rve.step_batch(solvers, warmup)
+    before = _iterations(solvers)
+    load = [torch.tensor(v, dtype=d).pin_memory().numpy() for v, d in
+            (([0, 0, 1e-3, 0, 0, 0], torch.float64), ([0, 0, 1, 0, 0, 0], torch.uint8), ([0.0] * 6, torch.float64))]
+    torch.cuda.synchronize()
+    c0 = time.perf_counter()
+    for _ in range(steps):
+        for s in solvers:
+            s.set_mixed_load(Edot=load[0], strain_ctrl=load[1], Sigma=load[2], dt=DT)
+        rve.step_batch(solvers, 1)
+        for s in solvers:
+            s.effective()
+    fields = [s.field(rve.FIELD_STRESS) for s in solvers]
+    torch.cuda.synchronize()
+    c1 = time.perf_counter()
+    its = [a - b for a, b in zip(_iterations(solvers), before)]
+    nvox = [s.nvox for s in solvers]
+    for s in solvers:
+        s.close()
+    status_bytes = 224  # the per-increment status record (IterStatus) each member copies back
+    d2h = len(solvers) * status_bytes + sum(f.nbytes for f in fields) / steps
+    h2d = len(solvers) * 6 * 8  # each member's macroscopic strain E(0) of the increment, from pinned memory
+    return {"value": sum(n * i for n, i in zip(nvox, its)) / (c1 - c0), "unit": METRIC,
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "what": f"increments {warmup + 1}..{warmup + steps} of every member through the public API: per step "
+                    "the load restated from pinned host memory, rve_step_batch, the effective records read; "
+                    "every member's stress field (FP64) to host memory after the last step; host clock"}
+
+
+def leg_single_128(warmup, steps, rank=0):
+    """The twinned 128^3 RVE alone (FP32), per-launch CUDA events on the handle's stream
+    (host-driven iteration loop): the dominant kernel's duration for the roofline."""
+    import torch
+
+    from paper_2402_09996_gb300 import rve
+
+    inp = make_workload(rank)
+    s = rve.RVE(rve.label_voronoi(inp), inp.euler, precision=rve.FP32, timing=True, n_sub=0)
+    s.set_mixed_load(dt=DT)
+    s.step(warmup)
+    s.kernel_times(reset=True)
+    torch.cuda.synchronize()
+    t0, t1 = _event_pair()
+    stream = torch.cuda.current_stream()
+    t0.record(stream)
+    its = s.step(steps)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    kt = s.kernel_times()
+    nvox = s.nvox
+    s.close()
+    tot = sum(m for m, _ in kt.values())
+    return {"value": nvox * its / (t0.elapsed_time(t1) * 1e-3), "unit": METRIC, "voxels": nvox,
+            "increments_timed": f"{warmup + 1}..{warmup + steps}", "iterations": its,
+            "kernel_share": {k: round(m / tot, 4) for k, (m, _) in kt.items() if tot > 0},
+            "kernel_avg_ms": {k: (m / n if n else None) for k, (m, n) in kt.items()},
+            "kernel_launches": {k: n for k, (_, n) in kt.items()}}
+
+
+def leg_fp64_plain():
+    """The FP64 path without batching: the 16^3 plain workload (8 untwinned grains) over its
+    whole load history (10 increments of 1 s), and the twinned 128^3 grid on a bounded
+    sample (increments 1-2 untimed, increment 3 -- the first with developed slip -- timed)."""
+    import torch
+
+    from paper_2402_09996_gb300 import inputs, rve
+
+    out = {}
+    stream = torch.cuda.current_stream()
+    inp = inputs.workload_plain_16()
+    with rve.RVE(rve.label_voronoi(inp), inp.euler, precision=rve.FP64) as s:
+        s.set_mixed_load(dt=1.0)
+        torch.cuda.synchronize()
+        t0, t1 = _event_pair()
+        t0.record(stream)
+        its = s.step(10)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        out["plain16"] = {"value": s.nvox * its / (t0.elapsed_time(t1) * 1e-3), "unit": METRIC,
+                          "iterations": its, "sample": "16^3, 8 grains, increments 1..10 (dt 1 s), FP64 throughout"}
+    inp = make_workload(0)
+    with rve.RVE(rve.label_voronoi(inp), inp.euler, precision=rve.FP64, n_sub=0) as s:
+        s.set_mixed_load(dt=DT)
+        s.step(2)
+        torch.cuda.synchronize()
+        t0, t1 = _event_pair()
+        t0.record(stream)
+        its = s.step(1)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        out["grid128"] = {"value": s.nvox * its / (t0.elapsed_time(t1) * 1e-3), "unit": METRIC,
+                          "iterations": its, "sample": "twinned 128^3 grid, increment 3 (dt 0.5 s), FP64 throughout"}
+    return out
+
+
+def leg_adjoint(n_inc=30, checkpoint_every=5):
+    """Adjoint calibration workload: 96^3 RVE, 300 Voronoi grains twinned with p 0.5, FP32
+    forward and adjoint, n_inc increments of 0.5 s; misfit of the sigma_zz curve against the
+    curve with r0 raised by 10 %; gradient by the adjoint of the history with checkpoints
+    every `checkpoint_every` increments (segments replayed in the reverse pass)."""
+    import torch
+
+    from paper_2402_09996_gb300 import inputs, rve
+
+    inp = inputs.make_inputs((96, 96, 96), 300, 0.5, seed=1000 * 4 + 0)
+    gid = rve.label_voronoi(inp)
+    base = rve.default_material().as_dict()
+    perturbed = {k: 1.1 * base[k] for k in ("r0_ord", "r0_sup", "r0_twin")}
+
+    def forward(mat):
+        with rve.RVE(gid, inp.euler, precision=rve.FP32) as s:
+            if mat:
+                s.set_material(**mat)
+            s.set_mixed_load(dt=DT)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            its = s.step(n_inc)
+            torch.cuda.synchronize()
+            return np.array([h["S"][2] for h in s.history()]), time.perf_counter() - t0, its
+
+    target, _, _ = forward(perturbed)
+    _, t_fwd, its = forward({})
+    torch.cuda.synchronize()
+    g0 = time.perf_counter()
+    J, gp, ge, info = rve.history_gradient(gid, inp.euler, n_inc, DT, target, precision=rve.FP32,
+                                           checkpoint_every=checkpoint_every)
+    torch.cuda.synchronize()
+    t_grad = time.perf_counter() - g0
+    return {"value": t_grad / t_fwd, "unit": "ratio", "seconds": {"forward": t_fwd, "gradient": t_grad},
+            "forward_iterations": its, "adjoint_iterations": info["adjoint_iterations"],
+            "checkpoints": info["checkpoints"], "J": J,
+            "workload": f"twinned 96^3, 300 grains, FP32 forward and adjoint, {n_inc} increments of 0.5 s, "
+                        f"checkpoints every {checkpoint_every} increments; target from r0 + 10 %"}
+
+
+def leg_fft_comparison(sizes=(96, 128, 160, 256), reps=5):
+    """cuFFT (torch.fft) R2C + C2R of 6 FP32 components on n^3 grids beside this library's
+    own transforms of the same fields (rve_fft_r2c / rve_fft_c2r) and the solver's y and
+    z/Green passes per iteration (per-launch CUDA events, first increment of a twinned n^3
+    RVE).  Comparison only: the solver never calls cuFFT."""
+    import torch
+
+    from paper_2402_09996_gb300 import inputs, rve
+
+    stream = torch.cuda.current_stream()
+
+    def med(fn):
+        fn()
+        ts = []
+        for _ in range(reps):
+            a, b = _event_pair()
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    rows = []
+    for n in sizes:
+        x = torch.randn((6, n, n, n), dtype=torch.float32, device="cuda")
+        spec = torch.fft.rfftn(x, dim=(1, 2, 3))
+        cu_f = med(lambda: torch.fft.rfftn(x, dim=(1, 2, 3)))
+        cu_i = med(lambda: torch.fft.irfftn(spec, s=(n, n, n), dim=(1, 2, 3)))
+        own_f = med(lambda: rve.fft_r2c(x, precision=rve.FP32))
+        own_spec = rve.fft_r2c(x, precision=rve.FP32)
+        own_i = med(lambda: rve.fft_c2r(own_spec.clone(), n, precision=rve.FP32))
+        del x, spec, own_spec
+        inp = inputs.make_inputs((n, n, n), 60, 0.5, seed=7)
+        with rve.RVE(rve.label_voronoi(inp), inp.euler, precision=rve.FP32, timing=True) as s:
+            s.set_mixed_load(dt=DT)
+            s.step(1)
+            kt = s.kernel_times()
+        avg = {k: (m / c if c else None) for k, (m, c) in kt.items()}
+        rows.append({"n": n, "cufft_r2c_ms": cu_f, "cufft_c2r_ms": cu_i, "own_r2c_ms": own_f, "own_c2r_ms": own_i,
+                     "solver_y_fwd_ms": avg["yfwd"], "solver_z_green_ms": avg["zgreen"],
+                     "solver_y_inv_ms": avg["yinv"], "solver_x_pass_ms": avg["xpass"],
+                     "solver_fft_passes_ms": avg["yfwd"] + avg["zgreen"] + avg["yinv"]})
+        torch.cuda.empty_cache()
+    return {"rows": rows,
+            "what": "6 FP32 components, n^3: cuFFT forward and inverse (torch.fft), this library's stand-alone "
+                    "transforms, and the solver's per-iteration y-forward, z/Green (forward z, Green operator, "
+                    "residual, inverse z) and y-inverse passes; the solver's x transforms are fused into the x pass "
+                    "with the constitutive update"}
+
+
+# ---------------------------------------------------------------- CPU oracle -------------
+def _oracle_block(k):
+    """A 32^3 block of ensemble member k % 16's parent grain map (ids compacted), as a
+    periodic oracle RVE with one fixed-point iteration per step."""
+    from oracle.rve_oracle import Load, Material, OracleRVE, Options
+    from oracle.voronoi import voronoi_labels
+    from paper_2402_09996_gb300 import inputs
+
+    inp = inputs.workload_ensemble()[k % 16]
+    nz, ny, nx = inp.shape
+    b = 32
+    o = (k // 16) * 8  # later blocks of a member are offset along the diagonal
+    kk, jj, ii = np.meshgrid(np.arange(b) + o, np.arange(b) + o, np.arange(b) + o, indexing="ij")
+    vox = ((ii % nx) + nx * ((jj % ny) + ny * (kk % nz))).reshape(-1)
+    parents = voronoi_labels(inp.shape, inp.seeds, voxels=vox).reshape(b, b, b)
+    ids, gid = np.unique(parents, return_inverse=True)
+    rve = OracleRVE(gid.reshape(b, b, b), inp.euler[ids], Material(), Options(fixed_iters=1))
+    rve.set_load(Load(dt=DT))
+    return rve
+
+
+def _oracle_worker(k, conn):
+    rve = _oracle_block(k)
+    conn.send(("ready", rve.N))
+    while True:
+        cmd = conn.recv()
+        if cmd is None:
+            break
+        t0 = time.perf_counter()
+        for _ in range(cmd):
+            rve.step()
+        conn.send(("done", time.perf_counter() - t0))
+
+
+class OraclePool:
+    """One spawned process per block (the oracle itself is single-threaded numpy); a step
+    runs `n` fixed-point iterations in every process at once."""
+
+    def __init__(self, n_proc):
+        ctx = mp.get_context("spawn")
+        env_keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+        saved = {k: os.environ.get(k) for k in env_keys}
+        for k in env_keys:
+            os.environ[k] = "1"
+        self.procs, self.conns = [], []
+        try:
+            for k in range(n_proc):
+                a, b = ctx.Pipe()
+                p = ctx.Process(target=_oracle_worker, args=(k, b), daemon=True)
+                p.start()
+                self.procs.append(p)
+                self.conns.append(a)
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+        self.voxels = [c.recv()[1] for c in self.conns]
+
+    def step(self, n=1):
+        for c in self.conns:
+            c.send(n)
+        return [c.recv()[1] for c in self.conns]
+
+    def close(self):
+        for c in self.conns:
+            c.send(None)
+        for p in self.procs:
+            p.join(timeout=10)
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(seconds=20.0):
+    """The oracle as it stands on bounded samples: one process per host core, each running
+    fixed-point iterations of its own 32^3 block, for about `seconds`; and one process
+    alone for per-core context."""
+    cores = cpu_cores()
+    out = {}
+    for n_proc, budget in ((cores, seconds), (1, seconds / 2)):
+        pool = OraclePool(n_proc)
+        pool.step(1)  # warm-up iteration
+        t0 = time.perf_counter()
+        done = 0
+        while time.perf_counter() - t0 < budget:
+            pool.step(1)
+            done += 1
+        el = time.perf_counter() - t0
+        pool.close()
+        out[n_proc] = {"value": sum(pool.voxels) * done / el, "iterations": done, "seconds": el}
+    all_c = out[cores]
+    return {"value": all_c["value"], "unit": METRIC, "cores": cores, "kind": "oracle",
+            "sample": f"{cores} processes (one per host core), each {all_c['iterations']} fixed-point iterations "
+                      f"of its own 32^3 block of an ensemble member's grain map (parents only), numpy FP64, "
+                      f"{all_c['seconds']:.1f} s",
+            "single_core": {"value": out[1]["value"], "unit": METRIC, "cores": 1,
+                            "sample": f"{out[1]['iterations']} iterations of one 32^3 block, {out[1]['seconds']:.1f} s"}}
+
+
+def run_reference(args):
+    dist, rank, ws = _dist()
+    if rank != 0:
+        return
+    cores = cpu_cores()
+    pool = OraclePool(cores)
+    for _ in range(args.warmup):
+        pool.step(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        pool.step(1)
+    el = time.perf_counter() - t0
+    pool.close()
+    value = sum(pool.voxels) * args.steps / el
+    sample = (f"{cores} processes (one per host core), each one fixed-point iteration per step of its own 32^3 "
+              f"block of an ensemble member's grain map, numpy FP64")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": ENSEMBLE_WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------- default line -----------
 def run_gpu(args):
     import torch
 
-    from paper_2402_09996_gb300 import build_lib, rve
+    from paper_2402_09996_gb300 import build_lib
 
     dist, rank, ws = _dist()
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     build_lib.build()
-    inp = make_workload(rank)
-    gid = rve.label_voronoi(inp)
-    dt = 0.5
-    n_sub = 4
-    solver = rve.RVE(gid, inp.euler, precision=rve.FP32, timing=True, n_sub=0)
-    solver.set_mixed_load(dt=dt)
-    nvox = solver.nvox
-    # warm-up: the first increments of the loading path
-    solver.step(args.warmup)
-    solver.kernel_times(reset=True)
-    stream = torch.cuda.current_stream()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks = ClockSampler(local)
-    clocks.start()
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
-    t0.record(stream)
-    iters = solver.step(args.steps)
-    t1.record(stream)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    clk = clocks.stop()
-    ms = t0.elapsed_time(t1)
-    ktimes = solver.kernel_times()
-    hist = solver.history()
-    solver.close()
-    # aggregate over ranks: total voxel-iterations, max time
-    tot = np.array(aggregate_ranks(dist, float(nvox * iters), ms, device="cuda"))
+    side = rank == 0 and ws == 1 and not args.headline_only
+    peaks = measure_alu_peaks() if side else None
+    members = ensemble_members(rank)
+    ens = leg_ensemble(members, args.warmup, args.steps, dist, ClockSampler(local))
+    tot = np.array(aggregate_ranks(dist, ens["voxit"], ens["ms"], device="cuda"))
     value = tot[0] / (tot[1] * 1e-3)
-
-    # end-to-end through the public API from host buffers: create (H2D of the grain map
-    # and orientations), warm-up + timed increments, effective curve and stress field D2H
-    e2e = None
-    if rank == 0 or True:
-        gid_host = np.ascontiguousarray(np.asarray(gid, dtype=np.uint32))
-        pinned_gid = torch.from_numpy(gid_host.reshape(-1).view(np.int32)).pin_memory()
-        torch.cuda.synchronize()
-        c0 = time.perf_counter()
-        s2 = rve.RVE(pinned_gid.numpy().view(np.uint32).reshape(gid_host.shape), inp.euler, precision=rve.FP32, n_sub=0)
-        s2.set_mixed_load(dt=dt)
-        it2 = s2.step(args.warmup + args.steps)
-        h2 = s2.history()
-        sig = s2.field(rve.FIELD_STRESS)
-        torch.cuda.synchronize()
-        c1 = time.perf_counter()
-        s2.close()
-        n_steps = args.warmup + args.steps
-        e2e = {"value": nvox * it2 / (c1 - c0), "unit": METRIC,
-               "h2d_bytes_per_step": int((gid_host.nbytes + inp.euler.nbytes) / n_steps),
-               "d2h_bytes_per_step": int((sig.nbytes + len(h2) * 160) / n_steps),
-               "what": f"create from host grain map + {n_steps} increments from rest + stress field to host"}
+    e2e = leg_e2e(members, args.warmup, args.steps)
     if rank != 0:
         return
-    # roofline of the dominant kernel (x pass: constitutive update fused with the x-FFTs)
-    kx_ms, kx_n = ktimes["xpass"]
-    avg = kx_ms / max(kx_n, 1)
-    flops = flops_per_voxit(n_sub) * nvox
-    peak_mhz = 2070.0
-    peak = FP32_LANES_PER_SM * N_SM * 2 * peak_mhz * 1e6 / 1e12
-    achieved = flops / (avg * 1e-3) / 1e12
-    launches = int(sum(n for _, n in ktimes.values()))
-    total_k_ms = sum(m for m, _ in ktimes.values())
     line = {
         "metric": METRIC,
         "value": value,
@@ -215,187 +642,47 @@ def run_gpu(args):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "voxels": nvox, "grains": int(inp.n_grains),
+        "config": {"workload": ENSEMBLE_WORKLOAD, "voxels": int(sum(ens["nvox"])),
                    "increments_timed": f"{args.warmup + 1}..{args.warmup + args.steps}",
-                   "fixed_point_iterations_timed": int(iters), "n_sub": n_sub,
-                   "l2": "inputs larger than L2 (per-iteration state ~390 MB)",
-                   "parallelism": f"replicas x{ws}"},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": XPASS_DRAM_BYTES_128 if nvox == 128 ** 3 else None,
-                     "traffic_unit": "bytes per launch", "kernel": "k_xpass", "avg_launch_ms": avg,
-                     "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz"},
-        "kernel_share": {k: round(m / total_k_ms, 4) for k, (m, _) in ktimes.items() if total_k_ms > 0},
-        "kernel_avg_ms": {k: (m / n if n else None) for k, (m, n) in ktimes.items()},
-        "hbm": {"bytes_per_voxit": BYTES_PER_VOXIT_FP32, "achieved_gbs": BYTES_PER_VOXIT_FP32 * value / 1e9,
-                "peak_gbs_measured": _measured_hbm()},
-        "gpu_launches": launches,
-        "clocks": clk,
+                   "fixed_point_iterations_timed": ens["iterations"], "n_sub": N_SUB,
+                   "l2": "inputs larger than L2 (per-iteration state ~6 GB)", "parallelism": f"replicas x{ws}"},
+        "gpu_launches": ens["launches"],
+        "clocks": ens["clocks"],
         "e2e": e2e,
-        "effective_last": {"E33": hist[-1]["E"][2], "S33": hist[-1]["S"][2], "iterations": hist[-1]["iterations"]},
+        "effective_last_member": ens["last"],
     }
-    if not args.no_cpu_baseline and ws == 1:
-        line["cpu_baseline"] = cpu_baseline(seconds=args.cpu_seconds)
-    print(json.dumps(line))
-
-
-def _measured_hbm():
-    try:
-        return json.load(open(ROOT / "MEASURED_PEAKS.json"))["hbm_gbs"]
-    except (OSError, KeyError, ValueError):
-        return None
-
-
-def _oracle_sample():
-    """A 32^3 block of the 128^3 workload's grain map (ids compacted), as a periodic RVE."""
-    from oracle.rve_oracle import Material, OracleRVE, Options, Load
-    from oracle.voronoi import voronoi_labels
-
-    inp = make_workload(0)
-    n = 32
-    k, j, i = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
-    vox = (i + 128 * (j + 128 * k)).reshape(-1)
-    parents = voronoi_labels(inp.shape, inp.seeds, voxels=vox).reshape(n, n, n)
-    ids, gid = np.unique(parents, return_inverse=True)
-    rve = OracleRVE(gid.reshape(n, n, n), inp.euler[ids], Material(), Options(fixed_iters=1))
-    rve.set_load(Load(dt=0.5))
-    return rve
-
-
-def cpu_baseline(seconds=20.0, steps=None):
-    """The oracle as it stands on a bounded sample: fixed-point iterations of a 32^3 block."""
-    rve = _oracle_sample()
-    done = 0
-    t0 = time.perf_counter()
-    while True:
-        rve.step()
-        done += 1
-        el = time.perf_counter() - t0
-        if (steps is not None and done >= steps) or (steps is None and el > seconds):
-            break
-    value = rve.N * done / el
-    return {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
-            "sample": f"{done} fixed-point iterations (one increment each) of a 32^3 block of the 128^3 grain map, "
-                      f"numpy FP64, {el:.1f} s"}
-
-
-def run_reference(args):
-    dist, rank, ws = _dist()
-    if rank != 0:
-        return
-    rve = _oracle_sample()
-    for _ in range(args.warmup):
-        rve.step()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        rve.step()
-    el = time.perf_counter() - t0
-    value = rve.N * args.steps / el
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": "32^3 block of the 128^3 grain map, one fixed-point "
-                                                     "iteration per step"},
-            "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} iterations of a 32^3 block"},
-            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line))
-
-
-def run_ensemble(args):
-    """Batched ensemble: 16 RVEs of 64^3..160^3 (half twinned) stepped together with
-    rve_step_batch in FP32 fields, against the FP64 plain path (one RVE at a time) timed
-    on a bounded sample.  One step = one load increment of every member."""
-    import torch
-
-    from paper_2402_09996_gb300 import build_lib, inputs, rve
-
-    build_lib.build()
-    members = inputs.workload_ensemble()
-    dt = 0.5
-    stream = torch.cuda.current_stream()
-
-    def build():
-        out = []
-        for inp in members:
-            s = rve.RVE(rve.label_voronoi(inp), inp.euler, precision=rve.FP32, n_sub=0)
-            s.set_mixed_load(dt=dt)
-            out.append(s)
-        rve.step_batch(out, args.warmup)
-        torch.cuda.synchronize()
-        return out, [sum(h["iterations"] for h in s.history()) for s in out]
-
-    def timed(fn, solvers, before):
-        t0 = torch.cuda.Event(enable_timing=True)
-        t1 = torch.cuda.Event(enable_timing=True)
-        t0.record(stream)
-        fn()
-        t1.record(stream)
-        torch.cuda.synchronize()
-        its = [sum(h["iterations"] for h in s.history()) - b for s, b in zip(solvers, before)]
-        return t0.elapsed_time(t1), its
-
-    # the same increments twice: every member stepped alone in turn, then all together
-    solvers, before = build()
-    nvox = [s.nvox for s in solvers]
-    ms_seq, its_seq = timed(lambda: [s.step(args.steps) for s in solvers], solvers, before)
-    for s in solvers:
-        s.close()
-    solvers, before = build()
-    clocks = ClockSampler(torch.cuda.current_device())
-    clocks.start()
-    ms, its = timed(lambda: rve.step_batch(solvers, args.steps), solvers, before)
-    clk = clocks.stop()
-    for s in solvers:
-        s.close()
-    voxit = float(sum(n * i for n, i in zip(nvox, its)))
-    value = voxit / (ms * 1e-3)
-    seq_value = float(sum(n * i for n, i in zip(nvox, its_seq))) / (ms_seq * 1e-3)
-
-    # FP64 plain path on a bounded sample: the first 64^3 twinned member alone, its first
-    # warm-up increments untimed, then one timed increment in the plastic regime
-    inp = members[0]
-    s64 = rve.RVE(rve.label_voronoi(inp), inp.euler, precision=rve.FP64, n_sub=0)
-    s64.set_mixed_load(dt=dt)
-    s64.step(args.warmup)
-    torch.cuda.synchronize()
-    u0 = torch.cuda.Event(enable_timing=True)
-    u1 = torch.cuda.Event(enable_timing=True)
-    u0.record(stream)
-    it64 = s64.step(1)
-    u1.record(stream)
-    torch.cuda.synchronize()
-    fp64_value = s64.nvox * it64 / (u0.elapsed_time(u1) * 1e-3)
-    s64.close()
-    n_sub = 4
-    line = {
-        "metric": METRIC,
-        "value": value,
-        "unit": METRIC,
-        "n_gpus": 1,
-        "steps": args.steps,
-        "warmup": args.warmup,
-        "ms_per_step": ms / args.steps,
-        "higher_is_better": True,
-        "scaling": "weak",
-        "vs_baseline": None,
-        "dtype": "f32",
-        "data": "synthetic",
-        "config": {"workload": "ensemble of 16 RVEs: 4 each of 64^3, 96^3, 128^3, 160^3 (50/125/241/400 grains), "
-                               "two of each size twinned (p_twin 0.5); FP32 fields + FP64 norms; uniaxial tension "
-                               "1e-3/s, dt 0.5 s; all members stepped together (rve_step_batch)",
-                   "voxels": int(sum(nvox)), "increments_timed": f"{args.warmup + 1}..{args.warmup + args.steps}",
-                   "fixed_point_iterations_timed": its, "n_sub": n_sub,
-                   "l2": "inputs larger than L2 (state ~6 GB)"},
-        "whole_step_alu": {"achieved": flops_per_voxit(n_sub) * value / 1e12,
-                           "peak": FP32_LANES_PER_SM * N_SM * 2 * 2070.0 * 1e6 / 1e12, "unit": "TFLOP/s",
-                           "what": "algorithmic flops of the whole iteration over the whole batch time"},
-        "fp32_sequential": {"value": seq_value, "unit": METRIC, "ms_per_step": ms_seq / args.steps,
-                            "what": "the same increments, each member stepped alone in turn (rve_step)"},
-        "fp64_plain": {"value": fp64_value, "unit": METRIC,
-                       "sample": f"64^3 twinned member alone in FP64, increment {args.warmup + 1}, {it64} iterations"},
-        "speedup_fp32_batched_vs_fp64_plain": value / fp64_value,
-        "clocks": clk,
-    }
+    if side:
+        single = leg_single_128(args.warmup, args.steps)
+        fp32_peak = peaks["fp32_fma_tflops"]
+        kx_ms = single["kernel_avg_ms"]["xpass"]
+        achieved = flops_per_voxit(N_SUB) * single["voxels"] / (kx_ms * 1e-3) / 1e12
+        hbm = _measured_hbm()
+        line["roofline"] = {
+            "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+            "traffic": XPASS_DRAM_BYTES_128, "traffic_unit": "bytes per launch", "kernel": "k_xpass",
+            "avg_launch_ms": kx_ms,
+            "measured_in": "twinned 128^3 RVE alone (single_rve_128 leg), per-launch CUDA events on its stream",
+            "peak_note": "FP32 FMA rate measured by rve_alu_probe in this run (of measured)",
+            "algorithmic_flops_per_voxit": flops_per_voxit(N_SUB)}
+        line["alu"] = {"whole_step_tflops": flops_per_voxit(N_SUB) * value / 1e12,
+                       "frac_of_measured_fp32": flops_per_voxit(N_SUB) * value / 1e12 / fp32_peak}
+        ridge = fp32_peak * 1e12 / (hbm * 1e9) if hbm else None
+        line["hbm"] = {"bytes_per_voxit": BYTES_PER_VOXIT_FP32, "achieved_gbs": BYTES_PER_VOXIT_FP32 * value / 1e9,
+                       "peak_gbs_measured": hbm,
+                       "frac_of_measured": BYTES_PER_VOXIT_FP32 * value / 1e9 / hbm if hbm else None,
+                       "flop_per_byte": flops_per_voxit(N_SUB) / BYTES_PER_VOXIT_FP32, "ridge_flop_per_byte": ridge,
+                       "ceiling_frac_at_fp32_peak": (ridge / (flops_per_voxit(N_SUB) / BYTES_PER_VOXIT_FP32)
+                                                     if ridge else None)}
+        line["peaks"] = peaks
+        line["single_rve_128"] = single
+        fp64 = leg_fp64_plain()
+        line["fp64_plain"] = fp64
+        line["speedup_fp32_batched_vs_fp64_plain"] = value / fp64["grid128"]["value"]
+        line["speedup_fp32_batched_vs_fp64_plain16"] = value / fp64["plain16"]["value"]
+        line["adjoint_over_forward"] = leg_adjoint()
+        line["fft_comparison"] = leg_fft_comparison()
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(seconds=args.cpu_seconds)
     print(json.dumps(line))
 
 
@@ -630,14 +917,18 @@ def main_args(argv=None):
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="twinned128",
-                    choices=["twinned128", "ensemble", "precision256", "paper", "eta", "adjoint"],
-                    help="ensemble: the 16-RVE batched workload; precision256: FP32 vs FP64 on the 256^3 RVE "
-                         "over --steps increments (each prints its own JSON line)")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="default workload: the ensemble and e2e legs only (no side legs)")
+    ap.add_argument("--workload", default="ensemble",
+                    choices=["ensemble", "twinned128", "precision256", "paper", "eta", "adjoint"],
+                    help="ensemble (default): the headline line; twinned128: the 128^3 RVE alone; "
+                         "precision256: FP32 vs FP64 on the 256^3 RVE over --steps increments; paper / eta / adjoint: "
+                         "the paper-setting, regularisation and adjoint studies (each prints its own JSON line)")
     ap.add_argument("--twins", default="neigh", choices=["neigh", "incl", "none"],
                     help="paper workload: twin configuration")
     ap.add_argument("--paper-size", type=int, default=256, help="paper workload: grid size")
     ap.add_argument("--seed", type=int, default=0, help="paper workload: realization seed")
+    ap.add_argument("--fp64-steps", type=int, default=20, help="precision256: FP64 increments (<= --steps)")
     ap.add_argument("--profile-case", type=int, default=0, metavar="N",
                     help="profiling case: an N^3 twinned RVE (60 grains, p=0.5, seed 11), "
                          "--warmup increments, then --steps increments between "
@@ -648,14 +939,26 @@ def main_args(argv=None):
     return args
 
 
+def run_twinned128(args):
+    """The twinned 128^3 RVE alone in FP32 (the single-RVE line)."""
+    import torch
+
+    from paper_2402_09996_gb300 import build_lib
+
+    torch.cuda.set_device(0)
+    build_lib.build()
+    single = leg_single_128(args.warmup, args.steps)
+    print(json.dumps({"metric": METRIC, "workload": WORKLOAD_128, **single}))
+
+
 def main():
     args = main_args()
     if args.impl == "reference":
         run_reference(args)
     elif args.profile_case:
         run_profile_case(args)
-    elif args.workload == "ensemble":
-        run_ensemble(args)
+    elif args.workload == "twinned128":
+        run_twinned128(args)
     elif args.workload == "precision256":
         run_precision(args)
     elif args.workload == "paper":

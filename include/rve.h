@@ -83,7 +83,7 @@ typedef struct {
                          iteration until the residual kernel decides; the commit follows in the
                          same graph), so the host waits once per increment.  The graphs are
                          built on first use per buffer rotation (three per handle) and rebuilt
-                         after rve_set_mixed_load.  Ignored when timing is set. */
+                         after rve_set_mixed_load changes the load.  Ignored when timing is set. */
   int autotune;       /* nonzero (default): before the first increment, time the y and z FFT
                          passes for kx tile widths 1, 2, 4, 8, 16 on scratch buffers and keep the
                          fastest (results do not depend on the widths) */
@@ -328,6 +328,18 @@ rve_status rve_label_voronoi(int nx, int ny, int nz, int n_parent, const double*
 rve_status rve_label_voronoi_noalloc(int nx, int ny, int nz, int n_parent, const double* seeds,
                                      const uint8_t* twinned, const double* twin_normal,
                                      uint32_t* grain_id_out, void* stream);
+
+/* ALU throughput probe (the paper has no counterpart: measurement support).  The
+ * per-voxel update of rve_material_point is bound by the FP32 (or FP64) FMA pipe and the
+ * MUFU unit, so its roofline is taken against rates measured with this probe.
+ *   kind     0 FP32 FMA, 1 FP64 FMA, 2 FP32 MUFU ex2.approx;
+ *   blocks   CTAs of 256 threads; iters loop trips, each 128 operations per thread
+ *            (8 independent chains of 16);
+ *   sink     device buffer of at least 8 bytes (written only in a case that does not
+ *            occur, so the work is not optimised away);
+ *   ops_out  (host, may be NULL) operations of one launch: 2 per FMA, 1 per ex2.
+ * Enqueued on `stream` without synchronising; time it with events on that stream. */
+rve_status rve_alu_probe(int kind, int blocks, int iters, void* sink, void* stream, double* ops_out);
 
 #ifdef __cplusplus
 }

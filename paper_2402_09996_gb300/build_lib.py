@@ -21,7 +21,7 @@ BUILD = ROOT / "_build"
 LIB = PKG / "librve.so"
 SOURCES = ["xpass_f32_np10.cu", "xpass_f64_np10.cu", "xpass_f32_np0.cu", "xpass_f64_np0.cu", "xpass_f32_npr.cu",
            "xpass_f64_npr.cu", "xpass_f32_lin.cu", "xpass_f64_lin.cu",
-           "kernels_f32.cu", "kernels_f64.cu", "api.cu", "label.cu"]
+           "kernels_f32.cu", "kernels_f64.cu", "api.cu", "label.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

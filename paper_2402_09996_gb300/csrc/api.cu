@@ -528,9 +528,9 @@ rve_status alloc_fields(rve_s* h) {
     h->L = (int)std::max(fill, std::min(most, keep));
   }
   h->xgrid = (int)((h->NL + h->L - 1) / h->L);
-  // x sequences in shared memory: odd stride nx + 1 for the register transforms of
-  // power-of-two lines (conflict-free steps), nx for the Stockham passes
-  h->xs = (h->nx == 64 || h->nx == 128 || h->nx == 256) ? h->nx + 1 : h->nx;
+  // x sequences in shared memory: odd stride nx + 1 for the register transforms of the
+  // lengths with a two-step split (conflict-free steps), nx for the Stockham passes
+  h->xs = pencil_n1(h->nx) > 0 ? h->nx + 1 : h->nx;
   h->xsmem = (size_t)(h->nx + 6 * h->L * h->xs) * 2 * sizeof(T);  // FFT buffers; + tables: xsmem_total
   // y and z passes: tiles of HC kx values x 6 components (two buffers of padded lines);
   // default about 50 KB per CTA so that four CTAs share an SM (the autotuner may change it)
@@ -541,7 +541,7 @@ rve_status alloc_fields(rve_s* h) {
   if (h->opt.z_tile > 0) h->zHC = h->opt.z_tile;
   h->yHC = std::min(h->yHC, h->H);
   h->zHC = std::min(h->zHC, h->H);
-  // power-of-two lines run the register transforms at every width: clamp to their limit
+  // lines with a two-step split run the register transforms at every width: clamp to their limit
   if (pencil_max_hc(h->ny) > 0) h->yHC = std::min(h->yHC, pencil_max_hc(h->ny));
   if (pencil_max_hc(h->nz) > 0) h->zHC = std::min(h->zHC, pencil_max_hc(h->nz));
   h->ysmem = y_smem<T>(h, h->yHC);
@@ -632,8 +632,8 @@ XArgs<T> x_args(rve_s* h, const void* in, void* out, int it) {
   a.ep = (T*)h->ep; a.v = (T*)h->v; a.al = (T*)h->al; a.eps_n = (T*)h->eps_n; a.sig_n = (T*)h->sig_n;
   a.grain = h->grain;
   a.Rg = (const T*)h->Rg;
-  a.root_tab = (const T*)h->root_tab;
-  a.M = make_mat<T>(h);
+  a.k.root_tab = (const T*)h->root_tab;
+  a.k.M = make_mat<T>(h);
   if (h->lin_mode) {
     a.lin_B = (const T*)h->lin_B;
     a.lin_g = (const T*)h->lin_g;
@@ -642,25 +642,26 @@ XArgs<T> x_args(rve_s* h, const void* in, void* out, int it) {
   // mixed load
   double M0[36];
   c0_mandel(h->lam0, h->mu0, M0);
-  std::memset(&a.ld, 0, sizeof(a.ld));
+  LoadDev& ld = a.k.ld;
+  std::memset(&ld, 0, sizeof(ld));
   int fi[6], nf = 0;
   for (int c = 0; c < 6; ++c) {
-    a.ld.free_mask[c] = h->ctrl[c] ? 0 : 1;
-    a.ld.Sigma_m[c] = h->lin_mode ? 0.0 : h->Sigma[c] * kMw[c];
+    ld.free_mask[c] = h->ctrl[c] ? 0 : 1;
+    ld.Sigma_m[c] = h->lin_mode ? 0.0 : h->Sigma[c] * kMw[c];
     if (!h->ctrl[c]) fi[nf++] = c;
   }
-  a.ld.any_free = nf > 0;
-  a.ld.s_ref = h->lin_mode ? h->lin_sref : 0.0;
+  ld.any_free = nf > 0;
+  ld.s_ref = h->lin_mode ? h->lin_sref : 0.0;
   if (nf > 0) {
     std::vector<double> Mff(nf * nf);
     for (int i = 0; i < nf; ++i)
       for (int j = 0; j < nf; ++j) Mff[i * nf + j] = M0[fi[i] * 6 + fi[j]];
     invert(Mff.data(), nf);
     for (int i = 0; i < nf; ++i)
-      for (int j = 0; j < nf; ++j) a.ld.Minv[fi[i] * 6 + fi[j]] = Mff[i * nf + j];
+      for (int j = 0; j < nf; ++j) ld.Minv[fi[i] * 6 + fi[j]] = Mff[i * nf + j];
   }
-  a.dt = (T)h->dt;
-  a.nsub = h->opt.n_sub > 0 ? h->opt.n_sub : default_nsub(h->dt);
+  a.k.dt = (T)h->dt;
+  a.k.nsub = h->opt.n_sub > 0 ? h->opt.n_sub : default_nsub(h->dt);
   a.partial = h->partial;
   a.counter = h->counter;
   a.st = h->st;
@@ -1004,7 +1005,7 @@ rve_status tune_tiles(rve_s* h) {
 // Starts increment n -> n+1: macroscopic step and initial guess (a1), then the first
 // batch of iterations (or the whole increment as one graph launch).
 template <typename T>
-rve_status inc_begin(rve_s* h) {
+rve_status inc_prepare(rve_s* h) {
   cudaStream_t s = h->stream;
   if (h->opt.autotune && !h->tuned) {
     rve_status st = tune_tiles<T>(h);
@@ -1020,6 +1021,14 @@ rve_status inc_begin(rve_s* h) {
   tstart(h, kSlotShift, RVE_K_SHIFT);
   RVE_CUDA(h, launch_shift<T>((C2<T>*)h->spec[r.s0], (C2<T>*)h->backup, h->NL, h->H, h->inc_dE0, false, s));
   tstop(h, kSlotShift);
+  return RVE_OK;
+}
+
+template <typename T>
+rve_status inc_begin(rve_s* h) {
+  cudaStream_t s = h->stream;
+  rve_status pst = inc_prepare<T>(h);
+  if (pst) return pst;
   if (use_graphs(h)) {
     if (!h->gexec[h->sb]) {
       rve_status st = build_graph<T>(h);
@@ -1554,6 +1563,10 @@ rve_status rve_set_mixed_load(rve_t h, const double Edot[6], const uint8_t ctrl[
     nc += ctrl[c] ? 1 : 0;
   }
   if (nc == 0) return fail(h, RVE_ERR_INVALID_ARG, "at least one component must be strain-controlled");
+  bool same = dt == h->dt;
+  for (int c = 0; c < 6; ++c)
+    same = same && Edot[c] == h->Edot[c] && (ctrl[c] ? 1 : 0) == h->ctrl[c] && Sigma[c] == h->Sigma[c];
+  if (same) return RVE_OK;  // unchanged load: the increment graphs stay valid
   for (int c = 0; c < 6; ++c) {
     h->Edot[c] = Edot[c];
     h->ctrl[c] = ctrl[c] ? 1 : 0;

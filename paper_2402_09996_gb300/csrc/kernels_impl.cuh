@@ -32,6 +32,20 @@ cudaError_t launch_xpass_np(const XArgs<T>& a, bool commit, int grid, size_t sme
 }
 
 template <typename T, int NP>
+cudaError_t launch_xpass_group_np(const XGroup<T>& g, bool commit, int grid, size_t smem, cudaStream_t s) {
+  if (commit) {
+    cudaError_t e = set_smem<T>((const void*)k_xpass_group<T, true, NP>, smem);
+    if (e != cudaSuccess) return e;
+    k_xpass_group<T, true, NP><<<grid, kXThreads, smem, s>>>(g);
+  } else {
+    cudaError_t e = set_smem<T>((const void*)k_xpass_group<T, false, NP>, smem);
+    if (e != cudaSuccess) return e;
+    k_xpass_group<T, false, NP><<<grid, kXThreads, smem, s>>>(g);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T, int NP>
 cudaError_t launch_material_point_np(const MatDev<T>& M, long long nvox, const T* R, const T* eps_n, const T* eps,
                                      T* state, T* sigma, T dt, int nsub, const T* root_tab, cudaStream_t s) {
   if (nvox <= 0) return cudaSuccess;
@@ -82,6 +96,7 @@ cudaError_t launch_adj_tangent_np(const MatDev<T>& M, long long nvox, const T* R
 
 #define RVE_INSTANTIATE_X(T, NP)                                                                                \
   template cudaError_t launch_xpass_np<T, NP>(const XArgs<T>&, bool, int, size_t, cudaStream_t);              \
+  template cudaError_t launch_xpass_group_np<T, NP>(const XGroup<T>&, bool, int, size_t, cudaStream_t);       \
   template cudaError_t launch_material_point_np<T, NP>(const MatDev<T>&, long long, const T*, const T*, const T*, \
                                                        T*, T*, T, int, const T*, cudaStream_t);              \
   template cudaError_t launch_material_point_vjp_np<T, NP>(const MatDev<T>&, long long, const T*, const T*,      \
@@ -92,10 +107,7 @@ cudaError_t launch_adj_tangent_np(const MatDev<T>& M, long long nvox, const T* R
                                                     const T*, cudaStream_t);
 
 // Threads of a pencil-pass CTA: N1 per line of the chunk, rounded up to whole warps.
-inline int pencil_threads(int n, int HC) {
-  const int n1 = n == 256 ? 16 : 8;
-  return (n1 * 6 * HC + 31) / 32 * 32;
-}
+inline int pencil_threads(int n, int HC) { return (pencil_n1(n) * 6 * HC + 31) / 32 * 32; }
 // The pencil kernels serve the component-interleaved passes whose length has a split and
 // whose chunk fits one CTA.
 inline bool pencil_ok(int n, int HC) { return HC <= pencil_max_hc(n); }
@@ -110,13 +122,22 @@ static cudaError_t launch_line_pencil(const LineArgs<T>& a, dim3 grid, cudaStrea
   return cudaGetLastError();
 }
 
+template <typename T, int N>
+static cudaError_t launch_line_pencil_n(const LineArgs<T>& a, int sign, dim3 grid, cudaStream_t s) {
+  constexpr int N1 = PencilSplit<N>::N1, N2 = PencilSplit<N>::N2;
+  return sign < 0 ? launch_line_pencil<T, -1, N1, N2>(a, grid, s) : launch_line_pencil<T, 1, N1, N2>(a, grid, s);
+}
+
 template <typename T>
 cudaError_t launch_line(const LineArgs<T>& a, int sign, dim3 grid, size_t smem, cudaStream_t s) {
   if (a.NC == 6 && a.hstride == 6 && pencil_ok(a.d.n, a.HC)) {
-    if (a.d.n == 64) return sign < 0 ? launch_line_pencil<T, -1, 8, 8>(a, grid, s) : launch_line_pencil<T, 1, 8, 8>(a, grid, s);
-    if (a.d.n == 128)
-      return sign < 0 ? launch_line_pencil<T, -1, 8, 16>(a, grid, s) : launch_line_pencil<T, 1, 8, 16>(a, grid, s);
-    return sign < 0 ? launch_line_pencil<T, -1, 16, 16>(a, grid, s) : launch_line_pencil<T, 1, 16, 16>(a, grid, s);
+    switch (a.d.n) {
+      case 64: return launch_line_pencil_n<T, 64>(a, sign, grid, s);
+      case 96: return launch_line_pencil_n<T, 96>(a, sign, grid, s);
+      case 128: return launch_line_pencil_n<T, 128>(a, sign, grid, s);
+      case 160: return launch_line_pencil_n<T, 160>(a, sign, grid, s);
+      default: return launch_line_pencil_n<T, 256>(a, sign, grid, s);
+    }
   }
   if (sign < 0) {
     cudaError_t e = set_smem<T>((const void*)k_line<T, -1>, smem);
@@ -143,14 +164,59 @@ static cudaError_t launch_zgreen_pencil(const ZArgs<T>& a, dim3 grid, cudaStream
 template <typename T>
 cudaError_t launch_zgreen(const ZArgs<T>& a, dim3 grid, size_t smem, cudaStream_t s) {
   if (pencil_ok(a.nz, a.HC)) {
-    if (a.nz == 64) return launch_zgreen_pencil<T, 8, 8>(a, grid, s);
-    if (a.nz == 128) return launch_zgreen_pencil<T, 8, 16>(a, grid, s);
-    return launch_zgreen_pencil<T, 16, 16>(a, grid, s);
+    switch (a.nz) {
+      case 64: return launch_zgreen_pencil<T, PencilSplit<64>::N1, PencilSplit<64>::N2>(a, grid, s);
+      case 96: return launch_zgreen_pencil<T, PencilSplit<96>::N1, PencilSplit<96>::N2>(a, grid, s);
+      case 128: return launch_zgreen_pencil<T, PencilSplit<128>::N1, PencilSplit<128>::N2>(a, grid, s);
+      case 160: return launch_zgreen_pencil<T, PencilSplit<160>::N1, PencilSplit<160>::N2>(a, grid, s);
+      default: return launch_zgreen_pencil<T, PencilSplit<256>::N1, PencilSplit<256>::N2>(a, grid, s);
+    }
   }
   cudaError_t e = set_smem<T>((const void*)k_zgreen<T, 0, 0>, smem);
   if (e != cudaSuccess) return e;
   k_zgreen<T, 0, 0><<<grid, kZThreads, smem, s>>>(a);
   return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_line_group(const LineGroup<T>& g, int sign, int grid, size_t smem, cudaStream_t s) {
+  if (sign < 0) {
+    cudaError_t e = set_smem<T>((const void*)k_line_group<T, -1>, smem);
+    if (e != cudaSuccess) return e;
+    k_line_group<T, -1><<<grid, kPencilThreads, smem, s>>>(g);
+  } else {
+    cudaError_t e = set_smem<T>((const void*)k_line_group<T, +1>, smem);
+    if (e != cudaSuccess) return e;
+    k_line_group<T, +1><<<grid, kPencilThreads, smem, s>>>(g);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_zgreen_group(const ZGroup<T>& g, int grid, size_t smem, cudaStream_t s) {
+  cudaError_t e = set_smem<T>((const void*)k_zgreen_group<T>, smem);
+  if (e != cudaSuccess) return e;
+  k_zgreen_group<T><<<grid, kPencilThreads, smem, s>>>(g);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_group_guard(const GuardGroup& g, cudaGraphConditionalHandle cond, cudaStream_t s) {
+  k_group_guard<T><<<1, 32, 0, s>>>(g, cond);
+  return cudaGetLastError();
+}
+
+// Dynamic shared memory of a member's y / z pass CTA in the grouped kernels (the larger of
+// the register-transform and Stockham layouts it may take).
+template <typename T>
+size_t line_group_smem(int n, int HC) {
+  const size_t pencil = ((size_t)n + (size_t)6 * HC * (n + 1)) * sizeof(C2<T>);
+  const size_t stock = ((size_t)n + (size_t)2 * 6 * HC * (n + 1)) * sizeof(C2<T>);
+  return HC <= pencil_max_hc(n) ? pencil : stock;
+}
+template <typename T>
+size_t zgreen_group_smem(int nz, int HC) {
+  return line_group_smem<T>(nz, HC) + (size_t)HC * nz * sizeof(double);
 }
 
 template <typename T>
@@ -410,6 +476,11 @@ cudaError_t launch_adj(int which, long long n, cudaStream_t s, const void* p0, c
   template cudaError_t launch_adj<T>(int, long long, cudaStream_t, const void*, const void*, const void*, void*,   \
                                      void*, const double*);                                                        \
   template cudaError_t launch_adj_sums<T>(const T*, const T*, const T*, const T*, const uint32_t*, const int*, int, \
-                                          long long, double*, double*, cudaStream_t);
+                                          long long, double*, double*, cudaStream_t);                              \
+  template cudaError_t launch_line_group<T>(const LineGroup<T>&, int, int, size_t, cudaStream_t);                  \
+  template cudaError_t launch_zgreen_group<T>(const ZGroup<T>&, int, size_t, cudaStream_t);                        \
+  template cudaError_t launch_group_guard<T>(const GuardGroup&, cudaGraphConditionalHandle, cudaStream_t);         \
+  template size_t line_group_smem<T>(int, int);                                                                    \
+  template size_t zgreen_group_smem<T>(int, int);
 
 }  // namespace rve

@@ -11,6 +11,10 @@ template <typename T> struct XArgs;
 template <typename T> struct LineArgs;
 template <typename T> struct ZArgs;
 template <typename T> struct XFftArgs;
+template <typename T> struct XGroup;
+template <typename T> struct LineGroup;
+template <typename T> struct ZGroup;
+struct GuardGroup;
 
 // Rate-solve variants of the constitutive kernels (see constitutive.cuh): NP = 10 for
 // eta > 0 and n = nt = 10, NP = -1 for eta > 0 and other exponents >= 1, NP = 0 (generic
@@ -19,10 +23,6 @@ inline int rate_variant(double eta, int n_int, int nt_int) {
   if (!(eta > 0.0)) return 0;
   return (n_int == 10 && nt_int == 10) ? 10 : -1;
 }
-
-// Largest kx chunk (HC) the two-step register transforms of the y and z passes take for a
-// line length n, 0 where n has no such split (those lengths run the Stockham kernels).
-inline int pencil_max_hc(int n) { return (n == 64 || n == 128) ? 8 : (n == 256 ? 4 : 0); }
 
 // Per-variant entry points (each instantiated in its own translation unit).
 template <typename T, int NP>
@@ -87,6 +87,26 @@ cudaError_t launch_material_point(const MatDev<T>& M, int np, long long nvox, co
 
 template <typename T>
 cudaError_t launch_line(const LineArgs<T>& a, int sign, dim3 grid, size_t smem, cudaStream_t s);
+// grouped passes (solver_kernels.cuh, k_*_group): one launch over several RVEs' grids; the
+// grouped x pass per rate variant as launch_xpass
+template <typename T, int NP>
+cudaError_t launch_xpass_group_np(const XGroup<T>& g, bool commit, int grid, size_t smem, cudaStream_t s);
+template <typename T>
+cudaError_t launch_xpass_group(const XGroup<T>& g, int np, bool commit, int grid, size_t smem, cudaStream_t s) {
+  if (np == 10) return launch_xpass_group_np<T, 10>(g, commit, grid, smem, s);
+  if (np < 0) return launch_xpass_group_np<T, -1>(g, commit, grid, smem, s);
+  return launch_xpass_group_np<T, 0>(g, commit, grid, smem, s);
+}
+template <typename T>
+cudaError_t launch_line_group(const LineGroup<T>& g, int sign, int grid, size_t smem, cudaStream_t s);
+template <typename T>
+cudaError_t launch_zgreen_group(const ZGroup<T>& g, int grid, size_t smem, cudaStream_t s);
+template <typename T>
+cudaError_t launch_group_guard(const GuardGroup& g, cudaGraphConditionalHandle cond, cudaStream_t s);
+template <typename T>
+size_t line_group_smem(int n, int HC);
+template <typename T>
+size_t zgreen_group_smem(int nz, int HC);
 template <typename T>
 cudaError_t launch_zgreen(const ZArgs<T>& a, dim3 grid, size_t smem, cudaStream_t s);
 template <typename T>

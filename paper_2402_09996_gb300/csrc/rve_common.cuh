@@ -29,6 +29,17 @@ __device__ __forceinline__ C2<T> cmulc(C2<T> a, C2<T> b) {
 template <typename T>
 __device__ __forceinline__ C2<T> cscale(C2<T> a, T s) { return mk<T>(a.x * s, a.y * s); }
 
+// Threads per line in the first step of the two-step register transform of a line length
+// n (n = N1 N2: 64 = 8 * 8, 96 = 8 * 12, 128 = 8 * 16, 160 = 10 * 16, 256 = 16 * 16; the
+// PencilSplit table of fft_reg.cuh), 0 where n has no such split (those lengths run the
+// Stockham kernels).
+__host__ __device__ constexpr int pencil_n1(int n) {
+  return (n == 64 || n == 96 || n == 128) ? 8 : (n == 160 ? 10 : (n == 256 ? 16 : 0));
+}
+// Largest kx chunk (HC) the two-step transforms of the y and z passes take: a CTA holds at
+// most 384 threads, N1 for each of the chunk's 6 HC lines.
+__host__ __device__ constexpr int pencil_max_hc(int n) { return pencil_n1(n) > 0 ? 384 / (6 * pencil_n1(n)) : 0; }
+
 // One FFT length factored into radix stages (radices 2, 3, 4, 5).
 struct FftDim {
   int n;

@@ -48,21 +48,28 @@ __device__ __forceinline__ void block_sum(double* v, double (*red)[kNumRed]) {
   __syncthreads();
 }
 
-// Linear CTA index and CTA count of a 1-D or 2-D grid.
-__device__ __forceinline__ unsigned int block_linear() { return blockIdx.x + gridDim.x * blockIdx.y; }
-__device__ __forceinline__ unsigned int block_count() { return gridDim.x * gridDim.y; }
+// A CTA's place in the (2-D) grid of one RVE's pass: coordinates, linear index and the
+// pass's CTA count.  A stand-alone launch takes them from blockIdx / gridDim; a grouped
+// launch over several RVEs (k_*_group) from the CTA's slice of the combined grid, so every
+// RVE's CTAs compute and reduce exactly as in their own launch.
+struct Cta {
+  unsigned bx, by, lin, count;
+};
+__device__ __forceinline__ Cta own_grid() {
+  return Cta{blockIdx.x, blockIdx.y, blockIdx.x + gridDim.x * blockIdx.y, gridDim.x * gridDim.y};
+}
 
 // Stores this CTA's sums and returns true (in all threads) in the CTA that finished last.
 template <int NV>
 __device__ __forceinline__ bool publish_partial(double* v, double* partial, unsigned int* counter,
-                                                double (*red)[kNumRed], int* s_last) {
+                                                double (*red)[kNumRed], int* s_last, const Cta& cta) {
   block_sum<NV>(v, red);
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int i = 0; i < NV; ++i) partial[(size_t)block_linear() * kNumRed + i] = v[i];
+    for (int i = 0; i < NV; ++i) partial[(size_t)cta.lin * kNumRed + i] = v[i];
     __threadfence();
     const unsigned int prev = atomicAdd(counter, 1u);
-    *s_last = (prev == block_count() - 1) ? 1 : 0;
+    *s_last = (prev == cta.count - 1) ? 1 : 0;
   }
   __syncthreads();
   return *s_last != 0;
@@ -74,7 +81,7 @@ __device__ __forceinline__ bool publish_partial(double* v, double* partial, unsi
 // publish_partial's arithmetic.
 template <typename T, int NV>
 __device__ __forceinline__ bool publish_partial_t(const T* s, double* partial, unsigned int* counter,
-                                                  double (*red)[kNumRed], int* s_last) {
+                                                  double (*red)[kNumRed], int* s_last, const Cta& cta) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   T v[NV];
 #pragma unroll
@@ -94,10 +101,10 @@ __device__ __forceinline__ bool publish_partial_t(const T* s, double* partial, u
     warp_sum<NV>(w);
     if (lane == 0) {
 #pragma unroll
-      for (int i = 0; i < NV; ++i) partial[(size_t)block_linear() * kNumRed + i] = w[i];
+      for (int i = 0; i < NV; ++i) partial[(size_t)cta.lin * kNumRed + i] = w[i];
       __threadfence();
       const unsigned int prev = atomicAdd(counter, 1u);
-      *s_last = (prev == block_count() - 1) ? 1 : 0;
+      *s_last = (prev == cta.count - 1) ? 1 : 0;
     }
   }
   __syncthreads();
@@ -106,11 +113,12 @@ __device__ __forceinline__ bool publish_partial_t(const T* s, double* partial, u
 
 // Deterministic grand total of all CTAs' partials (fixed assignment and tree order).
 template <int NV>
-__device__ __forceinline__ void total_partials(const double* partial, double* v, double (*red)[kNumRed]) {
+__device__ __forceinline__ void total_partials(const double* partial, double* v, double (*red)[kNumRed],
+                                               unsigned int count) {
   __threadfence();
 #pragma unroll
   for (int i = 0; i < NV; ++i) v[i] = 0.0;
-  for (int b = threadIdx.x; b < (int)block_count(); b += blockDim.x)
+  for (int b = threadIdx.x; b < (int)count; b += blockDim.x)
 #pragma unroll
     for (int i = 0; i < NV; ++i) v[i] += __ldcg(&partial[(size_t)b * kNumRed + i]);
   block_sum<NV>(v, red);
@@ -119,10 +127,22 @@ __device__ __forceinline__ void total_partials(const double* partial, double* v,
 __device__ __forceinline__ double mandel_w(int a) { return a < 3 ? 1.0 : 1.41421356237309504880; }
 
 // ---------------------------------------------------------------- x pass -----------
+// The x pass's arguments that do not depend on the grid: material, load, increment and
+// the rate-root tables.  RVEs stepped as one group share them (identical material and
+// load), so a grouped launch reads them at fixed parameter offsets.
+template <typename T>
+struct XCommon {
+  const T* root_tab;  // rate-root tables: kRootTabs values
+  MatDev<T> M;
+  LoadDev ld;
+  T dt;
+  int nsub;
+};
+
 template <typename T>
 struct XArgs {
   int nx, ny, nz, H, L;
-  int xs;  // line stride of the shared-memory x sequences: nx + 1 for power-of-two nx, else nx
+  int xs;  // line stride of the shared-memory x sequences: nx + 1 for the register-split lengths, else nx
   long long nvox;
   FftDim dx;
   const C2<T>* tw;
@@ -135,12 +155,8 @@ struct XArgs {
   T* sig_n;
   const uint32_t* grain;
   const T* Rg;
-  const T* root_tab;  // rate-root tables: kRootTabs values
-  MatDev<T> M;
-  LoadDev ld;
+  XCommon<T> k;
   const int* done;  // iteration launches return at once when *done != 0 (NULL: always run)
-  T dt;
-  int nsub;
   double* partial;
   unsigned int* counter;
   IterStatus* st;
@@ -156,7 +172,7 @@ struct XArgs {
 };
 
 // The x transforms of a CTA's nseq packed lines (stride xs >= N + 1 in shared memory) for
-// a power-of-two length N = N1 N2: step 1 from a into b, step 2 back into a in natural
+// a length N = N1 N2 with a register split: step 1 from a into b, step 2 back into a in natural
 // order.  Consecutive threads take consecutive lines, so with an odd stride both steps
 // are free of bank conflicts.  Contains barriers: every thread of the CTA calls it.
 template <typename T, int SIGN, int N1, int N2>
@@ -180,24 +196,26 @@ __device__ __forceinline__ void xlines_pencil(C2<T>* a, C2<T>* b, int nseq, int 
   __syncthreads();
 }
 
-// The CTA's x transforms: register two-step transforms for nx = 64, 128, 256 (result in
-// a), shared-memory Stockham passes otherwise (result in a or b, returned).
+template <typename T, int SIGN, int N>
+__device__ __forceinline__ void xlines_split(C2<T>* a, C2<T>* b, int nseq, int xs, const C2<T>* tw, int tid,
+                                             int nthr) {
+  xlines_pencil<T, SIGN, PencilSplit<N>::N1, PencilSplit<N>::N2>(a, b, nseq, xs, tw, tid, nthr);
+}
+
+// The CTA's x transforms: register two-step transforms for the lengths of the PencilSplit
+// table (64, 96, 128, 160, 256; result in a), shared-memory Stockham passes otherwise
+// (result in a or b, returned).
 template <typename T, int SIGN>
 __device__ __forceinline__ C2<T>* xlines_fft(C2<T>* a, C2<T>* b, const FftDim& d, int nseq, int xs, const C2<T>* tw,
                                              int tid, int nthr) {
-  if (d.n == 128) {
-    xlines_pencil<T, SIGN, 8, 16>(a, b, nseq, xs, tw, tid, nthr);
-    return a;
+  switch (d.n) {
+    case 64: xlines_split<T, SIGN, 64>(a, b, nseq, xs, tw, tid, nthr); return a;
+    case 96: xlines_split<T, SIGN, 96>(a, b, nseq, xs, tw, tid, nthr); return a;
+    case 128: xlines_split<T, SIGN, 128>(a, b, nseq, xs, tw, tid, nthr); return a;
+    case 160: xlines_split<T, SIGN, 160>(a, b, nseq, xs, tw, tid, nthr); return a;
+    case 256: xlines_split<T, SIGN, 256>(a, b, nseq, xs, tw, tid, nthr); return a;
+    default: return smem_fft<T, SIGN>(a, b, d, nseq, xs, tw, tid, nthr);
   }
-  if (d.n == 64) {
-    xlines_pencil<T, SIGN, 8, 8>(a, b, nseq, xs, tw, tid, nthr);
-    return a;
-  }
-  if (d.n == 256) {
-    xlines_pencil<T, SIGN, 16, 16>(a, b, nseq, xs, tw, tid, nthr);
-    return a;
-  }
-  return smem_fft<T, SIGN>(a, b, d, nseq, xs, tw, tid, nthr);
 }
 
 constexpr int kXThreads = 128;
@@ -207,8 +225,10 @@ constexpr int kXThreads = 128;
 template <typename T> struct XMinBlocks { static constexpr int value = 1; };
 template <> struct XMinBlocks<float> { static constexpr int value = 3; };
 
+// One CTA of the x pass (see the file header) at grid place `cta`; k holds a.k or the
+// group's common arguments.
 template <typename T, bool COMMIT, int NP>
-__global__ void __launch_bounds__(kXThreads, XMinBlocks<T>::value) k_xpass(const XArgs<T> a) {
+__device__ __forceinline__ void xpass_cta(const XArgs<T>& a, const XCommon<T>& k, const Cta& cta) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[32][kNumRed];
   __shared__ int s_last;
@@ -219,7 +239,7 @@ __global__ void __launch_bounds__(kXThreads, XMinBlocks<T>::value) k_xpass(const
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int nx = a.nx, H = a.H, half = nx / 2, xs = a.xs;
   const size_t NL = (size_t)a.ny * a.nz;
-  const int line0 = blockIdx.x * a.L;
+  const int line0 = (int)cta.bx * a.L;
   const int nl = min(a.L, (int)(NL - line0));
   if (a.done && *a.done) return;  // increment already decided: speculative launch
   const size_t nvox = (size_t)a.nvox;
@@ -233,7 +253,7 @@ __global__ void __launch_bounds__(kXThreads, XMinBlocks<T>::value) k_xpass(const
 
   for (int i = tid; i < nx; i += nthr) tw[i] = a.tw[i];
   if (NP != 0 && NP != kLinearLaw)
-    for (int i = tid; i < kRootTabs; i += nthr) tab[i] = a.root_tab[i];
+    for (int i = tid; i < kRootTabs; i += nthr) tab[i] = k.root_tab[i];
   // pack component pairs (2p, 2p+1) of each line as one complex Hermitian-extended
   // sequence Z = A + iB, so one complex inverse FFT yields both real lines
   // (spectra are component-interleaved: entry (line, kx, c) at (line * H + kx) * 6 + c,
@@ -304,7 +324,7 @@ __global__ void __launch_bounds__(kXThreads, XMinBlocks<T>::value) k_xpass(const
       const uint32_t g = a.grain[vox];
   #pragma unroll
       for (int i = 0; i < 9; ++i) R[i] = a.Rg[(size_t)g * 9 + i];
-      mc_voxel<T, NP>(a.M, R, epsn, eps, y, a.dt, a.nsub, sig, tab);
+      mc_voxel<T, NP>(k.M, R, epsn, eps, y, k.dt, k.nsub, sig, tab);
   #pragma unroll
       for (int c = 0; c < 6; ++c) sacc[c] += sig[c];
       if (COMMIT) {
@@ -329,8 +349,8 @@ __global__ void __launch_bounds__(kXThreads, XMinBlocks<T>::value) k_xpass(const
       }
     }
     {
-      const T tr = a.M.lam0 * (eps[0] + eps[1] + eps[2]);
-      const T m2 = T(2) * a.M.mu0;
+      const T tr = k.M.lam0 * (eps[0] + eps[1] + eps[2]);
+      const T m2 = T(2) * k.M.mu0;
       T tau[6];
 #pragma unroll
       for (int c = 0; c < 6; ++c) tau[c] = sig[c] - m2 * eps[c] - (c < 3 ? tr : T(0));
@@ -364,11 +384,11 @@ __global__ void __launch_bounds__(kXThreads, XMinBlocks<T>::value) k_xpass(const
   // commit and the linear-law mode all slots in FP64
   constexpr bool kSix = !COMMIT && NP != kLinearLaw;
   bool last;
-  if constexpr (kSix) last = publish_partial_t<T, 6>(sacc, a.partial, a.counter, red, &s_last);
-  else last = publish_partial<kNumRed>(acc, a.partial, a.counter, red, &s_last);
+  if constexpr (kSix) last = publish_partial_t<T, 6>(sacc, a.partial, a.counter, red, &s_last, cta);
+  else last = publish_partial<kNumRed>(acc, a.partial, a.counter, red, &s_last, cta);
   if (last) {
-    if constexpr (kSix) total_partials<6>(a.partial, acc, red);
-    else total_partials<kNumRed>(a.partial, acc, red);
+    if constexpr (kSix) total_partials<6>(a.partial, acc, red, cta.count);
+    else total_partials<kNumRed>(a.partial, acc, red, cta.count);
     if (tid == 0) {
       IterStatus* st = a.st;
       const double inv = 1.0 / (double)a.nvox;
@@ -386,7 +406,7 @@ __global__ void __launch_bounds__(kXThreads, XMinBlocks<T>::value) k_xpass(const
         bad |= !isfinite(acc[6]) | !isfinite(acc[7]) | !isfinite(acc[8]);
       } else {
         // mixed-load update of the free components (Mandel form)
-        const LoadDev& ld = a.ld;
+        const LoadDev& ld = k.ld;
         double miss[6], nm = 0.0, ns = 0.0;
         for (int c = 0; c < 6; ++c) {
           const double sm = S[c] * mandel_w(c);
@@ -413,12 +433,17 @@ __global__ void __launch_bounds__(kXThreads, XMinBlocks<T>::value) k_xpass(const
   }
 }
 
+template <typename T, bool COMMIT, int NP>
+__global__ void __launch_bounds__(kXThreads, XMinBlocks<T>::value) k_xpass(const XArgs<T> a) {
+  xpass_cta<T, COMMIT, NP>(a, a.k, own_grid());
+}
+
 // ---------------------------------------------------------------- line FFT pass -----
 // Transforms, in place, lines of length d.n along an axis with element stride `stride`
 // (complex units), for NC components at once.  Element (line j, kx offset hh, component
-// c) of CTA (blockIdx.x, o = blockIdx.y) sits at
+// c) of the CTA at grid place (bx, o = by) sits at
 //   (o / n_o2) * A + (o % n_o2) * B + (h0 + hh) * hstride + c + j * stride,
-// h0 = blockIdx.x * HC.  The solver's spectra are component-interleaved (NC = 6,
+// h0 = bx * HC.  The solver's spectra are component-interleaved (NC = 6,
 // hstride = 6: each (j, kx chunk) row is HC * 6 contiguous values); the stand-alone FFT
 // entry points use component-major spectra (NC = 1, hstride = 1).
 template <typename T>
@@ -478,7 +503,7 @@ __device__ __forceinline__ void tile_move(C2<T>* s, int ps, C2<T>* g, size_t gst
 constexpr int kLineThreads = 256;
 
 template <typename T, int SIGN>
-__global__ void __launch_bounds__(kLineThreads) k_line(const LineArgs<T> a) {
+__device__ __forceinline__ void line_cta(const LineArgs<T>& a, const Cta& cta) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2<T>* tw = reinterpret_cast<C2<T>*>(smem_raw);
   const int n = a.d.n;
@@ -488,9 +513,9 @@ __global__ void __launch_bounds__(kLineThreads) k_line(const LineArgs<T> a) {
   C2<T>* b1 = b0 + (size_t)NC * a.HC * ps;
   const int tid = threadIdx.x, nthr = blockDim.x;
   if (a.done && *a.done) return;
-  const int h0 = blockIdx.x * a.HC;
+  const int h0 = (int)cta.bx * a.HC;
   const int hc = min(a.HC, a.H - h0);
-  const int o = blockIdx.y;
+  const int o = (int)cta.by;
   const size_t base = (size_t)(o / a.n_o2) * a.A + (size_t)(o % a.n_o2) * a.B + (size_t)h0 * a.hstride;
   const int row = hc * NC;  // values per line position, contiguous when hstride == NC
   for (int i = tid; i < n; i += nthr) tw[i] = a.tw[i];
@@ -516,7 +541,12 @@ __global__ void __launch_bounds__(kLineThreads) k_line(const LineArgs<T> a) {
   }
 }
 
-// The y pass for a power-of-two line length N = N1 N2 (fft_reg.cuh), on the solver's
+template <typename T, int SIGN>
+__global__ void __launch_bounds__(kLineThreads) k_line(const LineArgs<T> a) {
+  line_cta<T, SIGN>(a, own_grid());
+}
+
+// The y pass for a line length N = N1 N2 with a register split (fft_reg.cuh), on the solver's
 // component-interleaved spectra (NC = hstride = 6).  CTA (kx chunk, outer index) as in
 // k_line; its S = 6 hc lines s sit contiguously in every row.  Thread t = n1 SP + s
 // (SP = 6 HC) loads column n1 of line s straight from global memory (rows n1 + N1 n2),
@@ -525,7 +555,7 @@ __global__ void __launch_bounds__(kLineThreads) k_line(const LineArgs<T> a) {
 constexpr int kPencilThreads = 384;  // at most N1 * 6 * HC threads per CTA
 
 template <typename T, int SIGN, int N1, int N2>
-__global__ void __launch_bounds__(kPencilThreads) k_line_pencil(const LineArgs<T> a) {
+__device__ __forceinline__ void line_pencil_cta(const LineArgs<T>& a, const Cta& cta) {
   constexpr int N = N1 * N2;
   constexpr int ps = N + 1;  // padded line stride in shared memory
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -534,9 +564,9 @@ __global__ void __launch_bounds__(kPencilThreads) k_line_pencil(const LineArgs<T
   if (a.done && *a.done) return;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int SP = 6 * a.HC;
-  const int h0 = blockIdx.x * a.HC;
+  const int h0 = (int)cta.bx * a.HC;
   const int S = 6 * min(a.HC, a.H - h0);
-  const int o = blockIdx.y;
+  const int o = (int)cta.by;
   C2<T>* g = a.spec + (size_t)(o / a.n_o2) * a.A + (size_t)(o % a.n_o2) * a.B + (size_t)h0 * 6;
   const size_t gs = (size_t)a.stride;
   const int s = tid % SP, n1 = tid / SP;
@@ -559,6 +589,11 @@ __global__ void __launch_bounds__(kPencilThreads) k_line_pencil(const LineArgs<T
       for (int q = 0; q < N1; ++q) g[(size_t)(k2 + N2 * q) * gs + s2] = w[q];
     }
   }
+}
+
+template <typename T, int SIGN, int N1, int N2>
+__global__ void __launch_bounds__(kPencilThreads) k_line_pencil(const LineArgs<T> a) {
+  line_pencil_cta<T, SIGN, N1, N2>(a, own_grid());
 }
 
 // ---------------------------------------------------------------- z pass + Green ----
@@ -593,11 +628,9 @@ constexpr int kZThreads = 256;
 // register transforms of fft_reg.cuh (one buffer, line s = 6 hh + c at s ps, as in the
 // global rows).
 template <typename T, int N1, int N2>
-__global__ void __launch_bounds__(N1 > 0 ? kPencilThreads : kZThreads) k_zgreen(const ZArgs<T> a) {
+__device__ __forceinline__ void zgreen_cta(const ZArgs<T>& a, const Cta& cta, double (*red)[kNumRed], int& s_last) {
   constexpr bool kPencil = N1 > 0;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double red[32][kNumRed];
-  __shared__ int s_last;
   const int nz = a.nz;
   C2<T>* tw = reinterpret_cast<C2<T>*>(smem_raw);
   const int ps = nz + 1;  // padded sequence stride
@@ -606,8 +639,8 @@ __global__ void __launch_bounds__(N1 > 0 ? kPencilThreads : kZThreads) k_zgreen(
   T* cres = reinterpret_cast<T*>((kPencil ? b0 : b1) + (size_t)6 * a.HC * ps);  // HC * nz residual terms
   const int tid = threadIdx.x, nthr = blockDim.x;
   if (a.done && *a.done) return;
-  const int j = blockIdx.y;
-  const int h0 = blockIdx.x * a.HC;
+  const int j = (int)cta.by;
+  const int h0 = (int)cta.bx * a.HC;
   const int hc = min(a.HC, a.H - h0);
   const size_t H = a.H, ny = a.ny;
   C2<T>* gz = a.spec + ((size_t)j * H + h0) * 6;
@@ -786,7 +819,7 @@ __global__ void __launch_bounds__(N1 > 0 ? kPencilThreads : kZThreads) k_zgreen(
   if (tid == 0) {
     __threadfence();
     const unsigned int prev = atomicAdd(a.counter, 1u);
-    s_last = (prev == block_count() - 1) ? 1 : 0;
+    s_last = (prev == cta.count - 1) ? 1 : 0;
   }
   __syncthreads();
   if (s_last) {
@@ -847,6 +880,13 @@ __global__ void __launch_bounds__(N1 > 0 ? kPencilThreads : kZThreads) k_zgreen(
   }
 }
 
+template <typename T, int N1, int N2>
+__global__ void __launch_bounds__(N1 > 0 ? kPencilThreads : kZThreads) k_zgreen(const ZArgs<T> a) {
+  __shared__ double red[32][kNumRed];
+  __shared__ int s_last;
+  zgreen_cta<T, N1, N2>(a, own_grid(), red, s_last);
+}
+
 // Graph mode: second bound on the device-side iteration loop, independent of the
 // residual kernel's decision: after `limit` executions of the loop body (two iterations
 // each) the loop condition is cleared.
@@ -855,6 +895,106 @@ __global__ void k_loop_guard(IterStatus* st, int limit, cudaGraphConditionalHand
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     const int g = ++st->guard;
     if (g >= limit || st->done) cudaGraphSetConditional(cond, 0u);
+  }
+}
+
+// ---------------------------------------------------------------- grouped passes ----
+// One launch of a pass over several RVEs (an ensemble stepped together): the combined grid
+// is the members' own grids laid end to end -- member m owns CTAs start[m] .. start[m+1]-1,
+// its grid gx[m] CTAs wide -- and each CTA runs its member's pass exactly as the member's
+// own launch would (same arguments, grid place, reductions and decisions), so results are
+// those of stepping each RVE alone.  A member whose increment is decided returns at once.
+constexpr int kMaxGroup = 16;
+
+// The CTA's member and its place in that member's grid.
+__device__ __forceinline__ Cta group_place(const int* start, const int* gx, int n, int* member) {
+  int m = 0;
+  while (m + 1 < n && (int)blockIdx.x >= start[m + 1]) ++m;
+  const unsigned loc = blockIdx.x - (unsigned)start[m];
+  *member = m;
+  return Cta{loc % (unsigned)gx[m], loc / (unsigned)gx[m], loc, (unsigned)(start[m + 1] - start[m])};
+}
+
+template <typename T>
+struct XGroup {
+  XCommon<T> k;  // shared by every member (the members' own k are not read)
+  XArgs<T> m[kMaxGroup];
+  int start[kMaxGroup + 1];
+  int gx[kMaxGroup];
+  int n;
+};
+template <typename T>
+struct LineGroup {
+  LineArgs<T> m[kMaxGroup];
+  int start[kMaxGroup + 1];
+  int gx[kMaxGroup];
+  int n;
+};
+template <typename T>
+struct ZGroup {
+  ZArgs<T> m[kMaxGroup];
+  int start[kMaxGroup + 1];
+  int gx[kMaxGroup];
+  int n;
+};
+
+template <typename T, bool COMMIT, int NP>
+__global__ void __launch_bounds__(kXThreads, XMinBlocks<T>::value) k_xpass_group(const __grid_constant__ XGroup<T> g) {
+  int m;
+  const Cta cta = group_place(g.start, g.gx, g.n, &m);
+  xpass_cta<T, COMMIT, NP>(g.m[m], g.k, cta);
+}
+
+// y pass of every member: the two-step register transform where the member's length has a
+// split and its chunk fits (as launch_line chooses), the Stockham kernel's CTA otherwise.
+template <typename T, int SIGN>
+__global__ void __launch_bounds__(kPencilThreads) k_line_group(const __grid_constant__ LineGroup<T> g) {
+  int m;
+  const Cta cta = group_place(g.start, g.gx, g.n, &m);
+  const LineArgs<T>& a = g.m[m];
+  const bool split = a.NC == 6 && a.hstride == 6 && a.HC <= pencil_max_hc(a.d.n);
+  switch (split ? a.d.n : 0) {
+    case 64: line_pencil_cta<T, SIGN, PencilSplit<64>::N1, PencilSplit<64>::N2>(a, cta); return;
+    case 96: line_pencil_cta<T, SIGN, PencilSplit<96>::N1, PencilSplit<96>::N2>(a, cta); return;
+    case 128: line_pencil_cta<T, SIGN, PencilSplit<128>::N1, PencilSplit<128>::N2>(a, cta); return;
+    case 160: line_pencil_cta<T, SIGN, PencilSplit<160>::N1, PencilSplit<160>::N2>(a, cta); return;
+    case 256: line_pencil_cta<T, SIGN, PencilSplit<256>::N1, PencilSplit<256>::N2>(a, cta); return;
+    default: line_cta<T, SIGN>(a, cta); return;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kPencilThreads) k_zgreen_group(const __grid_constant__ ZGroup<T> g) {
+  __shared__ double red[32][kNumRed];
+  __shared__ int s_last;
+  int m;
+  const Cta cta = group_place(g.start, g.gx, g.n, &m);
+  const ZArgs<T>& a = g.m[m];
+  switch (a.HC <= pencil_max_hc(a.nz) ? a.nz : 0) {
+    case 64: zgreen_cta<T, PencilSplit<64>::N1, PencilSplit<64>::N2>(a, cta, red, s_last); return;
+    case 96: zgreen_cta<T, PencilSplit<96>::N1, PencilSplit<96>::N2>(a, cta, red, s_last); return;
+    case 128: zgreen_cta<T, PencilSplit<128>::N1, PencilSplit<128>::N2>(a, cta, red, s_last); return;
+    case 160: zgreen_cta<T, PencilSplit<160>::N1, PencilSplit<160>::N2>(a, cta, red, s_last); return;
+    case 256: zgreen_cta<T, PencilSplit<256>::N1, PencilSplit<256>::N2>(a, cta, red, s_last); return;
+    default: zgreen_cta<T, 0, 0>(a, cta, red, s_last); return;
+  }
+}
+
+// Bound and exit of a group's device-side iteration loop: after `limit` executions of the
+// loop body, or once every member's increment is decided, the loop condition is cleared.
+// The execution count lives in the first member's status record.
+struct GuardGroup {
+  IterStatus* st[kMaxGroup];
+  int n;
+  int limit;
+};
+template <typename T>
+__global__ void k_group_guard(const GuardGroup g, cudaGraphConditionalHandle cond) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    const int c = ++g.st[0]->guard;
+    bool all = true;
+    for (int m = 0; m < g.n; ++m) all = all && g.st[m]->done != 0;
+    if (c >= g.limit || all) cudaGraphSetConditional(cond, 0u);
   }
 }
 

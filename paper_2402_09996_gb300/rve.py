@@ -118,7 +118,7 @@ EXPORTED = [
     "rve_set_mixed_load", "rve_step", "rve_get_effective", "rve_get_fields", "rve_save_state",
     "rve_load_state", "rve_last_error", "rve_destroy", "rve_material_point", "rve_fft_r2c",
     "rve_fft_c2r", "rve_label_voronoi", "rve_kernel_times", "rve_get_residuals", "rve_label_voronoi_noalloc",
-    "rve_step_batch", "rve_material_point_vjp", "rve_adjoint_increment",
+    "rve_step_batch", "rve_material_point_vjp", "rve_adjoint_increment", "rve_alu_probe",
 ]
 NOALLOC_MAX_PARENTS = 4096  # RVE_NOALLOC_MAX_PARENTS of include/rve.h
 
@@ -159,6 +159,7 @@ def load_library(path: str | os.PathLike | None = None):
                                            vp, d, i, vp]
     lib.rve_adjoint_increment.argtypes = [vp, vp, vp, vp, C.POINTER(C.c_double), d, vp, vp, C.POINTER(C.c_double),
                                           C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
+    lib.rve_alu_probe.argtypes = [i, i, i, vp, vp, C.POINTER(C.c_double)]
     for name in EXPORTED:
         getattr(lib, name).restype = C.c_int
     lib.rve_options_default.restype = None
@@ -581,6 +582,15 @@ class HistoryMisfit:
         return cls._fn().apply(params, euler, config)
 
 
+def alu_probe(kind, blocks, iters, sink):
+    """Enqueue one ALU throughput probe (rve_alu_probe) on torch's current stream; `sink`
+    is a CUDA tensor of at least 8 bytes.  Returns the operations of the launch."""
+    lib = load_library()
+    ops = C.c_double(0.0)
+    _check(lib.rve_alu_probe(int(kind), int(blocks), int(iters), _ptr(sink), _torch_stream(), C.byref(ops)))
+    return ops.value
+
+
 def fft_r2c(real, precision=FP64):
     """Forward 3-D R2C transform of (ncomp, nz, ny, nx) CUDA tensor -> (ncomp, nz, ny, nx//2+1) complex."""
     import torch
@@ -628,6 +638,8 @@ def label_voronoi_noalloc(inputs, out):
     """Grain-ID map of an inputs.RVEInputs written into `out`, a CUDA int32 tensor
     (nz, ny, nx), by the entry point that allocates no device memory (its scratch is a
     fixed static array: at most NOALLOC_MAX_PARENTS parents)."""
+    import torch
+
     lib = load_library()
     nz, ny, nx = inputs.shape
     seeds = np.ascontiguousarray(inputs.seeds, dtype=np.float64)
@@ -635,7 +647,12 @@ def label_voronoi_noalloc(inputs, out):
     nrm = np.ascontiguousarray(inputs.twin_normal, dtype=np.float64)
     if not getattr(out, "is_cuda", False) or tuple(out.shape) != (nz, ny, nx):
         raise ValueError("out must be a CUDA tensor of shape (nz, ny, nx)")
-    st = lib.rve_label_voronoi_noalloc(nx, ny, nz, seeds.shape[0], _ptr(seeds), _ptr(tw), _ptr(nrm), _ptr(out),
-                                       _torch_stream())
+    if out.dtype != torch.int32 or not out.is_contiguous():
+        raise ValueError("out must be a contiguous torch.int32 tensor")
+    # the library looks up its scratch and takes the stream on the current device: make
+    # it the output's device
+    with torch.cuda.device(out.device):
+        st = lib.rve_label_voronoi_noalloc(nx, ny, nz, seeds.shape[0], _ptr(seeds), _ptr(tw), _ptr(nrm), _ptr(out),
+                                           C.c_void_p(torch.cuda.current_stream(out.device).cuda_stream))
     _check(st, None)
     return out

@@ -257,3 +257,64 @@ def test_history_gradient_register_transform_grid(lib, cuda):
         jm, _ = _history_J(gid, inp.euler, {name: p0 - h}, target, n_inc, dt, **opts)
         num = (jp - jm) / (2 * h)
         assert abs(num - gp[k]) <= 1e-4 * max(abs(num), abs(gp[k])) + 1e-9 * J / abs(p0), (name, num, gp[k])
+
+
+def _oracle_fd_case():
+    """6 x 8 x 10 grid, 3 parent grains all twinned (6 orientations), 3 increments of 1 s
+    (0.3 % strain, slip and twinning active in increments 2 and 3), tolerance 1e-12: the
+    oracle's <sigma_zz> curve, a target 3 % below it, and central differences (relative
+    step 1e-4; 1e-4 rad for angles) of the oracle's misfit for the 9 parameters and two
+    Bunge angles."""
+    import oracle_jobs
+    from oracle.voronoi import label_rve
+
+    from paper_2402_09996_gb300 import inputs, rve
+
+    inp = inputs.make_inputs((6, 8, 10), 3, 1.0, seed=12)
+    gid = label_rve(inp)
+    euler = inp.euler.copy()
+    n_inc, dt, tol = 3, 1.0, 1e-12
+    base = orc.Material()
+    jobs = [(gid, euler, {}, n_inc, dt, tol)]
+    steps = []
+    for name in rve.PARAM_NAMES:
+        p0 = getattr(base, name)
+        h = 1e-4 * abs(p0)
+        steps.append(("param", name, h))
+        jobs += [(gid, euler, {name: p0 + h}, n_inc, dt, tol), (gid, euler, {name: p0 - h}, n_inc, dt, tol)]
+    for g, a in ((0, 1), (3, 0)):  # a parent's Phi and a twin's phi1
+        ep, em = euler.copy(), euler.copy()
+        ep[g, a] += 1e-4
+        em[g, a] -= 1e-4
+        steps.append(("euler", (g, a), 1e-4))
+        jobs += [(gid, ep, {}, n_inc, dt, tol), (gid, em, {}, n_inc, dt, tol)]
+    res = oracle_jobs.run_parallel(jobs)
+    target = 0.97 * res[0]
+    J = lambda S: float(np.sum((S - target) ** 2))  # noqa: E731
+    fd = {key: (J(res[1 + 2 * k]) - J(res[2 + 2 * k])) / (2 * h) for k, (_, key, h) in enumerate(steps)}
+    return gid, euler, n_inc, dt, target, J(res[0]), fd
+
+
+def test_history_gradient_matches_oracle_finite_differences(lib, cuda):
+    """The adjoint gradient of a load history against the FP64 oracle: the FP64 GPU
+    gradient (tolerance 1e-12) within 1e-4 of central differences of the oracle's own
+    misfit for all 9 parameters and two Bunge angles, and the misfit itself equal to the
+    oracle's; the FP32 gradient (FP32 forward and adjoint, tolerance 1e-6) against the same
+    differences within 1e-4 relative (measured: at most 3.1e-5)."""
+    from paper_2402_09996_gb300 import rve
+
+    gid, euler, n_inc, dt, target, J_ref, fd = _oracle_fd_case()
+    J, gp, ge, _ = rve.history_gradient(gid, euler, n_inc, dt, target, precision=rve.FP64, tol=1e-12,
+                                        max_iter=3000)
+    assert abs(J - J_ref) <= 1e-8 * J_ref, (J, J_ref)
+    got = {name: gp[k] for k, name in enumerate(rve.PARAM_NAMES)}
+    got.update({(0, 1): ge[0, 1], (3, 0): ge[3, 0]})
+    for key, num in fd.items():
+        assert abs(got[key] - num) <= 1e-4 * abs(num), (key, got[key], num)
+    J32, gp32, ge32, _ = rve.history_gradient(gid, euler, n_inc, dt, target, precision=rve.FP32)
+    got32 = {name: gp32[k] for k, name in enumerate(rve.PARAM_NAMES)}
+    got32.update({(0, 1): ge32[0, 1], (3, 0): ge32[3, 0]})
+    errs = {str(key): abs(got32[key] - num) / abs(num) for key, num in fd.items()}
+    print("FP32 adjoint vs oracle central differences, relative error:", errs)
+    assert abs(J32 - J_ref) <= 1e-3 * J_ref
+    assert max(errs.values()) <= 1e-4, errs

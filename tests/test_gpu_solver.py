@@ -48,11 +48,15 @@ def test_two_grain_fixed_iterations_fp64(lib, cuda):
 
 @pytest.mark.parametrize("shape,prec", [((12, 10, 6), "fp64"), ((12, 10, 6), "fp32"), ((64, 64, 6), "fp64"),
                                         ((64, 64, 6), "fp32"), ((256, 8, 4), "fp64"), ((8, 256, 4), "fp32"),
-                                        ((6, 8, 64), "fp64"), ((4, 4, 128), "fp32"), ((4, 6, 256), "fp64")])
+                                        ((6, 8, 64), "fp64"), ((4, 4, 128), "fp32"), ((4, 6, 256), "fp64"),
+                                        ((4, 6, 96), "fp64"), ((4, 96, 6), "fp32"), ((96, 4, 6), "fp64"),
+                                        ((4, 4, 160), "fp32"), ((4, 160, 4), "fp64"), ((160, 4, 4), "fp32")])
 def test_ragged_voronoi_tolerance_mode(lib, cuda, shape, prec):
     """5 twinned grains, 4 increments: a 6 x 10 x 12 grid (radix-3/5 lengths, odd line
     counts, shared-memory Stockham transforms), and grids whose x, y or z lines have the
-    power-of-two lengths of the two-step register transforms (64, 128, 256)."""
+    lengths of the two-step register transforms (64 = 8 * 8, 96 = 8 * 12, 128 = 8 * 16,
+    160 = 10 * 16, 256 = 16 * 16; the 12- and 10-point steps are mixed-radix 4 * 3 and
+    2 * 5)."""
     from paper_2402_09996_gb300 import inputs, rve
 
     inp = inputs.make_inputs(shape, 5, 0.5, seed=42)
@@ -173,6 +177,47 @@ def test_save_load_roundtrip(lib, cuda):
     assert np.array_equal(a["S"], b["S"]) and a["mean_v"] == b["mean_v"]
 
 
+@pytest.mark.parametrize("prec,graphs", [("fp64", True), ("fp64", False), ("fp32", True)])
+def test_nan_in_loaded_state_is_reported_and_committed_state_kept(lib, cuda, prec, graphs):
+    """Failure detection without a GPU fault: a checkpoint blob with a NaN planted (on the
+    host) in one voxel's plastic strain makes the next increment's mean stress NaN, which
+    the device-side decision reports as RVE_ERR_NAN; nothing is committed, and after the
+    clean blob is loaded the handle continues exactly like an uninterrupted run (in FP64
+    also like the oracle)."""
+    from paper_2402_09996_gb300 import rve
+
+    gid = np.zeros((8, 8, 8), dtype=np.uint32)
+    gid[:, :, 4:] = 1
+    gid[2:5, 1:6, 0:3] = 1
+    euler = np.array([[0.3, 0.9, 1.7], [2.1, 1.2, 0.4]])
+    P, dtype = (rve.FP64, np.float64) if prec == "fp64" else (rve.FP32, np.float32)
+    ts, nvox = np.dtype(dtype).itemsize, gid.size
+    with _rve(gid, euler, precision=P, fixed_iters=6, graphs=graphs) as s:
+        s.step(2)
+        clean = s.save_state()
+        # the blob ends with eps_p (6), v (16), alpha (12), eps_n (6), sigma_n (6) fields
+        bad = bytearray(clean)
+        off = len(bad) - 46 * nvox * ts + (2 * nvox + 77) * ts  # eps_p component 33, voxel 77
+        bad[off:off + ts] = np.array([np.nan], dtype=dtype).tobytes()
+        s.load_state(bytes(bad))
+        with pytest.raises(rve.RVEError) as ei:
+            s.step(1)
+        assert ei.value.status == rve.STATUS_CODES["RVE_ERR_NAN"]
+        assert len(s.history()) == 2  # nothing committed
+        s.load_state(clean)
+        s.step(1)
+        got = s.history()
+    with _rve(gid, euler, precision=P, fixed_iters=6, graphs=graphs) as s:
+        s.step(3)
+        uninterrupted = s.history()
+    assert np.array_equal(got[-1]["S"], uninterrupted[-1]["S"])
+    assert got[-1]["mean_v"] == uninterrupted[-1]["mean_v"]
+    if prec == "fp64":
+        ref = _oracle(gid, euler, fixed_iters=6)
+        ref.run(3)
+        _compare_histories(got, ref.history, 1e-9)
+
+
 def test_invalid_arguments(lib, cuda):
     from paper_2402_09996_gb300 import rve
 
@@ -220,12 +265,13 @@ def test_graph_loop_equals_host_driven_loop(lib, cuda, shape, prec, fixed):
 
 
 @pytest.mark.parametrize("shape,prec", [((20, 24, 32), "fp64"), ((20, 24, 32), "fp32"), ((64, 64, 16), "fp64"),
-                                        ((128, 64, 12), "fp32")])
+                                        ((128, 64, 12), "fp32"), ((160, 96, 10), "fp32"), ((96, 160, 8), "fp64")])
 def test_fft_tile_widths_do_not_change_results(lib, cuda, shape, prec):
     """The y / z pass kx tile widths (forced to 1 or 16, or chosen by the autotuner) leave
     every result bit-identical: each sequence's FFT is the same arithmetic and the
-    residual is summed per (ky, kx) column in a fixed order.  Power-of-two line lengths
-    (64, 128) run the two-step register transforms at every width (16 is clamped)."""
+    residual is summed per (ky, kx) column in a fixed order.  Line lengths with a register
+    split (64, 96, 128, 160) run the two-step register transforms at every width (16 is
+    clamped to the split's limit)."""
     from paper_2402_09996_gb300 import inputs, rve
 
     inp = inputs.make_inputs(shape, 7, 0.5, seed=99)

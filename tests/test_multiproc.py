@@ -27,6 +27,8 @@ def _worker(rank, world, port, out):
     # replicas draw different realizations (seed offset by rank) of the same workload recipe
     inp = bench.make_workload(rank)
     out[10 + rank] = float(inp.seeds[0, 0])
+    members = bench.ensemble_members(rank)
+    out[20 + rank] = (len(members), tuple(m.shape[0] for m in members), float(members[5].seeds[0, 0]))
     dist.destroy_process_group()
 
 
@@ -40,6 +42,9 @@ def test_two_rank_aggregation_gloo():
     mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
     assert out[0] == (3000.0, 15.0) and out[1] == (3000.0, 15.0)
     assert out[10] != out[11]
+    # each rank steps its own 16-member ensemble of the same sizes
+    assert out[20][:2] == out[21][:2] == (16, (64,) * 4 + (96,) * 4 + (128,) * 4 + (160,) * 4)
+    assert out[20][2] != out[21][2]
 
 
 def test_aggregate_without_process_group():

@@ -35,3 +35,16 @@ def test_noalloc_rejects_more_parents_than_its_scratch_holds(lib, cuda):
         rve.label_voronoi_noalloc(big, out)
     assert ei.value.status == 1
     assert "maximum" in str(ei.value)
+
+
+def test_noalloc_wrapper_refuses_wrong_output_tensors(lib, cuda):
+    import torch
+
+    from paper_2402_09996_gb300 import inputs, rve
+
+    inp = inputs.make_inputs((8, 8, 8), 5, 0.5, seed=2)
+    for bad in (torch.empty((8, 8, 8), dtype=torch.int64, device=cuda),
+                torch.empty((8, 8, 16), dtype=torch.int32, device=cuda)[:, :, ::2],
+                torch.empty((8, 8, 8), dtype=torch.int32)):
+        with pytest.raises(ValueError):
+            rve.label_voronoi_noalloc(inp, bad)

@@ -231,18 +231,22 @@ def _iterations(solvers):
 
 
 # ---------------------------------------------------------------- legs ------------------
-def leg_ensemble(members, warmup, steps, dist=None, clocks=None):
+def leg_ensemble(members, warmup, steps, dist=None, clocks=None, grouped=False):
     """The headline: every member stepped together; device time of the K timed increments
-    (CUDA events on the launching stream, which the batch call's private streams join)."""
+    (CUDA events on the launching stream, which the batch call's private streams join).
+    grouped: the members run as one group (one launch per pass over all of them, lockstep
+    iterations, one graph launch per increment) instead of on private streams."""
     import torch
 
     from paper_2402_09996_gb300 import rve
 
     solvers = []
     for inp in members:
-        s = rve.RVE(rve.label_voronoi(inp), inp.euler, precision=rve.FP32, n_sub=0)
+        s = rve.RVE(rve.label_voronoi(inp), inp.euler, precision=rve.FP32, n_sub=0, batch_group=grouped)
         s.set_mixed_load(dt=DT)
         solvers.append(s)
+    if rve.batch_grouped(solvers) != grouped:
+        raise RuntimeError("the ensemble did not take the requested batch mode")
     rve.step_batch(solvers, warmup)
     before = _iterations(solvers)
     stream = torch.cuda.current_stream()
@@ -267,7 +271,11 @@ def leg_ensemble(members, warmup, steps, dist=None, clocks=None):
     for s in solvers:
         s.close()
     voxit = float(sum(n * i for n, i in zip(nvox, its)))
-    launches = int(sum(launches_per_increment(i) for row in per_inc for i in row))
+    if grouped:  # per increment: every member's strain shift, then one graph of grouped launches
+        n_m = len(per_inc)
+        launches = int(sum(n_m + 5 + 9 * (max(row[k] for row in per_inc) // 2) + 1 for k in range(len(per_inc[0]))))
+    else:
+        launches = int(sum(launches_per_increment(i) for row in per_inc for i in row))
     return {"ms": ms, "voxit": voxit, "iterations": its, "nvox": nvox, "clocks": clk, "launches": launches,
             "last": {"E33": hist_last["E"][2], "S33": hist_last["S"][2]}}
 
@@ -679,6 +687,12 @@ def run_gpu(args):
         line["fp64_plain"] = fp64
         line["speedup_fp32_batched_vs_fp64_plain"] = value / fp64["grid128"]["value"]
         line["speedup_fp32_batched_vs_fp64_plain16"] = value / fp64["plain16"]["value"]
+        grp = leg_ensemble(members, args.warmup, args.steps, grouped=True)
+        line["ensemble_grouped"] = {
+            "value": grp["voxit"] / (grp["ms"] * 1e-3), "unit": METRIC, "ms_per_step": grp["ms"] / args.steps,
+            "fixed_point_iterations_timed": grp["iterations"],
+            "what": "the same increments with the members stepped as one group: one kernel launch per pass over all "
+                    "16 members' grids, lockstep iterations, one CUDA graph launch per increment (batch_group on)"}
         line["adjoint_over_forward"] = leg_adjoint()
         line["fft_comparison"] = leg_fft_comparison()
         if not args.no_cpu_baseline:
@@ -686,34 +700,76 @@ def run_gpu(args):
     print(json.dumps(line))
 
 
+def _sample_fields(s, rve, flat):
+    """The committed fields of a solver at the sampled voxels (components x samples)."""
+    out = {}
+    for key, f in (("sigma", rve.FIELD_STRESS), ("eps", rve.FIELD_STRAIN), ("eps_p", rve.FIELD_EPS_P),
+                   ("v", rve.FIELD_V), ("alpha", rve.FIELD_ALPHA)):
+        a = s.field(f)
+        out[key] = a.reshape(a.shape[0], -1)[:, flat].copy()
+    return out
+
+
 def run_precision(args):
-    """Precision study on the twinned 256^3 RVE (1000 grains): the same --steps increments
-    in FP32 fields (FP64 norms) and in FP64 throughout, both on this GPU; reports the
-    relative difference of every effective result per increment and of the local fields
-    at the end, and the throughput of each precision.  (The FP64 GPU path itself matches
-    the FP64 oracle to 1e-9 on the 16^3 history and on sampled voxels; see tests/.)"""
+    """Precision study on a twinned RVE (256^3 with 1000 grains, or 128^3 with 200; p_twin
+    0.5): FP32 fields with FP64 norms over --steps increments (40 = 2 % strain) against
+    FP64 throughout over --fp64-steps increments, both on this GPU.  Reports, per increment
+    both precisions reached, the relative difference of every effective result, and at
+    every 10th such increment (0.5 %, 1 %, ...) the L2 differences of the local stress,
+    strain, slip and twin fields; the throughput of each precision.  With --dump-sample
+    PATH it writes 384 sampled voxels' committed state before and after the last increment
+    of each precision (numpy .npz) for tests/check_material_point_sample.py, which checks
+    them against the oracle's material-point update.  (The FP64 GPU path matches the FP64
+    oracle to 1e-9 on the 16^3 history; see tests/.)"""
     import torch
 
     from paper_2402_09996_gb300 import build_lib, inputs, rve
 
     build_lib.build()
-    inp = inputs.workload_twinned_256()
+    n = args.precision_grid
+    inp = inputs.workload_twinned_256() if n == 256 else make_workload(0)
     gid = rve.label_voronoi(inp)
     stream = torch.cuda.current_stream()
+    flat = np.random.default_rng(2024).choice(gid.size, 384, replace=False)
+    l2 = lambda x, y: float(np.linalg.norm(x - y) / np.linalg.norm(y))  # noqa: E731
+    n64 = min(args.fp64_steps, args.steps)
+    marks = [k for k in range(10, n64 + 1, 10)] or [n64]
+    keep = {}
     runs = {}
-    for name, prec in (("fp32", rve.FP32), ("fp64", rve.FP64)):
+    sample = {"flat": flat, "grid": np.array(gid.shape), "euler": inp.euler, "grain": gid.reshape(-1)[flat],
+              "dt": DT}
+    for name, prec, steps in (("fp64", rve.FP64, n64), ("fp32", rve.FP32, args.steps)):
         s = rve.RVE(gid, inp.euler, precision=prec, n_sub=0)
-        s.set_mixed_load(dt=0.5)
-        torch.cuda.synchronize()
-        t0 = torch.cuda.Event(enable_timing=True)
-        t1 = torch.cuda.Event(enable_timing=True)
-        t0.record(stream)
-        its = s.step(args.steps)
-        t1.record(stream)
-        torch.cuda.synchronize()
-        ms = t0.elapsed_time(t1)
-        runs[name] = {"hist": s.history(), "ms": ms, "iters": its, "nvox": s.nvox,
-                      "sig": s.field(rve.FIELD_STRESS), "v": s.field(rve.FIELD_V), "eps": s.field(rve.FIELD_STRAIN)}
+        s.set_mixed_load(dt=DT)
+        ms = 0.0
+        its = 0
+        local = {}
+        for k in range(1, steps + 1):
+            if k == steps:
+                before = _sample_fields(s, rve, flat)
+            torch.cuda.synchronize()
+            t0, t1 = _event_pair()
+            t0.record(stream)
+            its += s.step(1)
+            t1.record(stream)
+            torch.cuda.synchronize()
+            ms += t0.elapsed_time(t1)
+            if k in marks:
+                f = {"sig": s.field(rve.FIELD_STRESS), "eps": s.field(rve.FIELD_STRAIN), "v": s.field(rve.FIELD_V)}
+                if name == "fp64":
+                    keep[k] = f
+                else:
+                    b = keep[k]
+                    local[k] = {"E33": s.history()[-1]["E"][2], "sigma_L2": l2(f["sig"], b["sig"]),
+                                "sigma_max_abs_MPa": float(np.max(np.abs(f["sig"] - b["sig"]))),
+                                "strain_L2": l2(f["eps"], b["eps"]), "v_slip_L2": l2(f["v"][:12], b["v"][:12]),
+                                "f_twin_L2": l2(f["v"][12:], b["v"][12:]) if np.any(b["v"][12:]) else 0.0}
+                del f
+        after = _sample_fields(s, rve, flat)
+        sample.update({f"{name}_before_{key}": v for key, v in before.items()})
+        sample.update({f"{name}_after_{key}": v for key, v in after.items()})
+        sample[f"{name}_n_sub"] = np.array(N_SUB)
+        runs[name] = {"hist": s.history(), "ms": ms, "iters": its, "nvox": s.nvox, "local": local}
         s.close()
     a, b = runs["fp32"], runs["fp64"]
 
@@ -728,20 +784,20 @@ def run_precision(args):
                         "S": rel(ha["S"], hb["S"]), "mean_S_eq": rel(ha["mean_S_eq"], hb["mean_S_eq"]),
                         "S_eq_of_mean": rel(ha["S_eq_of_mean"], hb["S_eq_of_mean"]),
                         "mean_f": rel(ha["mean_f"], hb["mean_f"]), "mean_v": rel(ha["mean_v"], hb["mean_v"])})
-    l2 = lambda x, y: float(np.linalg.norm(x - y) / np.linalg.norm(y))  # noqa: E731
+    if args.dump_sample:
+        np.savez(args.dump_sample, **sample)
     nv = a["nvox"]
-    f32 = np.sqrt(2.0) * a["v"][12:]
-    f64 = np.sqrt(2.0) * b["v"][12:]
     line = {
         "metric": "relative difference FP32 fields vs FP64 (GPU)",
-        "workload": "twinned RVE 256^3, 1000 Voronoi grains (p_twin 0.5), uniaxial tension 1e-3/s, dt 0.5 s",
-        "increments": args.steps,
+        "workload": (f"twinned RVE {n}^3, {inp.n_parent} Voronoi grains (p_twin 0.5), uniaxial tension 1e-3/s, "
+                     f"dt 0.5 s; FP32 {args.steps} increments, FP64 {n64}"),
         "per_increment": per_inc,
-        "local_final": {"sigma_L2": l2(a["sig"], b["sig"]), "sigma_max_abs_MPa": float(np.max(np.abs(a["sig"] - b["sig"]))),
-                        "strain_L2": l2(a["eps"], b["eps"]), "v_L2": l2(a["v"][:12], b["v"][:12]),
-                        "f_L2": l2(f32, f64) if np.any(f64) else 0.0},
+        "local": a["local"],
+        "fp32_curve": [[h["E"][2], h["S"][2], h["S_eq_of_mean"], h["mean_S_eq"], h["mean_v"], h["mean_f"],
+                        h["iterations"]] for h in a["hist"]],
         "throughput": {"fp32": nv * a["iters"] / (a["ms"] * 1e-3), "fp64": nv * b["iters"] / (b["ms"] * 1e-3),
                        "unit": METRIC},
+        "seconds": {"fp32": a["ms"] * 1e-3, "fp64": b["ms"] * 1e-3},
     }
     print(json.dumps(line))
 
@@ -929,6 +985,9 @@ def main_args(argv=None):
     ap.add_argument("--paper-size", type=int, default=256, help="paper workload: grid size")
     ap.add_argument("--seed", type=int, default=0, help="paper workload: realization seed")
     ap.add_argument("--fp64-steps", type=int, default=20, help="precision256: FP64 increments (<= --steps)")
+    ap.add_argument("--precision-grid", type=int, default=256, choices=[128, 256],
+                    help="precision256: grid (256^3 with 1000 grains or the 128^3 workload)")
+    ap.add_argument("--dump-sample", default="", help="precision256: write the sampled voxels (.npz) here")
     ap.add_argument("--profile-case", type=int, default=0, metavar="N",
                     help="profiling case: an N^3 twinned RVE (60 grains, p=0.5, seed 11), "
                          "--warmup increments, then --steps increments between "

@@ -89,6 +89,9 @@ typedef struct {
                          fastest (results do not depend on the widths) */
   int y_tile, z_tile; /* > 0: force the kx tile width of the y (z) pass, overriding the
                          autotuner and the default (at most 16; clamped to nx/2 + 1) */
+  int batch_group;    /* nonzero: rve_step_batch may step this handle in a group (one
+                         launch per pass over all members); 0 (default) keeps it on its own
+                         stream.  See rve_step_batch. */
 } rve_options;
 
 /* Kernel kinds reported by rve_kernel_times. */
@@ -177,13 +180,22 @@ rve_status rve_set_mixed_load(rve_t h, const double Edot[6], const uint8_t strai
 rve_status rve_step(rve_t h, int n_increments, long long* iterations_out);
 
 /* Run n_increments load increments on each of n independent solvers at once (an
- * ensemble of RVE realizations of any sizes and precisions, each with its own material
- * and load; Sec. 5 averages over such realizations).  Each handle works on a private
- * stream created for the call, ordered after the work already enqueued on its own
- * stream and before any work enqueued there afterwards, so the RVEs' kernels run
- * concurrently and a small RVE does not leave the GPU idle.  The host resumes each
- * handle as soon as its enqueued iterations finish.  Results are identical to calling
- * rve_step on each handle in turn.
+ * ensemble of RVE realizations of any sizes; Sec. 5 averages over such realizations).
+ * Results are identical to calling rve_step on each handle in turn.
+ *  - Grouped (2 to 16 handles of one precision with the same material, load and
+ *    substeps, all with graphs and batch_group on and timing off; batch_group is off by
+ *    default because the private-stream mode measured faster on the ensemble
+ *    workload): the handles are
+ *    stepped as one group on a private stream.  Every pass of a fixed-point iteration
+ *    is one kernel launch whose grid spans all members' grids (each CTA runs its
+ *    member's pass unchanged), the members iterate in lockstep (a member whose
+ *    increment is decided returns at once from later launches), and one increment of
+ *    the whole group is one CUDA graph launch.
+ *  - Otherwise each handle works on a private stream created for the call, and the host
+ *    resumes each handle as soon as its enqueued iterations finish, so the RVEs' kernels
+ *    run concurrently.
+ * In both modes the private streams are ordered after the work already enqueued on each
+ * handle's own stream and before any work enqueued there afterwards.
  *   hs             n distinct handles on one device (host array, not retained);
  *   iterations_out total committed fixed-point iterations over all handles (may be NULL);
  *   failed_out     index of the first handle that returned an error, or -1 (may be NULL).
@@ -192,6 +204,10 @@ rve_status rve_step(rve_t h, int n_increments, long long* iterations_out);
  * rve_last_error(NULL) names its handle.  With opt.timing the kernel times of a handle
  * include the time its kernels shared the GPU with the other handles'. */
 rve_status rve_step_batch(rve_t* hs, int n, int n_increments, long long* iterations_out, int* failed_out);
+
+/* Whether rve_step_batch would step these n handles as one group (*grouped = 1) or on
+ * private streams (*grouped = 0), by the rule stated there.  No device work. */
+rve_status rve_batch_grouped(rve_t* hs, int n, int* grouped);
 
 /* Adjoint of one converged load increment n (t_{n-1} -> t_n) of a history objective J
  * (the paper defines no adjoint; this extends its method to gradients).  The increment's

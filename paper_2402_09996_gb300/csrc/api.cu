@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <string>
 #include <thread>
 #include <vector>
@@ -1195,6 +1196,297 @@ rve_status step_one(rve_s* h, long long* iters) {
   return st;
 }
 
+// ---------------------------------------------------------------- grouped batch ------
+// An ensemble stepped as one group (rve_step_batch): every pass of a fixed-point iteration
+// is one launch over all members (k_*_group; each CTA runs its member's pass exactly as the
+// member's own launch would), the members iterate in lockstep (a member whose increment is
+// decided returns at once from later launches), and one increment of the whole group is
+// one CUDA graph launch: iteration 0, a while-node whose body runs two iterations and the
+// group guard, the commit, and every member's status copy.
+
+int nsub_of(const rve_s* h) { return h->opt.n_sub > 0 ? h->opt.n_sub : default_nsub(h->dt); }
+
+// Handles that can run as one group: one device and precision, the graph loop, the same
+// material, load and substeps (the grouped x pass reads them once), at most kMaxGroup.
+bool groupable(rve_s* const* hs, int n) {
+  if (n < 2 || n > kMaxGroup) return false;
+  const rve_s* a = hs[0];
+  for (int i = 0; i < n; ++i) {
+    const rve_s* h = hs[i];
+    if (!h->opt.batch_group || !use_graphs(h) || h->lin_mode || h->opt.precision != a->opt.precision ||
+        h->opt.device != a->opt.device)
+      return false;
+    if (std::memcmp(&h->mat, &a->mat, sizeof(rve_material)) != 0 || h->dt != a->dt || nsub_of(h) != nsub_of(a))
+      return false;
+    for (int c = 0; c < 6; ++c)
+      if (h->Edot[c] != a->Edot[c] || h->ctrl[c] != a->ctrl[c] || h->Sigma[c] != a->Sigma[c]) return false;
+  }
+  return true;
+}
+
+// Arguments of one grouped iteration (heap: the blocks are kilobytes each).
+template <typename T>
+struct GroupIter {
+  XGroup<T> x;
+  LineGroup<T> y;
+  ZGroup<T> z;
+  int xgrid = 0, ygrid = 0, zgrid = 0;
+  size_t xsmem = 0, ysmem = 0, zsmem = 0;
+};
+
+// which: 0 = iteration 0 (S0 -> S1), 1 = first body iteration (S1 -> S2), 2 = second (S2 -> S1).
+template <typename T>
+void group_iter_args(const std::vector<rve_s*>& hs, int which, GroupIter<T>& g) {
+  const int n = (int)hs.size();
+  for (int m = 0; m < n; ++m) {
+    rve_s* h = hs[m];
+    const Rotation r(h);
+    const int si = which == 0 ? r.s0 : (which == 1 ? r.s1 : r.s2);
+    const int so = which == 1 ? r.s2 : r.s1;
+    const int pi = which == 0 ? r.p0 : (which == 1 ? r.p1 : r.p2);
+    const int po = which == 1 ? r.p2 : r.p1;
+    g.x.m[m] = x_args<T>(h, h->spec[si], h->spec[so], -1);
+    g.x.start[m] = g.xgrid;
+    g.x.gx[m] = h->xgrid;
+    g.xgrid += h->xgrid;
+    g.xsmem = std::max(g.xsmem, xsmem_total(h));
+    g.y.m[m] = y_args<T>(h, h->spec[so]);
+    const int ygx = (h->H + h->yHC - 1) / h->yHC;
+    g.y.start[m] = g.ygrid;
+    g.y.gx[m] = ygx;
+    g.ygrid += ygx * h->nz;
+    g.ysmem = std::max(g.ysmem, line_group_smem<T>(h->ny, h->yHC));
+    ZArgs<T> za = z_args<T>(h, h->spec[so], h->P[pi], h->P[po], -1);
+    za.has_cond = 0;  // the group guard ends the loop
+    g.z.m[m] = za;
+    const int zgx = (h->H + h->zHC - 1) / h->zHC;
+    g.z.start[m] = g.zgrid;
+    g.z.gx[m] = zgx;
+    g.zgrid += zgx * h->ny;
+    g.zsmem = std::max(g.zsmem, zgreen_group_smem<T>(h->nz, h->zHC));
+  }
+  g.x.k = g.x.m[0].k;
+  g.x.n = g.y.n = g.z.n = n;
+  g.x.start[n] = g.xgrid;
+  g.y.start[n] = g.ygrid;
+  g.z.start[n] = g.zgrid;
+}
+
+template <typename T>
+cudaError_t group_iteration(const GroupIter<T>& g, int np, cudaStream_t s) {
+  cudaError_t e = launch_xpass_group<T>(g.x, np, false, g.xgrid, g.xsmem, s);
+  if (e == cudaSuccess) e = launch_line_group<T>(g.y, -1, g.ygrid, g.ysmem, s);
+  if (e == cudaSuccess) e = launch_zgreen_group<T>(g.z, g.zgrid, g.zsmem, s);
+  if (e == cudaSuccess) e = launch_line_group<T>(g.y, +1, g.ygrid, g.ysmem, s);
+  return e;
+}
+
+struct GroupGraph {
+  std::vector<int> key;  // (index, sb, pb) of every member: the buffer rotations baked in
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+void drop_group_graph(GroupGraph& gg) {
+  if (gg.exec) cudaGraphExecDestroy(gg.exec);
+  if (gg.graph) cudaGraphDestroy(gg.graph);
+  gg.exec = nullptr;
+  gg.graph = nullptr;
+}
+
+// The graph of one increment of the group (see above), captured on cs (main graph) and cb
+// (loop body).
+template <typename T>
+cudaError_t build_group_graph(const std::vector<rve_s*>& hs, cudaStream_t cs, cudaStream_t cb, GroupGraph& out) {
+  const int n = (int)hs.size();
+  const int np = np_of(hs[0]);
+  auto it0 = std::make_unique<GroupIter<T>>();
+  auto itA = std::make_unique<GroupIter<T>>();
+  auto itB = std::make_unique<GroupIter<T>>();
+  auto cm = std::make_unique<XGroup<T>>();
+  group_iter_args<T>(hs, 0, *it0);
+  group_iter_args<T>(hs, 1, *itA);
+  group_iter_args<T>(hs, 2, *itB);
+  GuardGroup gd{};
+  gd.n = n;
+  gd.limit = 0;
+  int cgrid = 0;
+  size_t csmem = 0;
+  for (int m = 0; m < n; ++m) {
+    rve_s* h = hs[m];
+    const Rotation r(h);
+    gd.st[m] = h->st;
+    gd.limit = std::max(gd.limit, max_iter_of(h) / 2 + 2);
+    XArgs<T> ca = x_args<T>(h, h->spec[r.s0], nullptr, -1);
+    ca.pick = 1;
+    ca.cand[0] = (const C2<T>*)h->spec[r.s0];
+    ca.cand[1] = (const C2<T>*)h->spec[r.s1];
+    ca.cand[2] = (const C2<T>*)h->spec[r.s2];
+    cm->m[m] = ca;
+    cm->start[m] = cgrid;
+    cm->gx[m] = h->xgrid;
+    cgrid += h->xgrid;
+    csmem = std::max(csmem, xsmem_total(h));
+  }
+  cm->k = cm->m[0].k;
+  cm->n = n;
+  cm->start[n] = cgrid;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  if (e != cudaSuccess) return e;
+  out.graph = g;
+  cudaGraphConditionalHandle cond;
+  if ((e = cudaGraphConditionalHandleCreate(&cond, g, 1u, cudaGraphCondAssignDefault)) != cudaSuccess) return e;
+  if ((e = cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed)) != cudaSuccess)
+    return e;
+  bool body_open = false;
+  do {
+    if ((e = group_iteration<T>(*it0, np, cs)) != cudaSuccess) break;
+    if ((e = launch_group_guard<T>(gd, cond, cs)) != cudaSuccess) break;
+    cudaStreamCaptureStatus cst;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    if ((e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, nullptr, &deps, nullptr, &nd)) != cudaSuccess) break;
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t wn;
+    if ((e = cudaGraphAddNode(&wn, g, deps, nullptr, nd, &cp)) != cudaSuccess) break;
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if ((e = cudaStreamUpdateCaptureDependencies(cs, &wn, nullptr, 1, cudaStreamSetCaptureDependencies)) != cudaSuccess)
+      break;
+    if ((e = cudaStreamBeginCaptureToGraph(cb, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed)) != cudaSuccess)
+      break;
+    body_open = true;
+    if ((e = group_iteration<T>(*itA, np, cb)) != cudaSuccess) break;
+    if ((e = group_iteration<T>(*itB, np, cb)) != cudaSuccess) break;
+    if ((e = launch_group_guard<T>(gd, cond, cb)) != cudaSuccess) break;
+    cudaGraph_t bout = nullptr;
+    body_open = false;
+    if ((e = cudaStreamEndCapture(cb, &bout)) != cudaSuccess) break;
+    if ((e = launch_xpass_group<T>(*cm, np, true, cgrid, csmem, cs)) != cudaSuccess) break;
+    for (int m = 0; m < n && e == cudaSuccess; ++m)
+      e = cudaMemcpyAsync(hs[m]->st_host, hs[m]->st, sizeof(IterStatus), cudaMemcpyDeviceToHost, cs);
+  } while (false);
+  if (body_open) {
+    cudaGraph_t tmp = nullptr;
+    cudaStreamEndCapture(cb, &tmp);
+  }
+  cudaGraph_t done = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(cs, &done);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&out.exec, g, 0);
+  return e;
+}
+
+// rve_step_batch for a groupable batch: n_increments increments of every member as one
+// group on a private stream (ordered after each member's own stream and before later work
+// there).  A failing member keeps its last committed increment and leaves the group.
+template <typename T>
+rve_status step_batch_group(rve_s* const* hs, int n, int n_increments, long long* iters, int* failed) {
+  rve_status first = RVE_OK;
+  int first_i = -1;
+  auto note = [&](int i, rve_status st) {
+    if (st != RVE_OK && first == RVE_OK) {
+      first = st;
+      first_i = i;
+    }
+  };
+  cudaStream_t gs = nullptr, cap[2] = {nullptr, nullptr};
+  cudaError_t e = cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking);
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaStreamCreateWithFlags(&cap[k], cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    for (cudaStream_t q : {gs, cap[0], cap[1]})
+      if (q) cudaStreamDestroy(q);
+    return cuda_fail(nullptr, e, "group stream set-up");
+  }
+  std::vector<cudaStream_t> orig(n);
+  for (int i = 0; i < n; ++i) {
+    rve_s* h = hs[i];
+    orig[i] = h->stream;
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_sync, h->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(gs, h->ev_sync, 0);
+    h->stream = gs;
+  }
+  if (e != cudaSuccess) note(0, cuda_fail(hs[0], e, "group stream ordering"));
+  std::vector<char> active(n, first == RVE_OK ? 1 : 0);
+  std::vector<GroupGraph> cache;
+  constexpr size_t kCache = 8;
+  for (int inc = 0; inc < n_increments; ++inc) {
+    std::vector<rve_s*> cur;
+    std::vector<int> idx;
+    for (int i = 0; i < n; ++i) {
+      if (!active[i]) continue;
+      rve_status st = inc_prepare<T>(hs[i]);
+      if (st) {
+        note(i, st);
+        active[i] = 0;
+        continue;
+      }
+      cur.push_back(hs[i]);
+      idx.push_back(i);
+    }
+    if (cur.empty()) break;
+    std::vector<int> key;
+    for (size_t m = 0; m < cur.size(); ++m) key.insert(key.end(), {idx[m], cur[m]->sb, cur[m]->pb});
+    GroupGraph* gg = nullptr;
+    for (GroupGraph& c : cache)
+      if (c.key == key) gg = &c;
+    if (!gg) {
+      if (cache.size() >= kCache) {
+        drop_group_graph(cache.front());
+        cache.erase(cache.begin());
+      }
+      cache.emplace_back();
+      gg = &cache.back();
+      gg->key = key;
+      e = build_group_graph<T>(cur, cap[0], cap[1], *gg);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        drop_group_graph(*gg);
+        cache.pop_back();
+        for (int i : idx) active[i] = 0;
+        note(idx[0], cuda_fail(cur[0], e, "group graph"));
+        break;
+      }
+    }
+    e = cudaGraphLaunch(gg->exec, gs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(gs);
+    if (e != cudaSuccess) {
+      for (int i : idx) active[i] = 0;
+      note(idx[0], cuda_fail(cur[0], e, "group increment"));
+      break;
+    }
+    for (size_t m = 0; m < cur.size(); ++m) {
+      rve_s* h = cur[m];
+      const IterStatus stat = *h->st_host;
+      rve_status st = close_iterations<T>(h, stat);
+      if (st == RVE_OK) {
+        note_converged(h, stat);
+        st = finish_increment(h, iters);
+      }
+      if (st) {
+        note(idx[m], st);
+        active[idx[m]] = 0;
+      }
+    }
+  }
+  for (GroupGraph& c : cache) drop_group_graph(c);
+  for (int i = 0; i < n; ++i) {
+    rve_s* h = hs[i];
+    e = cudaEventRecord(h->ev_sync, gs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(orig[i], h->ev_sync, 0);
+    if (e != cudaSuccess) note(i, cuda_fail(h, e, "group stream join"));
+    h->stream = orig[i];
+  }
+  for (cudaStream_t q : {gs, cap[0], cap[1]}) cudaStreamDestroy(q);
+  if (failed) *failed = first_i;
+  if (first != RVE_OK) g_err = "handle " + std::to_string(first_i) + ": " + hs[first_i]->err;
+  return first;
+}
+
 // ---------------------------------------------------------------- adjoint ------------
 // Per-voxel scratch of the adjoint of one increment, in units of T per voxel.
 enum AdjSlot {
@@ -1446,6 +1738,7 @@ void rve_options_default(rve_options* o) {
   o->autotune = 1;
   o->y_tile = 0;
   o->z_tile = 0;
+  o->batch_group = 0;
 }
 
 void rve_material_default(rve_material* m) {
@@ -1604,6 +1897,9 @@ rve_status rve_step_batch(rve_t* hs, int n, int n_increments, long long* iters, 
   if (n == 0 || n_increments == 0) return RVE_OK;
   cudaError_t e = cudaSetDevice(hs[0]->opt.device);
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaSetDevice");
+  if (groupable(hs, n))
+    return hs[0]->opt.precision == RVE_FP64 ? step_batch_group<double>(hs, n, n_increments, iters, failed)
+                                            : step_batch_group<float>(hs, n, n_increments, iters, failed);
   // Each handle runs on a private stream, ordered after the work already enqueued on its
   // own stream and before anything enqueued there after this call.
   std::vector<cudaStream_t> orig(n), priv(n, nullptr);
@@ -1675,6 +1971,14 @@ rve_status rve_step_batch(rve_t* hs, int n, int n_increments, long long* iters, 
   if (failed) *failed = first_i;
   if (first != RVE_OK) g_err = "handle " + std::to_string(first_i) + ": " + hs[first_i]->err;
   return first;
+}
+
+rve_status rve_batch_grouped(rve_t* hs, int n, int* grouped) {
+  if (!grouped || n < 0 || (n > 0 && !hs)) return fail(nullptr, RVE_ERR_INVALID_ARG, "bad batch arguments");
+  for (int i = 0; i < n; ++i)
+    if (!hs[i]) return fail(nullptr, RVE_ERR_INVALID_ARG, "NULL handle in the batch");
+  *grouped = groupable(hs, n) ? 1 : 0;
+  return RVE_OK;
 }
 
 rve_status rve_adjoint_increment(rve_t h, const double* eps_prev, const double* eps_cur, const double* state_prev,

@@ -938,6 +938,11 @@ struct ZGroup {
   int n;
 };
 
+// the grouped argument blocks are passed by value: within the 32764-byte kernel-parameter limit
+static_assert(sizeof(XGroup<double>) <= 32764 && sizeof(LineGroup<double>) <= 32764 &&
+                  sizeof(ZGroup<double>) <= 32764,
+              "grouped pass arguments exceed the kernel parameter limit");
+
 template <typename T, bool COMMIT, int NP>
 __global__ void __launch_bounds__(kXThreads, XMinBlocks<T>::value) k_xpass_group(const __grid_constant__ XGroup<T> g) {
   int m;

@@ -57,6 +57,7 @@ class Options(C.Structure):
         ("autotune", C.c_int),
         ("y_tile", C.c_int),
         ("z_tile", C.c_int),
+        ("batch_group", C.c_int),
     ]
 
 
@@ -118,7 +119,7 @@ EXPORTED = [
     "rve_set_mixed_load", "rve_step", "rve_get_effective", "rve_get_fields", "rve_save_state",
     "rve_load_state", "rve_last_error", "rve_destroy", "rve_material_point", "rve_fft_r2c",
     "rve_fft_c2r", "rve_label_voronoi", "rve_kernel_times", "rve_get_residuals", "rve_label_voronoi_noalloc",
-    "rve_step_batch", "rve_material_point_vjp", "rve_adjoint_increment", "rve_alu_probe",
+    "rve_step_batch", "rve_material_point_vjp", "rve_adjoint_increment", "rve_alu_probe", "rve_batch_grouped",
 ]
 NOALLOC_MAX_PARENTS = 4096  # RVE_NOALLOC_MAX_PARENTS of include/rve.h
 
@@ -160,6 +161,7 @@ def load_library(path: str | os.PathLike | None = None):
     lib.rve_adjoint_increment.argtypes = [vp, vp, vp, vp, C.POINTER(C.c_double), d, vp, vp, C.POINTER(C.c_double),
                                           C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
     lib.rve_alu_probe.argtypes = [i, i, i, vp, vp, C.POINTER(C.c_double)]
+    lib.rve_batch_grouped.argtypes = [C.POINTER(vp), i, C.POINTER(i)]
     for name in EXPORTED:
         getattr(lib, name).restype = C.c_int
     lib.rve_options_default.restype = None
@@ -242,7 +244,7 @@ class RVE:
 
     def __init__(self, grain_id, euler, precision=FP64, green=GREEN_WILLOT, n_sub=0, tol=1e-6, max_iter=1000,
                  fixed_iters=0, device=0, use_torch=True, timing=False, graphs=True, autotune=True, y_tile=0,
-                 z_tile=0):
+                 z_tile=0, batch_group=False):
         self.lib = load_library()
         euler = np.ascontiguousarray(np.asarray(euler, dtype=np.float64))
         shape = tuple(grain_id.shape)
@@ -257,6 +259,7 @@ class RVE:
         opt.graphs = 1 if graphs else 0
         opt.autotune = 1 if autotune else 0
         opt.y_tile, opt.z_tile = int(y_tile), int(z_tile)
+        opt.batch_group = 1 if batch_group else 0
         self._allocator = None
         on_dev = 0
         if use_torch:
@@ -387,6 +390,19 @@ def step_batch(solvers, n_increments=1) -> int:
     if st != 0:
         raise RVEError(st, lib.rve_last_error(None).decode(), index=failed.value)
     return int(it.value)
+
+
+def batch_grouped(solvers) -> bool:
+    """Whether step_batch steps these solvers as one group (one launch per pass over all
+    members) rather than on private streams (rve_batch_grouped)."""
+    solvers = list(solvers)
+    lib = load_library()
+    arr = (C.c_void_p * max(1, len(solvers)))(*[s.h for s in solvers])
+    out = C.c_int(0)
+    st = lib.rve_batch_grouped(arr, len(solvers), C.byref(out))
+    if st != 0:
+        raise RVEError(st, lib.rve_last_error(None).decode())
+    return bool(out.value)
 
 
 def material_point(R, eps_n, eps, state, dt, n_sub, precision=FP64, **material):

@@ -40,6 +40,7 @@ def test_defaults_roundtrip(lib):
 
     o = rve.default_options()
     assert (o.precision, o.green, o.n_sub, o.max_iter, o.fixed_iters, o.tol) == (0, 0, 0, 1000, 0, 1e-6)
+    assert (o.graphs, o.autotune, o.y_tile, o.z_tile, o.batch_group) == (1, 1, 0, 0, 0)
     m = rve.default_material().as_dict()
     assert m["C33"] == 178000.0 and m["eta"] == 1e4 and m["h_off"] == 1.2 and m["Kc"] == 1.45
 

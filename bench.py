@@ -664,6 +664,7 @@ def run_gpu(args):
         fp32_peak = peaks["fp32_fma_tflops"]
         kx_ms = single["kernel_avg_ms"]["xpass"]
         achieved = flops_per_voxit(N_SUB) * single["voxels"] / (kx_ms * 1e-3) / 1e12
+        derived = peaks["sms"] * 128 * 2 * 2070.0e6 / 1e12
         hbm = _measured_hbm()
         line["roofline"] = {
             "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
@@ -671,6 +672,8 @@ def run_gpu(args):
             "avg_launch_ms": kx_ms,
             "measured_in": "twinned 128^3 RVE alone (single_rve_128 leg), per-launch CUDA events on its stream",
             "peak_note": "FP32 FMA rate measured by rve_alu_probe in this run (of measured)",
+            "peak_derived": derived, "frac_of_derived": achieved / derived,
+            "peak_derived_note": f"{peaks['sms']} SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
             "algorithmic_flops_per_voxit": flops_per_voxit(N_SUB)}
         line["alu"] = {"whole_step_tflops": flops_per_voxit(N_SUB) * value / 1e12,
                        "frac_of_measured_fp32": flops_per_voxit(N_SUB) * value / 1e12 / fp32_peak}

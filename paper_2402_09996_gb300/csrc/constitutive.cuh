@@ -352,10 +352,27 @@ __device__ __forceinline__ float2 root_newton2(float2 z, float2 aa, const RootCo
   return __fmul2_rn(f2(q.Pout), __fmul2_rn(zn1, w));
 }
 
+// With a compile-time power (NP = n = nt = 10) an inactive system (a <= 0, or NaN) is solved
+// at the floor kRateFloor instead of being masked: from there the table start is
+// z ~ kRateFloor / K, whose power z^(n-1) underflows float, so the returned rate is exactly
+// 0 -- the masked form's value -- while one min replaces a compare and two selects per
+// system.  A real exponent near 1 would not underflow, so NP = -1 keeps the mask.
+constexpr float kRateFloor = 1e-30f;
+
+template <int NP>
+__device__ __forceinline__ float2 rate_arg2(float2 a) {
+  if constexpr (NP > 0) return make_float2(fmaxf(a.x, kRateFloor), fmaxf(a.y, kRateFloor));
+  else return make_float2(a.x > 0.f ? a.x : 1.f, a.y > 0.f ? a.y : 1.f);
+}
+template <int NP>
+__device__ __forceinline__ float2 rate_out2(float2 a, float2 rho) {
+  if constexpr (NP > 0) return rho;
+  else return make_float2(a.x > 0.f ? rho.x : 0.f, a.y > 0.f ? rho.y : 0.f);
+}
+
 template <int NP>
 __device__ __forceinline__ float2 reg_rate_slip2(float2 a, const RootCoef<float>& q, int n_int, const float* tab) {
-  const bool on0 = a.x > 0.f, on1 = a.y > 0.f;
-  const float2 aa = make_float2(on0 ? a.x : 1.f, on1 ? a.y : 1.f);
+  const float2 aa = rate_arg2<NP>(a);
   const float2 la = make_float2(fast_log2<float>(aa.x), fast_log2<float>(aa.y));
   const float2 t = __ffma2_rn(la, f2(q.a2), f2(q.b2));
   const float2* tb = reinterpret_cast<const float2*>(tab);
@@ -363,13 +380,12 @@ __device__ __forceinline__ float2 reg_rate_slip2(float2 a, const RootCoef<float>
   const float2 ex = __ffma2_rn(make_float2(ab0.y, ab1.y), la, make_float2(ab0.x, ab1.x));
   const float2 z = make_float2(fast_exp2<float>(ex.x), fast_exp2<float>(ex.y));
   const float2 rho = root_newton2<NP>(z, aa, q, n_int);
-  return make_float2(on0 ? rho.x : 0.f, on1 ? rho.y : 0.f);
+  return rate_out2<NP>(a, rho);
 }
 
 template <int NP>
 __device__ __forceinline__ float2 reg_rate_tab2(float2 a, const RootCoef<float>& q, int n_int, const float* tab) {
-  const bool on0 = a.x > 0.f, on1 = a.y > 0.f;
-  const float2 aa = make_float2(on0 ? a.x : 1.f, on1 ? a.y : 1.f);
+  const float2 aa = rate_arg2<NP>(a);
   const float2 la = make_float2(fast_log2<float>(aa.x), fast_log2<float>(aa.y));
   const float2 lzB = __ffma2_rn(la, f2(q.a1), f2(q.b1));
   const float2 t = __ffma2_rn(la, f2(q.a2), f2(q.b2));
@@ -378,7 +394,7 @@ __device__ __forceinline__ float2 reg_rate_tab2(float2 a, const RootCoef<float>&
   const float2 ex = __fadd2_rn(lzB, __ffma2_rn(make_float2(ab0.y, ab1.y), t, make_float2(ab0.x, ab1.x)));
   const float2 z = make_float2(fast_exp2<float>(ex.x), fast_exp2<float>(ex.y));
   const float2 rho = root_newton2<NP>(z, aa, q, n_int);
-  return make_float2(on0 ? rho.x : 0.f, on1 ? rho.y : 0.f);
+  return rate_out2<NP>(a, rho);
 }
 
 // Generic solve (any eta >= 0 and exponent n >= 1): per-system branch, a smooth-minimum

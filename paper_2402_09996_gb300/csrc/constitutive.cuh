@@ -468,6 +468,11 @@ __device__ __forceinline__ pair_t<T> pmul(pair_t<T> a, pair_t<T> b) {
   if constexpr (std::is_same<T, float>::value) return __fmul2_rn(a, b);
   else return pmk<T>(a.x * b.x, a.y * b.y);
 }
+template <typename T>
+__device__ __forceinline__ pair_t<T> padd(pair_t<T> a, pair_t<T> b) {
+  if constexpr (std::is_same<T, float>::value) return __fadd2_rn(a, b);
+  else return pmk<T>(a.x + b.x, a.y + b.y);
+}
 
 // Evaluates the rates at elastic strain e0 + s*de - yt.ep and state yt, adds
 // wacc * rates to acc and overwrites yt with y0 + cnext * rates.
@@ -512,26 +517,25 @@ __device__ __forceinline__ void rk_stage(const MatDev<T>& M, const T* e0, const 
     hooke<T>(M, e, sg);
   }
   T ex[16];
-  T Es = T(0), Et = T(0), vtw = T(0);
   const T cb_s = -M.b_s * T(kLog2e), cb_t = -M.b_b * T(kLog2e);
+  // sums of the hardening terms and twin slips, even and odd systems in the two lanes
+  pair_t<T> es2 = pmk<T>(T(0), T(0)), et2 = pmk<T>(T(0), T(0)), vt2 = pmk<T>(T(0), T(0));
 #pragma unroll
   for (int k = 0; k < 12; k += 2) {
     const pair_t<T> p = pmul<T>(pmk<T>(cb_s, cb_s), pmk<T>(yt.v[k], yt.v[k + 1]));
     ex[k] = fast_exp2<T>(p.x);
     ex[k + 1] = fast_exp2<T>(p.y);
-    Es += ex[k];
-    Es += ex[k + 1];
+    es2 = padd<T>(es2, pmk<T>(ex[k], ex[k + 1]));
   }
 #pragma unroll
   for (int k = 12; k < 16; k += 2) {
     const pair_t<T> p = pmul<T>(pmk<T>(cb_t, cb_t), pmk<T>(yt.v[k], yt.v[k + 1]));
     ex[k] = fast_exp2<T>(p.x);
     ex[k + 1] = fast_exp2<T>(p.y);
-    Et += ex[k];
-    Et += ex[k + 1];
-    vtw += yt.v[k];
-    vtw += yt.v[k + 1];
+    et2 = padd<T>(et2, pmk<T>(ex[k], ex[k + 1]));
+    vt2 = padd<T>(vt2, pmk<T>(yt.v[k], yt.v[k + 1]));
   }
+  const T Es = es2.x + es2.y, Et = et2.x + et2.y, vtw = vt2.x + vt2.y;
   const T ftot = T(1.41421356237309504880) * vtw;
   const T wslip = T(1) - ftot;
   T fm_left = M.fm - ftot;

@@ -61,10 +61,10 @@ BYTES_PER_VOXIT_FP32 = 260          # state + strain/stress traffic of the fused
 FLOPS_RHS = 1100                    # one evaluation of the constitutive right-hand side
 N_SUB = 4                           # RK4 substeps at dt = 0.5 s
 DT = 0.5
-# DRAM bytes (read + write) of one trial x-pass launch on the 128^3 FP32 workload, from ncu
-# (dram__bytes_read.sum + dram__bytes_write.sum, mean of two launches); valid for the x-pass
-# source as profiled, to be re-taken whenever that kernel changes
-XPASS_DRAM_BYTES_128 = 438_034_560
+# DRAM bytes (read + write) of one trial x-pass launch on the twinned 128^3 FP32 case, from
+# ncu (dram__bytes_read.sum + dram__bytes_write.sum, mean of three launches in the plastic
+# regime); valid for the x-pass source as profiled, to be re-taken whenever that kernel changes
+XPASS_DRAM_BYTES_128 = 435_002_965
 
 
 def flops_per_voxit(n_sub):

@@ -142,8 +142,16 @@ typedef enum {
   RVE_FIELD_EPS_P = 2,  /* plastic strain, crystal frame, 6 x nvox */
   RVE_FIELD_V = 3,      /* accumulated slip v (12 slip + 4 twin), 16 x nvox */
   RVE_FIELD_ALPHA = 4,  /* kinematic variables of the slip systems, 12 x nvox */
-  RVE_FIELD_VM = 5      /* local von Mises stress, 1 x nvox */
+  RVE_FIELD_VM = 5,     /* local von Mises stress, 1 x nvox */
+  RVE_FIELD_F = 6       /* twin volume fractions f = sqrt(2) v of the 4 twin systems (Sec. 3),
+                           4 x nvox */
 } rve_field;
+
+/* Element type of a field copy (rve_get_fields_as). */
+typedef enum {
+  RVE_DTYPE_F64 = 0, /* double */
+  RVE_DTYPE_F32 = 1  /* float (exact for the fields of an RVE_FP32 handle, rounded otherwise) */
+} rve_dtype;
 
 void rve_options_default(rve_options* opt);
 void rve_material_default(rve_material* mat);
@@ -210,7 +218,10 @@ rve_status rve_step_batch(rve_t* hs, int n, int n_increments, long long* iterati
 rve_status rve_batch_grouped(rve_t* hs, int n, int* grouped);
 
 /* Adjoint of one converged load increment n (t_{n-1} -> t_n) of a history objective J
- * (the paper defines no adjoint; this extends its method to gradients).  The increment's
+ * (the paper defines no adjoint; this extends its method to gradients).  The objective
+ * itself is the caller's: it supplies dJ/d<sigma>_n for the increment (dS) and the
+ * adjoints handed back by the later increments; the Python binding's history_gradient
+ * forms J = sum_n w_n (<sigma_zz>_n - target_n)^2 and its dS this way.  The increment's
  * converged strain solves the Green-operator fixed point (Sec. 4) with the mixed load; the
  * adjoint solves the transposed linearised problem (the same fixed point with the
  * transposed algorithmic tangent and the derivative of J as a source) and runs the
@@ -248,6 +259,10 @@ rve_status rve_get_effective(rve_t h, rve_effective* last, rve_effective* hist, 
  * doubles (dst_bytes must be >= components * nvox * 8).  dst is a host pointer,
  * or a device pointer when dst_on_device. */
 rve_status rve_get_fields(rve_t h, int which, void* dst, size_t dst_bytes, int dst_on_device);
+
+/* rve_get_fields with the element type of dst chosen by dtype (rve_dtype):
+ * dst_bytes must be >= components * nvox * (8 or 4). */
+rve_status rve_get_fields_as(rve_t h, int which, int dtype, void* dst, size_t dst_bytes, int dst_on_device);
 
 /* Checkpoint: rve_save_state with blob == NULL stores the required size in *bytes. */
 rve_status rve_save_state(rve_t h, void* blob, size_t* bytes);

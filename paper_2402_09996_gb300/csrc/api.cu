@@ -1675,9 +1675,10 @@ bool valid_grid(int nx, int ny, int nz) {
 }
 
 template <typename T>
-rve_status get_field_t(rve_s* h, int which, void* dst, size_t bytes, int on_dev) {
+rve_status get_field_t(rve_s* h, int which, int dtype, void* dst, size_t bytes, int on_dev) {
   const void* src = nullptr;
   int comps = 0;
+  double scale = 1.0;
   switch (which) {
     case RVE_FIELD_STRESS: src = h->sig_n; comps = 6; break;
     case RVE_FIELD_STRAIN: src = h->eps_n; comps = 6; break;
@@ -1685,25 +1686,52 @@ rve_status get_field_t(rve_s* h, int which, void* dst, size_t bytes, int on_dev)
     case RVE_FIELD_V: src = h->v; comps = 16; break;
     case RVE_FIELD_ALPHA: src = h->al; comps = 12; break;
     case RVE_FIELD_VM: src = h->sig_n; comps = 1; break;
+    case RVE_FIELD_F:  // f = sqrt(2) v of the 4 twin systems (components 12..15 of v)
+      src = (const T*)h->v + 12 * (size_t)h->nvox;
+      comps = 4;
+      scale = 1.41421356237309504880;
+      break;
     default: return fail(h, RVE_ERR_INVALID_ARG, "unknown field");
   }
+  if (dtype != RVE_DTYPE_F64 && dtype != RVE_DTYPE_F32) return fail(h, RVE_ERR_INVALID_ARG, "unknown dtype");
   const size_t n = (size_t)comps * h->nvox;
-  if (!dst || bytes < n * sizeof(double)) return fail(h, RVE_ERR_INVALID_ARG, "destination too small");
+  const size_t elem = dtype == RVE_DTYPE_F64 ? sizeof(double) : sizeof(float);
+  if (!dst || bytes < n * elem) return fail(h, RVE_ERR_INVALID_ARG, "destination too small");
+  // the field in double on the device (in dst itself when it is a device double array),
+  // then narrowed and / or copied to the destination
+  const bool direct = on_dev && dtype == RVE_DTYPE_F64;
   double* out = (double*)dst;
   void* tmp = nullptr;
-  if (!on_dev) {
+  void* tmp32 = nullptr;
+  if (!direct) {
     rve_status s = dalloc(h, &tmp, n * sizeof(double));
     if (s) return s;
     out = (double*)tmp;
   }
+  if (dtype == RVE_DTYPE_F32 && !on_dev) {
+    rve_status s = dalloc(h, &tmp32, n * sizeof(float));
+    if (s) {
+      h->owned.pop_back();
+      if (h->opt.free) h->opt.free(tmp, h->opt.alloc_ctx);
+      else cudaFree(tmp);
+      return s;
+    }
+  }
   cudaError_t e = which == RVE_FIELD_VM ? launch_von_mises<T>((const T*)src, out, h->nvox, h->stream)
-                                        : launch_to_double<T>((const T*)src, out, (long long)n, h->stream);
-  if (e == cudaSuccess && !on_dev) e = cudaMemcpyAsync(dst, tmp, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+                                        : launch_to_double<T>((const T*)src, out, (long long)n, h->stream, scale);
+  if (dtype == RVE_DTYPE_F32) {
+    float* f32 = on_dev ? (float*)dst : (float*)tmp32;
+    if (e == cudaSuccess) e = launch_to_float<T>(out, f32, (long long)n, h->stream);
+    if (e == cudaSuccess && !on_dev) e = cudaMemcpyAsync(dst, f32, n * sizeof(float), cudaMemcpyDeviceToHost, h->stream);
+  } else if (e == cudaSuccess && !on_dev) {
+    e = cudaMemcpyAsync(dst, tmp, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  if (tmp) {
+  for (void* t : {tmp32, tmp}) {  // the last allocations first, as dalloc recorded them
+    if (!t) continue;
     h->owned.pop_back();
-    if (h->opt.free) h->opt.free(tmp, h->opt.alloc_ctx);
-    else cudaFree(tmp);
+    if (h->opt.free) h->opt.free(t, h->opt.alloc_ctx);
+    else cudaFree(t);
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "get_fields");
   return RVE_OK;
@@ -2012,12 +2040,16 @@ rve_status rve_get_effective(rve_t h, rve_effective* last, rve_effective* hist, 
   return RVE_OK;
 }
 
-rve_status rve_get_fields(rve_t h, int which, void* dst, size_t bytes, int on_dev) {
+rve_status rve_get_fields_as(rve_t h, int which, int dtype, void* dst, size_t bytes, int on_dev) {
   if (!h) return fail(h, RVE_ERR_INVALID_ARG, "NULL handle");
   cudaError_t e = cudaSetDevice(h->opt.device);
   if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
-  return h->opt.precision == RVE_FP64 ? get_field_t<double>(h, which, dst, bytes, on_dev)
-                                      : get_field_t<float>(h, which, dst, bytes, on_dev);
+  return h->opt.precision == RVE_FP64 ? get_field_t<double>(h, which, dtype, dst, bytes, on_dev)
+                                      : get_field_t<float>(h, which, dtype, dst, bytes, on_dev);
+}
+
+rve_status rve_get_fields(rve_t h, int which, void* dst, size_t bytes, int on_dev) {
+  return rve_get_fields_as(h, which, RVE_DTYPE_F64, dst, bytes, on_dev);
 }
 
 rve_status rve_save_state(rve_t h, void* blob, size_t* bytes) {

@@ -267,17 +267,33 @@ cudaError_t launch_loop_guard(IterStatus* st, int limit, cudaGraphConditionalHan
   return cudaGetLastError();
 }
 
+// dst = scale * src in double (scale 1: an exact widening copy)
 template <typename T>
-__global__ void k_to_double(const T* __restrict__ src, double* __restrict__ dst, long long n) {
+__global__ void k_to_double(const T* __restrict__ src, double* __restrict__ dst, long long n, double scale) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) dst[i] = (double)src[i];
+  if (i < n) dst[i] = (double)src[i] * scale;
 }
 
 template <typename T>
-cudaError_t launch_to_double(const T* src, double* dst, long long n, cudaStream_t s) {
+cudaError_t launch_to_double(const T* src, double* dst, long long n, cudaStream_t s, double scale) {
   if (n <= 0) return cudaSuccess;
   const int thr = 256;
-  k_to_double<T><<<(unsigned)((n + thr - 1) / thr), thr, 0, s>>>(src, dst, n);
+  k_to_double<T><<<(unsigned)((n + thr - 1) / thr), thr, 0, s>>>(src, dst, n, scale);
+  return cudaGetLastError();
+}
+
+// double -> float (round to nearest)
+template <typename T>
+__global__ void k_to_float(const double* __restrict__ src, float* __restrict__ dst, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = (float)src[i];
+}
+
+template <typename T>
+cudaError_t launch_to_float(const double* src, float* dst, long long n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int thr = 256;
+  k_to_float<T><<<(unsigned)((n + thr - 1) / thr), thr, 0, s>>>(src, dst, n);
   return cudaGetLastError();
 }
 
@@ -470,7 +486,8 @@ cudaError_t launch_adj(int which, long long n, cudaStream_t s, const void* p0, c
   template cudaError_t launch_zgreen<T>(const ZArgs<T>&, dim3, size_t, cudaStream_t);                             \
   template cudaError_t launch_shift<T>(C2<T>*, C2<T>*, long long, int, const double*, bool, cudaStream_t);        \
   template cudaError_t launch_xfft<T>(const XFftArgs<T>&, int, dim3, size_t, cudaStream_t);                       \
-  template cudaError_t launch_to_double<T>(const T*, double*, long long, cudaStream_t);                           \
+  template cudaError_t launch_to_double<T>(const T*, double*, long long, cudaStream_t, double);                   \
+  template cudaError_t launch_to_float<T>(const double*, float*, long long, cudaStream_t);                          \
   template cudaError_t launch_von_mises<T>(const T*, double*, long long, cudaStream_t);                          \
   template cudaError_t launch_loop_guard<T>(IterStatus*, int, cudaGraphConditionalHandle, cudaStream_t);           \
   template cudaError_t launch_adj<T>(int, long long, cudaStream_t, const void*, const void*, const void*, void*,   \

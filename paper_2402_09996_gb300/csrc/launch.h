@@ -115,7 +115,9 @@ cudaError_t launch_shift(C2<T>* spec, C2<T>* backup, long long NL, int H, const 
 template <typename T>
 cudaError_t launch_xfft(const XFftArgs<T>& a, int sign, dim3 grid, size_t smem, cudaStream_t s);
 template <typename T>
-cudaError_t launch_to_double(const T* src, double* dst, long long n, cudaStream_t s);
+cudaError_t launch_to_double(const T* src, double* dst, long long n, cudaStream_t s, double scale = 1.0);
+template <typename T>
+cudaError_t launch_to_float(const double* src, float* dst, long long n, cudaStream_t s);
 template <typename T>
 cudaError_t launch_von_mises(const T* sig6, double* dst, long long nvox, cudaStream_t s);
 template <typename T>

@@ -20,8 +20,10 @@ LIB_PATH = _PKG / "librve.so"
 
 FP64, FP32 = 0, 1
 GREEN_WILLOT, GREEN_MS = 0, 1
-FIELD_STRESS, FIELD_STRAIN, FIELD_EPS_P, FIELD_V, FIELD_ALPHA, FIELD_VM = range(6)
-FIELD_COMPONENTS = {FIELD_STRESS: 6, FIELD_STRAIN: 6, FIELD_EPS_P: 6, FIELD_V: 16, FIELD_ALPHA: 12, FIELD_VM: 1}
+FIELD_STRESS, FIELD_STRAIN, FIELD_EPS_P, FIELD_V, FIELD_ALPHA, FIELD_VM, FIELD_F = range(7)
+FIELD_COMPONENTS = {FIELD_STRESS: 6, FIELD_STRAIN: 6, FIELD_EPS_P: 6, FIELD_V: 16, FIELD_ALPHA: 12, FIELD_VM: 1,
+                    FIELD_F: 4}
+DTYPE_F64, DTYPE_F32 = 0, 1
 KERNELS = ["xpass", "yfwd", "zgreen", "yinv", "commit", "shift", "idle"]
 STATUS = {
     0: "RVE_OK",
@@ -120,6 +122,7 @@ EXPORTED = [
     "rve_load_state", "rve_last_error", "rve_destroy", "rve_material_point", "rve_fft_r2c",
     "rve_fft_c2r", "rve_label_voronoi", "rve_kernel_times", "rve_get_residuals", "rve_label_voronoi_noalloc",
     "rve_step_batch", "rve_material_point_vjp", "rve_adjoint_increment", "rve_alu_probe", "rve_batch_grouped",
+    "rve_get_fields_as",
 ]
 NOALLOC_MAX_PARENTS = 4096  # RVE_NOALLOC_MAX_PARENTS of include/rve.h
 
@@ -142,6 +145,7 @@ def load_library(path: str | os.PathLike | None = None):
     lib.rve_step.argtypes = [vp, i, C.POINTER(C.c_longlong)]
     lib.rve_get_effective.argtypes = [vp, C.POINTER(Effective), C.POINTER(Effective), i, C.POINTER(i)]
     lib.rve_get_fields.argtypes = [vp, i, vp, sz, i]
+    lib.rve_get_fields_as.argtypes = [vp, i, i, vp, sz, i]
     lib.rve_save_state.argtypes = [vp, vp, C.POINTER(sz)]
     lib.rve_load_state.argtypes = [vp, vp, sz]
     lib.rve_last_error.argtypes = [vp]
@@ -318,16 +322,19 @@ class RVE:
         _check(self.lib.rve_get_effective(self.h, None, arr, n.value, None), self.h)
         return [arr[i].as_dict() for i in range(n.value)]
 
-    def field(self, which: int, out=None):
-        """Committed field as float64 (components, nz, ny, nx); `out` may be a CUDA tensor."""
+    def field(self, which: int, out=None, dtype=np.float64):
+        """Committed field (components, nz, ny, nx) as float64 or float32 (`dtype`); `out`
+        may be a CUDA tensor of that type."""
         comps = FIELD_COMPONENTS[which]
+        single = np.dtype(dtype) == np.float32 if out is None else str(out.dtype) in ("torch.float32", "float32")
         if out is None:
-            out = np.empty((comps,) + self.shape, dtype=np.float64)
+            out = np.empty((comps,) + self.shape, dtype=np.float32 if single else np.float64)
             dev = 0
         else:
             dev = 1 if getattr(out, "is_cuda", False) else 0
-        nbytes = comps * self.nvox * 8
-        _check(self.lib.rve_get_fields(self.h, which, _ptr(out), nbytes, dev), self.h)
+        nbytes = comps * self.nvox * (4 if single else 8)
+        _check(self.lib.rve_get_fields_as(self.h, which, DTYPE_F32 if single else DTYPE_F64, _ptr(out), nbytes, dev),
+               self.h)
         return out
 
     def residuals(self):

@@ -218,6 +218,37 @@ def test_nan_in_loaded_state_is_reported_and_committed_state_kept(lib, cuda, pre
         _compare_histories(got, ref.history, 1e-9)
 
 
+def test_twin_fraction_field_and_typed_copies(lib, cuda):
+    """RVE_FIELD_F is the twin volume fraction f = sqrt(2) v of the 4 twin systems (Sec. 3);
+    float copies (rve_get_fields_as) are the round-to-nearest of the double copies (exact
+    for an FP32 handle), to host or device memory alike."""
+    import torch
+
+    from paper_2402_09996_gb300 import inputs, rve
+
+    inp = inputs.make_inputs((12, 10, 16), 6, 1.0, seed=3)
+    gid = label_rve(inp)
+    for P in (rve.FP32, rve.FP64):
+        with _rve(gid, inp.euler, precision=P) as s:
+            s.set_mixed_load(dt=1.0)
+            s.step(4)
+            v = s.field(rve.FIELD_V)
+            f = s.field(rve.FIELD_F)
+            assert f.shape == (4,) + gid.shape and np.any(f > 0.0)
+            assert np.array_equal(f, np.sqrt(2.0) * v[12:])
+            assert abs(np.mean(f) - s.history()[-1]["mean_f"]) <= 1e-6 * np.mean(f)
+            for which in (rve.FIELD_STRESS, rve.FIELD_V, rve.FIELD_VM, rve.FIELD_F):
+                d64 = s.field(which)
+                d32 = s.field(which, dtype=np.float32)
+                assert d32.dtype == np.float32 and np.array_equal(d32, d64.astype(np.float32))
+                dev = torch.empty(d32.shape, dtype=torch.float32, device=cuda)
+                s.field(which, out=dev)
+                assert np.array_equal(dev.cpu().numpy(), d32)
+            with pytest.raises(rve.RVEError):  # too small a destination
+                rve._check(s.lib.rve_get_fields_as(s.h, rve.FIELD_F, rve.DTYPE_F32,
+                                                   rve._ptr(np.empty(4, np.float32)), 16, 0), s.h)
+
+
 def test_invalid_arguments(lib, cuda):
     from paper_2402_09996_gb300 import rve
 

@@ -92,6 +92,11 @@ typedef struct {
   int batch_group;    /* nonzero: rve_step_batch may step this handle in a group (one
                          launch per pass over all members); 0 (default) keeps it on its own
                          stream.  See rve_step_batch. */
+  double c0_lambda, c0_mu; /* isotropic reference medium of the Green operator [MPa].  c0_mu > 0
+                         (with 3 c0_lambda + 2 c0_mu > 0) sets it; 0, 0 (default) takes
+                         3 k0 = 2 mu0 = (smallest + largest Mandel eigenvalue of C) / 2.  The
+                         converged solution does not depend on it; the convergence rate does
+                         (too soft a medium does not converge). */
 } rve_options;
 
 /* Kernel kinds reported by rve_kernel_times. */

@@ -502,6 +502,7 @@ class Options:
     max_iter: int = 500
     fixed_iters: int = 0          # > 0: exactly this many iterations per increment
     scheme: str = "willot"
+    c0: tuple | None = None       # (lam0, mu0) of the reference medium; None: reference_medium
 
 
 def _voigt6_to_tensor(v6):
@@ -535,7 +536,7 @@ class OracleRVE:
         self.opts = opts or Options()
         self.law = Constitutive(self.mat)
         self.R = bunge_rotation(np.asarray(euler, dtype=np.float64))[self.gid.reshape(-1)]   # (V,3,3)
-        self.lam0, self.mu0 = reference_medium(self.mat)
+        self.lam0, self.mu0 = self.opts.c0 if self.opts.c0 is not None else reference_medium(self.mat)
         self.C0 = isotropic_tensor(self.lam0, self.mu0)
         self.kappa = wave_vectors(self.shape, self.opts.scheme)
         V = self.N

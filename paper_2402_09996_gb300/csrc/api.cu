@@ -16,6 +16,8 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/rve.h"
 #include "launch.h"
 #include "solver_kernels.cuh"
@@ -156,6 +158,17 @@ void reference_medium(const rve_material& m, double* lam0, double* mu0) {
   *lam0 = two_mu / 3.0 - 2.0 * (*mu0) / 3.0;
 }
 
+// The handle's reference medium: the caller's (opt.c0_lambda, opt.c0_mu) when c0_mu > 0,
+// else reference_medium's rule.
+void set_reference_medium(const rve_options& o, const rve_material& m, double* lam0, double* mu0) {
+  if (o.c0_mu > 0.0) {
+    *lam0 = o.c0_lambda;
+    *mu0 = o.c0_mu;
+  } else {
+    reference_medium(m, lam0, mu0);
+  }
+}
+
 void c0_mandel(double lam, double mu, double M[36]) {
   std::memset(M, 0, 36 * sizeof(double));
   for (int i = 0; i < 3; ++i)
@@ -278,6 +291,16 @@ struct rve_s {
 };
 
 namespace {
+
+// A named NVTX range over a scope (an increment, a batch, an adjoint increment): profilers
+// attach the kernels launched inside it to the name (ncu --nvtx, nsys); without an
+// attached tool a push or pop does nothing.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 rve_status fail(rve_s* h, rve_status s, const std::string& msg) {
   if (h) h->err = msg;
@@ -1183,6 +1206,7 @@ rve_status inc_advance_any(rve_s* h, bool* finished, long long* iters) {
 
 // One increment on the handle's stream, waiting for each phase.
 rve_status step_one(rve_s* h, long long* iters) {
+  NvtxRange range("rve increment");
   rve_status st = inc_begin_any(h);
   bool finished = st != RVE_OK;
   while (!finished) {
@@ -1429,6 +1453,7 @@ rve_status step_batch_group(rve_s* const* hs, int n, int n_increments, long long
       idx.push_back(i);
     }
     if (cur.empty()) break;
+    NvtxRange range("rve group increment");
     std::vector<int> key;
     for (size_t m = 0; m < cur.size(); ++m) key.insert(key.end(), {idx[m], cur[m]->sb, cur[m]->pb});
     GroupGraph* gg = nullptr;
@@ -1782,6 +1807,7 @@ void rve_material_default(rve_material* m) {
 
 rve_status rve_create(rve_t* out, int nx, int ny, int nz, const uint32_t* grain_id, int grain_id_on_device,
                       int n_grains, const double* euler, const rve_options* opt) {
+  NvtxRange range("rve_create");
   if (!out) return fail(nullptr, RVE_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (!grain_id || !euler || n_grains < 1) return fail(nullptr, RVE_ERR_INVALID_ARG, "need grain_id, euler, n_grains >= 1");
@@ -1796,6 +1822,9 @@ rve_status rve_create(rve_t* out, int nx, int ny, int nz, const uint32_t* grain_
   if (o.green != RVE_GREEN_WILLOT && o.green != RVE_GREEN_MS) return fail(nullptr, RVE_ERR_INVALID_ARG, "bad green");
   if (o.n_sub < 0 || o.fixed_iters < 0 || o.max_iter < 0 || !(o.tol > 0)) return fail(nullptr, RVE_ERR_INVALID_ARG, "bad options");
   if ((o.alloc == nullptr) != (o.free == nullptr)) return fail(nullptr, RVE_ERR_INVALID_ARG, "alloc and free go together");
+  if ((o.c0_mu != 0.0 || o.c0_lambda != 0.0) &&
+      !(std::isfinite(o.c0_mu) && std::isfinite(o.c0_lambda) && o.c0_mu > 0.0 && 3.0 * o.c0_lambda + 2.0 * o.c0_mu > 0.0))
+    return fail(nullptr, RVE_ERR_INVALID_ARG, "the reference medium needs c0_mu > 0 and 3 c0_lambda + 2 c0_mu > 0");
   for (long long i = 0; i < 3LL * n_grains; ++i)
     if (!std::isfinite(euler[i])) return fail(nullptr, RVE_ERR_INVALID_ARG, "euler angle not finite");
   int ndev = 0;
@@ -1822,7 +1851,7 @@ rve_status rve_create(rve_t* out, int nx, int ny, int nz, const uint32_t* grain_
   factor_radices(ny, &h->dy);
   factor_radices(nz, &h->dz);
   h->euler.assign(euler, euler + 3LL * n_grains);
-  reference_medium(h->mat, &h->lam0, &h->mu0);
+  set_reference_medium(h->opt, h->mat, &h->lam0, &h->mu0);
   rve_status s;
   // grain map: validate on the host copy
   std::vector<uint32_t> gid((size_t)h->nvox);
@@ -1870,7 +1899,7 @@ rve_status rve_set_material(rve_t h, const rve_material* m) {
   rve_status s = check_material(h, *m);
   if (s) return s;
   h->mat = *m;
-  reference_medium(h->mat, &h->lam0, &h->mu0);
+  set_reference_medium(h->opt, h->mat, &h->lam0, &h->mu0);
   drop_graphs(h);  // the material is baked into the increment graphs
   return h->opt.precision == RVE_FP64 ? upload_root_tab<double>(h) : upload_root_tab<float>(h);
 }
@@ -1912,6 +1941,7 @@ rve_status rve_step(rve_t h, int n, long long* iters) {
 }
 
 rve_status rve_step_batch(rve_t* hs, int n, int n_increments, long long* iters, int* failed) {
+  NvtxRange range("rve_step_batch");
   if (failed) *failed = -1;
   if (iters) *iters = 0;
   if (n < 0 || n_increments < 0 || (n > 0 && !hs)) return fail(nullptr, RVE_ERR_INVALID_ARG, "bad batch arguments");
@@ -2012,6 +2042,7 @@ rve_status rve_batch_grouped(rve_t* hs, int n, int* grouped) {
 rve_status rve_adjoint_increment(rve_t h, const double* eps_prev, const double* eps_cur, const double* state_prev,
                                  const double dS[6], double dt, double* state_b, double* eps_b, double* param_grad,
                                  double* euler_grad, long long* iterations_out) {
+  NvtxRange range("rve_adjoint_increment");
   if (!h) return fail(h, RVE_ERR_INVALID_ARG, "NULL handle");
   if (!eps_prev || !eps_cur || !state_prev || !dS || !state_b || !eps_b || !param_grad || !euler_grad ||
       !(dt > 0))

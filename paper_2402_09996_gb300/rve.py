@@ -60,6 +60,8 @@ class Options(C.Structure):
         ("y_tile", C.c_int),
         ("z_tile", C.c_int),
         ("batch_group", C.c_int),
+        ("c0_lambda", C.c_double),
+        ("c0_mu", C.c_double),
     ]
 
 
@@ -248,7 +250,7 @@ class RVE:
 
     def __init__(self, grain_id, euler, precision=FP64, green=GREEN_WILLOT, n_sub=0, tol=1e-6, max_iter=1000,
                  fixed_iters=0, device=0, use_torch=True, timing=False, graphs=True, autotune=True, y_tile=0,
-                 z_tile=0, batch_group=False):
+                 z_tile=0, batch_group=False, c0=None):
         self.lib = load_library()
         euler = np.ascontiguousarray(np.asarray(euler, dtype=np.float64))
         shape = tuple(grain_id.shape)
@@ -264,6 +266,8 @@ class RVE:
         opt.autotune = 1 if autotune else 0
         opt.y_tile, opt.z_tile = int(y_tile), int(z_tile)
         opt.batch_group = 1 if batch_group else 0
+        if c0 is not None:  # (lambda0, mu0) of the reference medium [MPa]
+            opt.c0_lambda, opt.c0_mu = float(c0[0]), float(c0[1])
         self._allocator = None
         on_dev = 0
         if use_torch:

@@ -249,6 +249,37 @@ def test_twin_fraction_field_and_typed_copies(lib, cuda):
                                                    rve._ptr(np.empty(4, np.float32)), 16, 0), s.h)
 
 
+def test_user_reference_medium_matches_oracle(lib, cuda):
+    """A caller-chosen reference medium C0 (rve_options c0_lambda, c0_mu): the FP64 solve
+    equals the oracle run with the same C0 iteration by iteration (fixed count, 1e-9), and
+    in tolerance mode it converges to the default-C0 solution at another rate."""
+    from paper_2402_09996_gb300 import inputs, rve
+
+    inp = inputs.make_inputs((12, 10, 6), 5, 0.5, seed=42)
+    gid = label_rve(inp)
+    c0 = (50000.0, 150000.0)
+    with _rve(gid, inp.euler, fixed_iters=8, c0=c0) as s:
+        s.set_mixed_load(dt=0.5)
+        s.step(3)
+        got = s.history()
+    ref = _oracle(gid, inp.euler, fixed_iters=8, c0=c0)
+    ref.set_load(orc.Load(dt=0.5))
+    ref.run(3)
+    _compare_histories(got, ref.history, 1e-9)
+    hs = {}
+    for key, opt in (("default", None), ("c0", c0)):
+        with _rve(gid, inp.euler, tol=1e-10, max_iter=3000, c0=opt) as s:
+            s.set_mixed_load(dt=0.5)
+            s.step(3)
+            hs[key] = s.history()
+    for a, b in zip(hs["c0"], hs["default"]):
+        assert np.max(np.abs(a["S"] - b["S"])) < 1e-8 * np.max(np.abs(b["S"]))
+    assert [h["iterations"] for h in hs["c0"]] != [h["iterations"] for h in hs["default"]]
+    with pytest.raises(rve.RVEError) as ei:
+        _rve(gid, inp.euler, c0=(0.0, -1.0))
+    assert ei.value.status == rve.STATUS_CODES["RVE_ERR_INVALID_ARG"]
+
+
 def test_invalid_arguments(lib, cuda):
     from paper_2402_09996_gb300 import rve
 

@@ -93,6 +93,29 @@ def test_elastic_laminate_closed_form(scheme):
     assert abs(rec["S"][2] - x[9]) < 1e-8
 
 
+@pytest.mark.parametrize("c0", [(50000.0, 150000.0), (0.0, 250000.0), (30000.0, 120000.0)])
+def test_laminate_solution_does_not_depend_on_the_reference_medium(c0):
+    """The fixed point's solution is fixed by equilibrium and compatibility, not by C0:
+    any admissible isotropic reference medium reaches the laminate's closed-form response
+    (the default-C0 run, itself pinned to the closed form above), only at another rate."""
+    nz = 8
+    gid = np.zeros((nz, 4, 4), dtype=np.int64)
+    gid[nz // 2:] = 1
+    euler = np.array([[0.3, 0.9, 1.7], [2.1, 1.2, 0.4]])
+    mat = orc.Material(**ELASTIC)
+    runs = {}
+    for key, opt in (("default", None), ("c0", c0)):
+        rve = orc.OracleRVE(gid, euler, mat, orc.Options(tol=1e-12, c0=opt, max_iter=2000))
+        rve.set_load(orc.Load(dt=1.0))
+        rec = rve.step()
+        runs[key] = (rec, rve.fields()["sigma"], (rve.lam0, rve.mu0))
+    (r0, s0, m0), (r1, s1, m1) = runs["default"], runs["c0"]
+    assert m1 == c0 and m0 != c0
+    assert np.max(np.abs(r1["S"] - r0["S"])) < 1e-10 * abs(r0["S"][2])
+    assert np.max(np.abs(s1 - s0)) < 1e-9 * np.max(np.abs(s0))
+    assert r1["iterations"] != r0["iterations"]
+
+
 def test_mean_strain_is_prescribed_and_stress_constraint_met():
     rng = np.random.default_rng(9)
     gid = rng.integers(0, 3, size=(4, 6, 8))

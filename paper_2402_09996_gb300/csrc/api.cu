@@ -232,6 +232,7 @@ struct rve_s {
   void* backup = nullptr;
   double* dhist = nullptr;  // device (e_eq, c_F) history, 2 * max_iter
   void *ep = nullptr, *v = nullptr, *al = nullptr, *eps_n = nullptr, *sig_n = nullptr;
+  unsigned char* flow = nullptr;  // x pass: per warp of 32 voxels, flowed in iteration 0 (XArgs::flow)
   uint32_t* grain = nullptr;
   void* Rg = nullptr;
   void* root_tab = nullptr;  // kRootTabs rate-root table values (slip systems, twin exponent)
@@ -427,6 +428,9 @@ MatDev<T> make_mat(const rve_s* h) {
   M.lg_K = (T)std::log2(m.K);
   M.lg_Kt = (T)std::log2(m.Kt);
   M.lg_eta = (T)(m.eta > 0 ? std::log2(m.eta) : 0.0);
+  const double sc = 1.0 / std::sqrt(6.0);
+  M.C11s = (T)(m.C11 * sc); M.C12s = (T)(m.C12 * sc); M.C13s = (T)(m.C13 * sc); M.C33s = (T)(m.C33 * sc);
+  M.C44s2 = (T)(2.0 * m.C44 * sc); M.C66s2 = (T)(2.0 * m.C66 * sc);
   return M;
 }
 
@@ -540,6 +544,11 @@ rve_status alloc_fields(rve_s* h) {
   for (auto& f : fl) {
     if ((s = dalloc(h, f.p, fld * f.comps))) return s;
     RVE_CUDA(h, cudaMemsetAsync(*f.p, 0, fld * f.comps, h->stream));
+  }
+  {
+    const size_t nflow = (size_t)(h->nvox + 31) / 32;
+    if ((s = dalloc(h, (void**)&h->flow, nflow))) return s;
+    RVE_CUDA(h, cudaMemsetAsync(h->flow, 0, nflow, h->stream));
   }
   // launch geometry
   // x lines per CTA: enough to give every thread a voxel, up to 4 voxels per thread (a
@@ -656,6 +665,7 @@ XArgs<T> x_args(rve_s* h, const void* in, void* out, int it) {
   a.ep = (T*)h->ep; a.v = (T*)h->v; a.al = (T*)h->al; a.eps_n = (T*)h->eps_n; a.sig_n = (T*)h->sig_n;
   a.grain = h->grain;
   a.Rg = (const T*)h->Rg;
+  a.flow = h->flow;
   a.k.root_tab = (const T*)h->root_tab;
   a.k.M = make_mat<T>(h);
   if (h->lin_mode) {
@@ -796,7 +806,8 @@ struct Rotation {
 int max_iter_of(const rve_s* h) { return h->opt.max_iter > 0 ? h->opt.max_iter : 1000; }
 
 int np_of(const rve_s* h) {
-  return h->lin_mode ? kLinearLaw : rate_variant(h->mat.eta, is_small_int(h->mat.n), is_small_int(h->mat.nt));
+  const rve_material& m = h->mat;
+  return h->lin_mode ? kLinearLaw : rate_variant(m.eta, m.K, m.Kt, is_small_int(m.n), is_small_int(m.nt));
 }
 
 // One fixed-point iteration (x pass, forward y, z + Green, inverse y) on stream s:
@@ -1552,7 +1563,8 @@ rve_status adjoint_increment(rve_s* h, const double* eps_prev, const double* eps
   T* A = (T*)h->adj;
   auto at = [&](int slot) { return A + (size_t)slot * N; };
   const MatDev<T> M = make_mat<T>(h);
-  const int np = rate_variant(h->mat.eta, is_small_int(h->mat.n), is_small_int(h->mat.nt));
+  const rve_material& m = h->mat;
+  const int np = rate_variant(m.eta, m.K, m.Kt, is_small_int(m.n), is_small_int(m.nt));
   const int nsub = h->opt.n_sub > 0 ? h->opt.n_sub : default_nsub(dt_n);
   if (nsub > kMaxSubVjp) return fail(h, RVE_ERR_UNSUPPORTED, "adjoint: more than 16 RK4 substeps per increment");
   const T dt = (T)dt_n;
@@ -2203,7 +2215,7 @@ rve_status rve_material_point(int precision, const rve_material* mat, long long 
   if (precision != RVE_FP64 && precision != RVE_FP32) return fail(nullptr, RVE_ERR_INVALID_ARG, "bad precision");
   cudaStream_t st = stream ? (cudaStream_t)stream : cudaStreamPerThread;
   tmp.stream = st;
-  const int np = rate_variant(mat->eta, is_small_int(mat->n), is_small_int(mat->nt));
+  const int np = rate_variant(mat->eta, mat->K, mat->Kt, is_small_int(mat->n), is_small_int(mat->nt));
   s = precision == RVE_FP64 ? upload_root_tab<double>(&tmp) : upload_root_tab<float>(&tmp);
   if (s) {
     release(&tmp);
@@ -2240,7 +2252,7 @@ rve_status rve_material_point_vjp(int precision, const rve_material* mat, long l
   if (precision != RVE_FP64 && precision != RVE_FP32) return fail(nullptr, RVE_ERR_INVALID_ARG, "bad precision");
   cudaStream_t st = stream ? (cudaStream_t)stream : cudaStreamPerThread;
   tmp.stream = st;
-  const int np = rate_variant(mat->eta, is_small_int(mat->n), is_small_int(mat->nt));
+  const int np = rate_variant(mat->eta, mat->K, mat->Kt, is_small_int(mat->n), is_small_int(mat->nt));
   s = precision == RVE_FP64 ? upload_root_tab<double>(&tmp) : upload_root_tab<float>(&tmp);
   if (s) {
     release(&tmp);

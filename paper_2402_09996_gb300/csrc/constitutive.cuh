@@ -114,6 +114,82 @@ __device__ __forceinline__ T resolved(int s, const T* g) {
   return sys_scale<T>(s) * schmid_sum<T>(s, g);
 }
 
+// Schmid algebra by slip plane.  Every system of Table 1 has a {111} normal n with
+// components +-1; systems 3p, 3p+1, 3p+2 and the twin 12+p share plane p.  For such an n and
+// any l with n . l = 0 the shear coefficients of schmid_k are the diagonal ones times a sign
+// of the plane: n2 l3 + n3 l2 = -n2 n3 (n1 l1), n1 l3 + n3 l1 = -n1 n3 (n2 l2),
+// n1 l2 + n2 l1 = -n1 n2 (n3 l3) (from n . l = 0 and n_i^2 = 1).  Hence
+//   sum_c schmid_k(s, c) x_c = sum_i (n_i l_i) S_i,  S_i = x_i + sig_i x_(i+3)  (plane sums),
+// and sum_s g_s schmid_k(s, c) puts D_i = sum_s (n_i l_i) g_s on component i and sig_i D_i
+// on component i + 3.  A slip system has one zero n_i l_i, so its resolved stress is one
+// addition of plane sums and a plane's three systems add 3 + 6 terms to a rate sum
+// instead of 12; the twins all have n_i l_i = (1, 1, -2).
+__host__ __device__ __forceinline__ constexpr int diag_k(int s, int i) { return sys_n(s, i) * sys_l(s, i); }
+__host__ __device__ __forceinline__ constexpr int plane_sig(int p, int i) {
+  return -sys_n(3 * p, (i + 1) % 3) * sys_n(3 * p, (i + 2) % 3);
+}
+// s is the first slip system of its plane with a non-zero n_i l_i
+__host__ __device__ __forceinline__ constexpr bool first_in_plane(int s, int i) {
+  return diag_k(s, i) != 0 && (s % 3 == 0 || (diag_k(s - 1, i) == 0 && (s % 3 == 1 || diag_k(s - 2, i) == 0)));
+}
+__host__ __device__ constexpr bool schmid_by_plane_holds() {
+  for (int s = 0; s < 16; ++s) {
+    const int p = s < 12 ? s / 3 : s - 12;
+    for (int i = 0; i < 3; ++i)
+      if (schmid_k(s, i + 3) != plane_sig(p, i) * diag_k(s, i) || sys_n(s, i) != sys_n(3 * p, i)) return false;
+  }
+  for (int t = 12; t < 16; ++t)
+    if (diag_k(t, 0) != 1 || diag_k(t, 1) != 1 || diag_k(t, 2) != -2) return false;
+  return true;
+}
+static_assert(schmid_by_plane_holds(), "Table 1 systems: plane factorisation of the Schmid sums");
+
+// sum_i diag_k(s, i) S_i (zero coefficients drop out, unit ones are additions)
+template <typename T>
+__device__ __forceinline__ T plane_sum(int s, const T* S) {
+  T r = T(0);
+  bool any = false;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const int k = diag_k(s, i);
+    if (k != 0) {
+      const T term = k == 1 ? S[i] : (k == -1 ? -S[i] : T(k) * S[i]);
+      r = any ? r + term : term;
+      any = true;
+    }
+  }
+  return r;
+}
+
+// Adds the rate g of slip system s to its plane's sums D; after the plane's last system
+// adds D to du (the first plane assigns).
+template <typename T>
+__device__ __forceinline__ void plane_add(int s, T g, T* D, T* du) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const int k = diag_k(s, i);
+    if (k != 0) {
+      const T term = k == 1 ? g : (k == -1 ? -g : T(k) * g);
+      if (first_in_plane(s, i)) D[i] = term;
+      else D[i] = D[i] + term;
+    }
+  }
+  if (s % 3 == 2) {
+    const int p = s / 3;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const T hi = plane_sig(p, i) > 0 ? D[i] : -D[i];
+      if (p == 0) {
+        du[i] = D[i];
+        du[i + 3] = hi;
+      } else {
+        du[i] = du[i] + D[i];
+        du[i + 3] = du[i + 3] + hi;
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------- powers -------------
 // z^n for a small positive integer known at run time (loop).
 template <typename T>
@@ -218,6 +294,7 @@ template <> struct TabNewton<double> { static constexpr int value = 3; };
 template <typename T>
 struct RootCoef {
   T Pout, c, cn, Kn, Kn_n, a1, b1, a2, b2, nm1;
+  T lo;  // argument floor of the packed float solves with a compile-time power (root_floor)
 };
 
 template <typename T>
@@ -234,7 +311,20 @@ __device__ __forceinline__ RootCoef<T> root_coef(T P, T Kn, T n, T inv_n, T lg_K
   q.a2 = (inv_n - T(1)) * T(kRootPerUnit);
   q.b2 = (lg_Kn + q.b1 + T(kRootSpan)) * T(kRootPerUnit) - T(0.5);
   q.nm1 = n - T(1);
+  q.lo = T(0);
   return q;
+}
+
+// The argument whose table coordinate is kRootIv - 1.25, i.e. 3/4 of an interval inside the
+// table's upper end (a2 < 0 for n > 1: larger arguments map to smaller coordinates).  The
+// packed solves with a compile-time power floor their arguments here, so that their table
+// index needs a lower clamp only.  At this argument the root sits on the Norton asymptote
+// 2^16 below the kink, and the rate (a/eta) u*^n is below 2^-160 whenever eta >= K (the
+// host selects this variant only then), so it rounds to exactly 0 in float: every argument
+// at or below the floor -- inactive systems (a <= 0), NaN, and the positive arguments whose
+// exact rate underflows -- returns the masked form's value 0.
+__device__ __forceinline__ float root_floor(const RootCoef<float>& q) {
+  return fast_exp2<float>(__fdividef(float(kRootIv) - 1.25f - q.b2, q.a2));
 }
 
 // z^(n-1) for the table-started Newton steps (z > 0): a compile-time product for NP > 0,
@@ -342,27 +432,44 @@ __device__ __forceinline__ float2 root_zn1_2(float2 z, const RootCoef<float>& q,
   }
 }
 
-template <int NP>
+// UNIT_P: the slip systems' prefactor P = 1 (no final scaling).
+template <int NP, bool UNIT_P = false>
 __device__ __forceinline__ float2 root_newton2(float2 z, float2 aa, const RootCoef<float>& q, int n_int) {
   const float2 zn1 = root_zn1_2<NP>(z, q, n_int);
   const float2 phi = __ffma2_rn(z, __ffma2_rn(f2(q.c), zn1, f2(q.Kn)), make_float2(-aa.x, -aa.y));
   const float2 den = __ffma2_rn(f2(q.c), zn1, f2(q.Kn_n));
   const float2 r = make_float2(fast_rcp<float>(den.x), fast_rcp<float>(den.y));
   const float2 w = __ffma2_rn(make_float2(-phi.x, -phi.y), r, z);
-  return __fmul2_rn(f2(q.Pout), __fmul2_rn(zn1, w));
+  if constexpr (UNIT_P) return __fmul2_rn(zn1, w);
+  else return __fmul2_rn(f2(q.Pout), __fmul2_rn(zn1, w));
 }
 
 // With a compile-time power (NP = n = nt = 10) an inactive system (a <= 0, or NaN) is solved
-// at the floor kRateFloor instead of being masked: from there the table start is
-// z ~ kRateFloor / K, whose power z^(n-1) underflows float, so the returned rate is exactly
-// 0 -- the masked form's value -- while one min replaces a compare and two selects per
-// system.  A real exponent near 1 would not underflow, so NP = -1 keeps the mask.
-constexpr float kRateFloor = 1e-30f;
-
+// at the floor q.lo (root_floor) instead of being masked: its rate rounds to exactly 0 --
+// the masked form's value -- while one min replaces a compare and two selects per system,
+// and the floor bounds the table coordinate from above.  A real exponent near 1 would not
+// underflow, so NP = -1 keeps the mask.
 template <int NP>
-__device__ __forceinline__ float2 rate_arg2(float2 a) {
-  if constexpr (NP > 0) return make_float2(fmaxf(a.x, kRateFloor), fmaxf(a.y, kRateFloor));
+__device__ __forceinline__ float2 rate_arg2(float2 a, float lo) {
+  if constexpr (NP > 0) return make_float2(fmaxf(a.x, lo), fmaxf(a.y, lo));
   else return make_float2(a.x > 0.f ? a.x : 1.f, a.y > 0.f ? a.y : 1.f);
+}
+
+// Table entries at the coordinates t of a pair.  NP > 0: t <= kRootIv - 1.25 (floored
+// arguments), so only the lower clamp remains; it is taken in float on t rounded at the
+// 1.5 * 2^23 binade (any t, -inf included, gives an index in [0, kRootIv - 1]), and the
+// binade's offset folds into the table address.
+template <int NP>
+__device__ __forceinline__ void tab_pair(float2 t, const float* tab, float2& ab0, float2& ab1) {
+  const float2* tb = reinterpret_cast<const float2*>(tab);
+  if constexpr (NP > 0) {
+    const float2 m = __fadd2_rn(t, f2(12582912.0f));
+    ab0 = tb[__float_as_int(fmaxf(m.x, 12582912.0f)) - 0x4B400000];
+    ab1 = tb[__float_as_int(fmaxf(m.y, 12582912.0f)) - 0x4B400000];
+  } else {
+    ab0 = tb[root_interval<float>(t.x)];
+    ab1 = tb[root_interval<float>(t.y)];
+  }
 }
 template <int NP>
 __device__ __forceinline__ float2 rate_out2(float2 a, float2 rho) {
@@ -372,26 +479,27 @@ __device__ __forceinline__ float2 rate_out2(float2 a, float2 rho) {
 
 template <int NP>
 __device__ __forceinline__ float2 reg_rate_slip2(float2 a, const RootCoef<float>& q, int n_int, const float* tab) {
-  const float2 aa = rate_arg2<NP>(a);
+  const float2 aa = rate_arg2<NP>(a, q.lo);
   const float2 la = make_float2(fast_log2<float>(aa.x), fast_log2<float>(aa.y));
   const float2 t = __ffma2_rn(la, f2(q.a2), f2(q.b2));
-  const float2* tb = reinterpret_cast<const float2*>(tab);
-  const float2 ab0 = tb[root_interval<float>(t.x)], ab1 = tb[root_interval<float>(t.y)];
-  const float2 ex = __ffma2_rn(make_float2(ab0.y, ab1.y), la, make_float2(ab0.x, ab1.x));
+  float2 ab0, ab1;
+  tab_pair<NP>(t, tab, ab0, ab1);
+  // one FMA per lane: the two systems' table entries are not an operand pair
+  const float2 ex = make_float2(fmaf(ab0.y, la.x, ab0.x), fmaf(ab1.y, la.y, ab1.x));
   const float2 z = make_float2(fast_exp2<float>(ex.x), fast_exp2<float>(ex.y));
-  const float2 rho = root_newton2<NP>(z, aa, q, n_int);
+  const float2 rho = root_newton2<NP, true>(z, aa, q, n_int);
   return rate_out2<NP>(a, rho);
 }
 
 template <int NP>
 __device__ __forceinline__ float2 reg_rate_tab2(float2 a, const RootCoef<float>& q, int n_int, const float* tab) {
-  const float2 aa = rate_arg2<NP>(a);
+  const float2 aa = rate_arg2<NP>(a, q.lo);
   const float2 la = make_float2(fast_log2<float>(aa.x), fast_log2<float>(aa.y));
   const float2 lzB = __ffma2_rn(la, f2(q.a1), f2(q.b1));
   const float2 t = __ffma2_rn(la, f2(q.a2), f2(q.b2));
-  const float2* tb = reinterpret_cast<const float2*>(tab);
-  const float2 ab0 = tb[root_interval<float>(t.x)], ab1 = tb[root_interval<float>(t.y)];
-  const float2 ex = __fadd2_rn(lzB, __ffma2_rn(make_float2(ab0.y, ab1.y), t, make_float2(ab0.x, ab1.x)));
+  float2 ab0, ab1;
+  tab_pair<NP>(t, tab, ab0, ab1);
+  const float2 ex = __fadd2_rn(lzB, make_float2(fmaf(ab0.y, t.x, ab0.x), fmaf(ab1.y, t.y, ab1.x)));
   const float2 z = make_float2(fast_exp2<float>(ex.x), fast_exp2<float>(ex.y));
   const float2 rho = root_newton2<NP>(z, aa, q, n_int);
   return rate_out2<NP>(a, rho);
@@ -475,7 +583,9 @@ __device__ __forceinline__ pair_t<T> padd(pair_t<T> a, pair_t<T> b) {
 }
 
 // Evaluates the rates at elastic strain e0 + s*de - yt.ep and state yt, adds
-// wacc * rates to acc and overwrites yt with y0 + cnext * rates.
+// wacc * rates to acc and overwrites yt with y0 + cnext * rates.  FIRST (the first stage of
+// a substep, wacc = 1): the input state is y0 and acc is assigned the rates, so neither the
+// copy yt = y0 nor the zeroing of acc is needed.
 // tab: the rate-root tables (slip systems' at 0, twin exponent's at kRootTabLen), NP != 0 only.
 // The systems go in pairs (k, k + 1): both are resolved, solved and folded into acc / yt
 // before the next pair (yt.v and yt.al of a pair are read before they are overwritten;
@@ -485,36 +595,44 @@ __device__ __forceinline__ pair_t<T> padd(pair_t<T> a, pair_t<T> b) {
 // keeps fewer values live than solving all 16 systems first.
 // Rewritten forms (same quantities): with e_k = exp(-b v_k) = 1 - g_k,
 //   r_k = r0_k + Q (h_off sum g + (h_diag - h_off) g_k) = (r0_k + Q (h_off (N - sum e) + dq)) - Q dq e_k;
-// the slip stresses share the Schmid scale 1/sqrt6 (applied once to sigma), and the
-// plastic strain rate is summed with integer Schmid coefficients, scaled once at the end.
-template <typename T, int NP>
+// the slip systems' Schmid scale 1/sqrt6 is folded into the moduli (MatDev C*s, the stress
+// itself is not formed), the resolved stresses and the plastic strain rate go through the
+// plane sums (plane_sum, plane_add), and the rate sums are scaled once at the end.
+template <typename T, int NP, bool FIRST = false>
 __device__ __forceinline__ void rk_stage(const MatDev<T>& M, const T* e0, const T* de, T s,
                                          const MPState<T>& y0, MPState<T>& yt, MPState<T>& acc, T wacc,
                                          T cnext, const T* tab) {
   constexpr double kLog2e = 1.44269504088896340736;
-  T e[6], sg[6];
+  // the stage's input state: y0 in the first stage (so yt needs no copy of it), yt after
+  const MPState<T>& yin = FIRST ? y0 : yt;
+  // e = e0 + s de - eps_p and the slip-scaled stress ss = C : e / sqrt6 (MatDev's C*s)
+  T e[6], ss[6];
   if constexpr (std::is_same<T, float>::value) {
-    // e = e0 + s de - eps_p and sigma = C : e on packed pairs
 #pragma unroll
     for (int c = 0; c < 6; c += 2) {
       const pair_t<T> ec = pfma<T>(pmk<T>(s, s), pmk<T>(de[c], de[c + 1]), pmk<T>(e0[c], e0[c + 1]));
-      e[c] = ec.x - yt.ep[c];
-      e[c + 1] = ec.y - yt.ep[c + 1];
+      e[c] = ec.x - yin.ep[c];
+      e[c + 1] = ec.y - yin.ep[c + 1];
     }
-    const pair_t<T> s01 = pfma<T>(pmk<T>(M.C13, M.C13), pmk<T>(e[2], e[2]),
-                                  pfma<T>(pmk<T>(M.C12, M.C11), pmk<T>(e[1], e[1]),
-                                          pmul<T>(pmk<T>(M.C11, M.C12), pmk<T>(e[0], e[0]))));
-    const pair_t<T> s45 = pmul<T>(pmk<T>(T(2) * M.C44, T(2) * M.C66), pmk<T>(e[4], e[5]));
-    sg[0] = s01.x;
-    sg[1] = s01.y;
-    sg[2] = M.C13 * (e[0] + e[1]) + M.C33 * e[2];
-    sg[3] = T(2) * M.C44 * e[3];
-    sg[4] = s45.x;
-    sg[5] = s45.y;
+    const pair_t<T> s01 = pfma<T>(pmk<T>(M.C13s, M.C13s), pmk<T>(e[2], e[2]),
+                                  pfma<T>(pmk<T>(M.C12s, M.C11s), pmk<T>(e[1], e[1]),
+                                          pmul<T>(pmk<T>(M.C11s, M.C12s), pmk<T>(e[0], e[0]))));
+    const pair_t<T> s45 = pmul<T>(pmk<T>(M.C44s2, M.C66s2), pmk<T>(e[4], e[5]));
+    ss[0] = s01.x;
+    ss[1] = s01.y;
+    ss[2] = M.C13s * (e[0] + e[1]) + M.C33s * e[2];
+    ss[3] = M.C44s2 * e[3];
+    ss[4] = s45.x;
+    ss[5] = s45.y;
   } else {
 #pragma unroll
-    for (int c = 0; c < 6; ++c) e[c] = e0[c] + s * de[c] - yt.ep[c];
-    hooke<T>(M, e, sg);
+    for (int c = 0; c < 6; ++c) e[c] = e0[c] + s * de[c] - yin.ep[c];
+    ss[0] = M.C11s * e[0] + M.C12s * e[1] + M.C13s * e[2];
+    ss[1] = M.C12s * e[0] + M.C11s * e[1] + M.C13s * e[2];
+    ss[2] = M.C13s * (e[0] + e[1]) + M.C33s * e[2];
+    ss[3] = M.C44s2 * e[3];
+    ss[4] = M.C44s2 * e[4];
+    ss[5] = M.C66s2 * e[5];
   }
   T ex[16];
   const T cb_s = -M.b_s * T(kLog2e), cb_t = -M.b_b * T(kLog2e);
@@ -522,18 +640,18 @@ __device__ __forceinline__ void rk_stage(const MatDev<T>& M, const T* e0, const 
   pair_t<T> es2 = pmk<T>(T(0), T(0)), et2 = pmk<T>(T(0), T(0)), vt2 = pmk<T>(T(0), T(0));
 #pragma unroll
   for (int k = 0; k < 12; k += 2) {
-    const pair_t<T> p = pmul<T>(pmk<T>(cb_s, cb_s), pmk<T>(yt.v[k], yt.v[k + 1]));
+    const pair_t<T> p = pmul<T>(pmk<T>(cb_s, cb_s), pmk<T>(yin.v[k], yin.v[k + 1]));
     ex[k] = fast_exp2<T>(p.x);
     ex[k + 1] = fast_exp2<T>(p.y);
     es2 = padd<T>(es2, pmk<T>(ex[k], ex[k + 1]));
   }
 #pragma unroll
   for (int k = 12; k < 16; k += 2) {
-    const pair_t<T> p = pmul<T>(pmk<T>(cb_t, cb_t), pmk<T>(yt.v[k], yt.v[k + 1]));
+    const pair_t<T> p = pmul<T>(pmk<T>(cb_t, cb_t), pmk<T>(yin.v[k], yin.v[k + 1]));
     ex[k] = fast_exp2<T>(p.x);
     ex[k + 1] = fast_exp2<T>(p.y);
     et2 = padd<T>(et2, pmk<T>(ex[k], ex[k + 1]));
-    vt2 = padd<T>(vt2, pmk<T>(yt.v[k], yt.v[k + 1]));
+    vt2 = padd<T>(vt2, pmk<T>(yin.v[k], yin.v[k + 1]));
   }
   const T Es = es2.x + es2.y, Et = et2.x + et2.y, vtw = vt2.x + vt2.y;
   const T ftot = T(1.41421356237309504880) * vtw;
@@ -546,24 +664,35 @@ __device__ __forceinline__ void rk_stage(const MatDev<T>& M, const T* e0, const 
   const T Qdq_s = M.Q_s * dq, Qdq_t = M.Q_b * dq;
   const T Rb_s = M.Q_s * (M.h_off * (T(12) - Es) + dq);
   const T Rb_t = M.Q_b * (M.h_off * (T(4) - Et) + dq);
+  // initial resistance plus the stage's common hardening term per kind of system (Table 1:
+  // systems 3, 6, 9 and 12 ordinary, the other slip systems superdislocations; one value for
+  // the twins), as the host fills M.r0
+  const T rb_sup = M.r0[0] + Rb_s, rb_ord = M.r0[2] + Rb_s, rb_tw = M.r0[12] + Rb_t;
   RootCoef<T> qs, qt;
   if constexpr (NP != 0) {
     qs = root_coef<T>(T(1), M.K, M.n, M.inv_n, M.lg_K, M.eta, M.lg_eta, T(0));
     qt = root_coef<T>(Ptw, M.Kt, M.nt, M.inv_nt, M.lg_Kt, M.eta, M.lg_eta, lg_Ptw);
+    if constexpr (kPackedSolve<T, NP> && NP > 0) {
+      qs.lo = root_floor(qs);
+      qt.lo = root_floor(qt);
+    }
   }
-  T ss[6];
+  // plane sums of the slip-scaled stress (plane_sum)
+  T S[4][3];
 #pragma unroll
-  for (int c = 0; c < 6; ++c) ss[c] = sg[c] * sys_scale<T>(0);
-  T du_s[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
-  T du_t[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) S[p][i] = plane_sig(p, i) > 0 ? ss[i] + ss[i + 3] : ss[i] - ss[i + 3];
+  T du_s[6], D[3];
   // the systems in pairs: both driving forces, both rates (packed solve in float), then
   // each system folded into acc / yt
 #pragma unroll
   for (int k = 0; k < 12; k += 2) {
-    const pair_t<T> alk = pmk<T>(yt.al[k], yt.al[k + 1]);
-    const pair_t<T> tk = pfma<T>(pmk<T>(-M.c, -M.c), alk, pmk<T>(schmid_sum<T>(k, ss), schmid_sum<T>(k + 1, ss)));
+    const pair_t<T> alk = pmk<T>(yin.al[k], yin.al[k + 1]);
+    const pair_t<T> tk = pfma<T>(pmk<T>(-M.c, -M.c), alk,
+                                 pmk<T>(plane_sum<T>(k, S[k / 3]), plane_sum<T>(k + 1, S[(k + 1) / 3])));
     const pair_t<T> rr = pfma<T>(pmk<T>(-Qdq_s, -Qdq_s), pmk<T>(ex[k], ex[k + 1]),
-                                 pmk<T>(M.r0[k] + Rb_s, M.r0[k + 1] + Rb_s));
+                                 pmk<T>(k % 3 == 2 ? rb_ord : rb_sup, (k + 1) % 3 == 2 ? rb_ord : rb_sup));
     const T tek0 = tk.x, tek1 = tk.y;
     const T ak0 = fabs(tek0) - rr.x;
     const T ak1 = fabs(tek1) - rr.y;
@@ -578,15 +707,15 @@ __device__ __forceinline__ void rk_stage(const MatDev<T>& M, const T* e0, const 
     }
     const T gd0 = copysign(rk2[0], tek0);  // rk = 0 unless |tek| > r > 0
     const T gd1 = copysign(rk2[1], tek1);
-    schmid_add<T>(k, gd0, du_s);
-    schmid_add<T>(k + 1, gd1, du_s);
+    plane_add<T>(k, gd0, D, du_s);
+    plane_add<T>(k + 1, gd1, D, du_s);
     const pair_t<T> rk = pmk<T>(rk2[0], rk2[1]);
     const pair_t<T> drk = pmul<T>(pmk<T>(-M.d, -M.d), rk);
     const pair_t<T> ald = pfma<T>(drk, alk, pmk<T>(gd0, gd1));  // gd - d rk alpha
     const pair_t<T> wa = pmk<T>(wacc, wacc), cn = pmk<T>(cnext, cnext);
-    const pair_t<T> av = pfma<T>(wa, rk, pmk<T>(acc.v[k], acc.v[k + 1]));
+    const pair_t<T> av = FIRST ? rk : pfma<T>(wa, rk, pmk<T>(acc.v[k], acc.v[k + 1]));
     const pair_t<T> yv = pfma<T>(cn, rk, pmk<T>(y0.v[k], y0.v[k + 1]));
-    const pair_t<T> aa = pfma<T>(wa, ald, pmk<T>(acc.al[k], acc.al[k + 1]));
+    const pair_t<T> aa = FIRST ? ald : pfma<T>(wa, ald, pmk<T>(acc.al[k], acc.al[k + 1]));
     const pair_t<T> ya = pfma<T>(cn, ald, pmk<T>(y0.al[k], y0.al[k + 1]));
     acc.v[k] = av.x;
     acc.v[k + 1] = av.y;
@@ -597,12 +726,17 @@ __device__ __forceinline__ void rk_stage(const MatDev<T>& M, const T* e0, const 
     yt.al[k] = ya.x;
     yt.al[k + 1] = ya.y;
   }
+  // twins: the twin rates g_t enter the diagonal components as (G, G, -2 G), G = sum g_t,
+  // and component i + 3 as H_i = sum_t sig_i(plane of t) g_t (times -2 for i = 2)
+  T G = T(0), H[3] = {T(0), T(0), T(0)};
 #pragma unroll
   for (int k = 12; k < 16; k += 2) {
     const pair_t<T> rr = pfma<T>(pmk<T>(-Qdq_t, -Qdq_t), pmk<T>(ex[k], ex[k + 1]),
-                                 pmk<T>(M.r0[k] + Rb_t, M.r0[k + 1] + Rb_t));
-    const T ak0 = sys_scale<T>(k) * schmid_sum<T>(k, sg) - rr.x;
-    const T ak1 = sys_scale<T>(k + 1) * schmid_sum<T>(k + 1, sg) - rr.y;
+                                 pmk<T>(rb_tw, rb_tw));
+    // 1/(|n||l|) of a twin is (1/sqrt3) times the slip systems' scale in ss
+    constexpr T kTw = T(0.57735026918962576451);
+    const T ak0 = kTw * plane_sum<T>(k, S[k - 12]) - rr.x;
+    const T ak1 = kTw * plane_sum<T>(k + 1, S[k - 11]) - rr.y;
     T rk2[2];
     if constexpr (kPackedSolve<T, NP>) {
       const float2 r = reg_rate_tab2<NP>(make_float2(ak0, ak1), qt, M.nt_int, tab + kRootTabLen);
@@ -612,10 +746,19 @@ __device__ __forceinline__ void rk_stage(const MatDev<T>& M, const T* e0, const 
       rk2[0] = stage_rate<T, NP>(M, qt, ak0, Ptw, true, lg_Ptw, tab);
       rk2[1] = stage_rate<T, NP>(M, qt, ak1, Ptw, true, lg_Ptw, tab);
     }
-    schmid_add<T>(k, rk2[0], du_t);
-    schmid_add<T>(k + 1, rk2[1], du_t);
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int p = k - 12 + j;
+      const T g = rk2[j];
+      G = p == 0 ? g : G + g;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const T hg = plane_sig(p, i) > 0 ? g : -g;
+        H[i] = p == 0 ? hg : H[i] + hg;
+      }
+    }
     const pair_t<T> rk = pmk<T>(rk2[0], rk2[1]);
-    const pair_t<T> av = pfma<T>(pmk<T>(wacc, wacc), rk, pmk<T>(acc.v[k], acc.v[k + 1]));
+    const pair_t<T> av = FIRST ? rk : pfma<T>(pmk<T>(wacc, wacc), rk, pmk<T>(acc.v[k], acc.v[k + 1]));
     const pair_t<T> yv = pfma<T>(pmk<T>(cnext, cnext), rk, pmk<T>(y0.v[k], y0.v[k + 1]));
     acc.v[k] = av.x;
     acc.v[k + 1] = av.y;
@@ -626,12 +769,13 @@ __device__ __forceinline__ void rk_stage(const MatDev<T>& M, const T* e0, const 
   const T fs = wslip * sys_scale<T>(0);
   const T fsh = T(0.5) * fs;
   const T tsc = sys_scale<T>(12), tsh = T(0.5) * sys_scale<T>(12);
+  const T du_t[6] = {G, G, T(-2) * G, H[0], H[1], T(-2) * H[2]};
 #pragma unroll
   for (int c = 0; c < 6; c += 2) {
     const pair_t<T> dep = pfma<T>(pmk<T>(c < 3 ? fs : fsh, c + 1 < 3 ? fs : fsh), pmk<T>(du_s[c], du_s[c + 1]),
                                   pmul<T>(pmk<T>(c < 3 ? tsc : tsh, c + 1 < 3 ? tsc : tsh),
                                           pmk<T>(du_t[c], du_t[c + 1])));
-    const pair_t<T> ae = pfma<T>(pmk<T>(wacc, wacc), dep, pmk<T>(acc.ep[c], acc.ep[c + 1]));
+    const pair_t<T> ae = FIRST ? dep : pfma<T>(pmk<T>(wacc, wacc), dep, pmk<T>(acc.ep[c], acc.ep[c + 1]));
     const pair_t<T> ye = pfma<T>(pmk<T>(cnext, cnext), dep, pmk<T>(y0.ep[c], y0.ep[c + 1]));
     acc.ep[c] = ae.x;
     acc.ep[c + 1] = ae.y;
@@ -728,33 +872,34 @@ __device__ __forceinline__ void to_sample(const T* R, const T* s, T* out) {
 
 // Integrates one voxel over the increment [t_n, t_n + dt] (strain eps_n -> eps, sample
 // frame) and returns the sample-frame stress at t_n + dt; y is updated in place.
+// check: test first whether the increment is elastic and skip the integration if so.  The
+// test is a shortcut only: with every rate exactly 0 (inactive systems return 0 in every
+// rate-solve variant) the RK4 substeps leave the state bit for bit unchanged, so results do
+// not depend on it.  Returns false when the test ran and found the increment elastic.
 template <typename T, int NP>
-__device__ __forceinline__ void mc_voxel(const MatDev<T>& M, const T* R, const T* eps_n, const T* eps,
-                                         MPState<T>& y, T dt, int nsub, T* sig, const T* tab) {
+__device__ __forceinline__ bool mc_voxel(const MatDev<T>& M, const T* R, const T* eps_n, const T* eps,
+                                         MPState<T>& y, T dt, int nsub, T* sig, const T* tab, bool check = true) {
   T e0[6], e1[6], de[6];
   to_crystal<T>(R, eps_n, e0);
   to_crystal<T>(R, eps, e1);
 #pragma unroll
   for (int c = 0; c < 6; ++c) de[c] = e1[c] - e0[c];
-  if (!elastic_increment<T>(M, e0, de, y)) {
+  const bool flows = !(check && elastic_increment<T>(M, e0, de, y));
+  if (flows) {
     const T h = dt / T(nsub);
     const T inv = T(1) / T(nsub);
     for (int m = 0; m < nsub; ++m) {
       const T s0 = T(m) * inv, sh = (T(m) + T(0.5)) * inv, s1 = (T(m) + T(1)) * inv;
-      MPState<T> yt = y, acc;
-#pragma unroll
-      for (int c = 0; c < 6; ++c) acc.ep[c] = T(0);
-#pragma unroll
-      for (int c = 0; c < 16; ++c) acc.v[c] = T(0);
-#pragma unroll
-      for (int c = 0; c < 12; ++c) acc.al[c] = T(0);
-      // classical RK4: stages at s0, sh, sh, s1 with weights 1, 2, 2, 1; one copy of
-      // the stage body (not unrolled) keeps the code compact
+      MPState<T> yt, acc;
+      // classical RK4: stages at s0, sh, sh, s1 with weights 1, 2, 2, 1.  The first stage
+      // reads y and assigns acc and yt; the other three share one copy of the stage body
+      // (not unrolled, which keeps the code compact)
+      rk_stage<T, NP, true>(M, e0, de, s0, y, yt, acc, T(1), T(0.5) * h, tab);
 #pragma unroll 1
-      for (int stg = 0; stg < 4; ++stg) {
-        const T s = stg == 0 ? s0 : (stg == 3 ? s1 : sh);
-        const T wacc = (stg == 0 || stg == 3) ? T(1) : T(2);
-        const T cnext = stg < 2 ? T(0.5) * h : (stg == 2 ? h : T(0));
+      for (int stg = 1; stg < 4; ++stg) {
+        const T s = stg == 3 ? s1 : sh;
+        const T wacc = stg == 3 ? T(1) : T(2);
+        const T cnext = stg == 1 ? T(0.5) * h : (stg == 2 ? h : T(0));
         rk_stage<T, NP>(M, e0, de, s, y, yt, acc, wacc, cnext, tab);
       }
       const T w = h / T(6);
@@ -771,6 +916,7 @@ __device__ __forceinline__ void mc_voxel(const MatDev<T>& M, const T* R, const T
   for (int c = 0; c < 6; ++c) ee[c] = e1[c] - y.ep[c];
   hooke<T>(M, ee, sc);
   to_sample<T>(R, sc, sig);
+  return flows;
 }
 
 template <typename T>

@@ -17,11 +17,11 @@ template <typename T> struct ZGroup;
 struct GuardGroup;
 
 // Rate-solve variants of the constitutive kernels (see constitutive.cuh): NP = 10 for
-// eta > 0 and n = nt = 10, NP = -1 for eta > 0 and other exponents >= 1, NP = 0 (generic
-// per-system solve) for eta = 0.
-inline int rate_variant(double eta, int n_int, int nt_int) {
+// n = nt = 10 and eta >= max(K, Kt) (the floored solve, root_floor, is exact there), NP = -1
+// for eta > 0 otherwise (exponents >= 1), NP = 0 (generic per-system solve) for eta = 0.
+inline int rate_variant(double eta, double K, double Kt, int n_int, int nt_int) {
   if (!(eta > 0.0)) return 0;
-  return (n_int == 10 && nt_int == 10) ? 10 : -1;
+  return (n_int == 10 && nt_int == 10 && eta >= K && eta >= Kt) ? 10 : -1;
 }
 
 // Per-variant entry points (each instantiated in its own translation unit).

@@ -64,6 +64,9 @@ struct MatDev {
   T sm, smt;          // smooth-min exponents: 1 / log2(1/u1), u1^n + u1 = 1
   T lg_K, lg_Kt;      // log2 K, log2 Kt
   T lg_eta;           // log2 eta (eta > 0)
+  // Hooke's law scaled by the slip systems' Schmid factor 1/sqrt6 (shear rows with their
+  // factor 2): the stage's resolved stresses come from C_s : e directly
+  T C11s, C12s, C13s, C33s, C44s2, C66s2;
 };
 
 // Mixed-load controller data (always double).

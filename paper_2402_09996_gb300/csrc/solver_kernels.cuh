@@ -169,6 +169,10 @@ struct XArgs {
   // B 36 x nvox (entry (r, c) at (r * 6 + c) * nvox + voxel), g 6 x nvox
   const T* lin_B;
   const T* lin_g;
+  // one byte per warp's 32 consecutive voxels (index voxel / 32 of its first voxel): 1 when
+  // some voxel of the group flowed in the increment's first trial iteration, which then
+  // skips the elastic-increment test in the later ones (NULL: always test)
+  unsigned char* flow;
 };
 
 // The x transforms of a CTA's nseq packed lines (stride xs >= N + 1 in shared memory) for
@@ -324,7 +328,18 @@ __device__ __forceinline__ void xpass_cta(const XArgs<T>& a, const XCommon<T>& k
       const uint32_t g = a.grain[vox];
   #pragma unroll
       for (int i = 0; i < 9; ++i) R[i] = a.Rg[(size_t)g * 9 + i];
-      mc_voxel<T, NP>(k.M, R, epsn, eps, y, k.dt, k.nsub, sig, tab);
+      // The elastic-increment test saves work only where all 32 voxels of a warp stay
+      // elastic; in the developed plastic regime it is wasted.  Iteration 0 of an increment
+      // (and the commit) always tests and records per warp whether any voxel flowed;
+      // warps that flowed skip the test in the increment's later iterations.
+      const size_t grp = ((size_t)line0 * nx + (size_t)(t - (tid & 31))) >> 5;
+      const bool record = !COMMIT && a.flow != nullptr && it == 0;
+      const bool check = COMMIT || a.flow == nullptr || it == 0 || a.flow[grp] == 0;
+      const bool flowed = mc_voxel<T, NP>(k.M, R, epsn, eps, y, k.dt, k.nsub, sig, tab, check);
+      if (record) {
+        const bool any = __any_sync(__activemask(), flowed);
+        if ((tid & 31) == 0) a.flow[grp] = any ? 1 : 0;
+      }
   #pragma unroll
       for (int c = 0; c < 6; ++c) sacc[c] += sig[c];
       if (COMMIT) {

@@ -64,7 +64,7 @@ DT = 0.5
 # DRAM bytes (read + write) of one trial x-pass launch on the twinned 128^3 FP32 case, from
 # ncu (dram__bytes_read.sum + dram__bytes_write.sum, mean of three launches in the plastic
 # regime); valid for the x-pass source as profiled, to be re-taken whenever that kernel changes
-XPASS_DRAM_BYTES_128 = 435_002_965
+XPASS_DRAM_BYTES_128 = 435_345_749
 
 
 def flops_per_voxit(n_sub):

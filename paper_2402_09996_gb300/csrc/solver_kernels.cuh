@@ -638,10 +638,153 @@ struct ZArgs {
 
 constexpr int kZThreads = 256;
 
+// The six components of a spectral point, contiguous at p: 16-byte vector accesses when
+// vec (both tau_hat spectra 16-byte aligned; every point's offset 6 * 8 or 6 * 16 bytes
+// keeps that alignment), else one complex value at a time.
+template <typename T>
+__device__ __forceinline__ void load_point6(const C2<T>* p, C2<T>* v, bool vec) {
+  if constexpr (sizeof(C2<T>) == 8) {
+    if (vec) {
+      const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const float4 f = q[i];
+        v[2 * i] = mk<T>(f.x, f.y);
+        v[2 * i + 1] = mk<T>(f.z, f.w);
+      }
+      return;
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 6; ++c) v[c] = p[c];
+}
+template <typename T>
+__device__ __forceinline__ void store_point6(C2<T>* p, const C2<T>* v, bool vec) {
+  if constexpr (sizeof(C2<T>) == 8) {
+    if (vec) {
+      float4* q = reinterpret_cast<float4*>(p);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) q[i] = make_float4(v[2 * i].x, v[2 * i].y, v[2 * i + 1].x, v[2 * i + 1].y);
+      return;
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 6; ++c) p[c] = v[c];
+}
+
+// Green operator step of one spectral point (kx index h, ky index j, kz): t holds tau_hat
+// on entry and the new strain spectrum on exit; tau_hat is kept for the next iteration's
+// residual (P_out) and the point's weighted residual term |kappa . sigma_hat|^2 is returned.
+template <typename T>
+__device__ __forceinline__ T green_point(const ZArgs<T>& a, int h, int j, int kz, const double* En, T coef,
+                                         bool vec, C2<T>* t) {
+  T k0, k1, k2;
+  if (a.scheme == 0) {
+    const T sx = a.kx[2 * h], cx = a.kx[2 * h + 1];
+    const T sy = a.ky[2 * j], cy = a.ky[2 * j + 1];
+    const T sz = a.kzt[2 * kz], cz = a.kzt[2 * kz + 1];
+    k0 = sx * cy * cz;
+    k1 = cx * sy * cz;
+    k2 = cx * cy * sz;
+  } else {
+    k0 = a.kx[2 * h];
+    k1 = a.ky[2 * j];
+    k2 = a.kzt[2 * kz];
+  }
+  const size_t g0 = (((size_t)kz * a.ny + j) * a.H + h) * 6;
+  T rterm;
+  // equilibrium residual kappa . sigma_hat = kappa . (tau_hat - tau_hat_prev)
+  {
+    C2<T> d[6];
+    load_point6<T>(a.P_prev + g0, d, vec);
+    store_point6<T>(a.P_out + g0, t, vec);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) d[c] = csub<T>(t[c], d[c]);
+    // symmetric order (11,22,33,23,13,12): row i of d times kappa.  The point's term and
+    // its column's sum over kz are formed in the field precision (relative rounding
+    // below 1e-5 in float, on an error compared with tolerances of 1e-6 and above); the
+    // sum over columns is FP64.
+    const T r0x = d[0].x * k0 + d[5].x * k1 + d[4].x * k2;
+    const T r0y = d[0].y * k0 + d[5].y * k1 + d[4].y * k2;
+    const T r1x = d[5].x * k0 + d[1].x * k1 + d[3].x * k2;
+    const T r1y = d[5].y * k0 + d[1].y * k1 + d[3].y * k2;
+    const T r2x = d[4].x * k0 + d[3].x * k1 + d[2].x * k2;
+    const T r2y = d[4].y * k0 + d[3].y * k1 + d[2].y * k2;
+    const T wgt = (h == 0 || 2 * h == a.nx) ? T(1) : T(2);
+    rterm = wgt * (r0x * r0x + r0y * r0y + r1x * r1x + r1y * r1y + r2x * r2x + r2y * r2y);
+  }
+  const T kk = k0 * k0 + k1 * k1 + k2 * k2;
+  if (h == 0 && j == 0 && kz == 0) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) t[c] = mk<T>(T(En[c]), T(0));
+  } else if (!(kk > T(0))) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) t[c] = mk<T>(T(0), T(0));
+  } else {
+    // Gamma0 is homogeneous of degree 0 in kappa: with the unit direction n = kappa/|kappa|,
+    // eps_hat = -[ (n_i u_j + n_j u_i) / (2 mu0) - coef n_i n_j (n.u) ] / N,  u = tau_hat n
+    const T inv_k = T(1) / sqrt(kk);
+    const T n0 = k0 * inv_k, n1 = k1 * inv_k, n2 = k2 * inv_k;
+    const C2<T> u0 = mk<T>(t[0].x * n0 + t[5].x * n1 + t[4].x * n2, t[0].y * n0 + t[5].y * n1 + t[4].y * n2);
+    const C2<T> u1 = mk<T>(t[5].x * n0 + t[1].x * n1 + t[3].x * n2, t[5].y * n0 + t[1].y * n1 + t[3].y * n2);
+    const C2<T> u2 = mk<T>(t[4].x * n0 + t[3].x * n1 + t[2].x * n2, t[4].y * n0 + t[3].y * n1 + t[2].y * n2);
+    const C2<T> nun = mk<T>(n0 * u0.x + n1 * u1.x + n2 * u2.x, n0 * u0.y + n1 * u1.y + n2 * u2.y);
+    const T ia = -a.invN / (T(2) * a.mu0);
+    const T ib = a.invN * coef;
+    const T nv[3] = {n0, n1, n2};
+    const C2<T> uv[3] = {u0, u1, u2};
+    const int ii[6] = {0, 1, 2, 1, 0, 0};
+    const int jj[6] = {0, 1, 2, 2, 2, 1};
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      const T ni = nv[ii[c]], nj = nv[jj[c]];
+      const C2<T> ui = uv[ii[c]], uj = uv[jj[c]];
+      const T nij = ni * nj;
+      t[c] = mk<T>(ia * (ni * uj.x + nj * ui.x) + ib * nij * nun.x, ia * (ni * uj.y + nj * ui.y) + ib * nij * nun.y);
+    }
+  }
+  return rterm;
+}
+
+// The second step of the two-step transform on every column of the CTA's lines, in place:
+// the column k2 of line s (slots k2 N1 + n1, n1 = 0 .. N1 - 1) is replaced by its N1-point
+// DFT, each thread reading and writing only its own columns' slots.  Forward (SIGN < 0):
+// slot k2 N1 + k1 then holds X[k2 + N2 k1].  Inverse (SIGN > 0, the first step of the
+// transposed inverse): the slots hold X[k2 + N2 k1] on entry and
+// Z[n1][k2] = W^(n1 k2) sum_k1 X[k2 + N2 k1] W_N1^(n1 k1) at slot k2 N1 + n1 on exit,
+// W = e^(2 pi i / N), W_N1 = e^(2 pi i / N1) (tw[e] = e^(-2 pi i e / N)).
+template <typename T, int SIGN, int N1, int N2>
+__device__ __forceinline__ void pencil_cols_inplace(C2<T>* b, int ps, int SP, int S, const C2<T>* tw, int tid,
+                                                    int nthr) {
+  constexpr int kCols = (N2 + N1 - 1) / N1;  // columns per thread (N2 * SP columns, >= N1 * SP threads)
+#pragma unroll
+  for (int r = 0; r < kCols; ++r) {
+    const int col = tid + r * nthr;
+    const int s2 = col % SP, k2 = col / SP;
+    if (col < N2 * SP && s2 < S) {
+      C2<T>* line = b + (size_t)s2 * ps;
+      C2<T> w[N1];
+      pencil_step2<T, SIGN, N1, N2>(w, k2, line);
+      if constexpr (SIGN > 0) {
+#pragma unroll
+        for (int q = 1; q < N1; ++q)
+          if (k2 > 0) w[q] = cmulc<T>(w[q], tw[q * k2]);
+      }
+#pragma unroll
+      for (int q = 0; q < N1; ++q) line[k2 * N1 + q] = w[q];
+    }
+  }
+}
+
 // N1 = N2 = 0: Stockham transforms of any supported nz in shared memory (two buffers,
 // line of component c and chunk column hh at (c hc + hh) ps); N1 N2 = nz: the two-step
 // register transforms of fft_reg.cuh (one buffer, line s = 6 hh + c at s ps, as in the
-// global rows).
+// global rows).  The register path runs the forward transform's second step in place, so
+// the Green step reads the spectrum in that step's slot order (point kz = k2 + N2 k1 at
+// slot k2 N1 + k1), and the inverse as the transposed two-step transform (the N1-point
+// DFTs of the columns first, in place, then the N2-point DFTs straight to global memory):
+// three barriers between the global load and the global store; twiddles are read through
+// L1.
 template <typename T, int N1, int N2>
 __device__ __forceinline__ void zgreen_cta(const ZArgs<T>& a, const Cta& cta, double (*red)[kNumRed], int& s_last) {
   constexpr bool kPencil = N1 > 0;
@@ -660,157 +803,68 @@ __device__ __forceinline__ void zgreen_cta(const ZArgs<T>& a, const Cta& cta, do
   const size_t H = a.H, ny = a.ny;
   C2<T>* gz = a.spec + ((size_t)j * H + h0) * 6;
   const size_t gs = ny * H * 6;
-  // line of (component c, chunk column hh) in shared memory
-  auto line = [&](int c, int hh) -> size_t { return (size_t)(kPencil ? hh * 6 + c : c * hc + hh) * ps; };
-  C2<T>* res;
-  C2<T>* oth = nullptr;
+  const bool vec = ((reinterpret_cast<uintptr_t>(a.P_prev) | reinterpret_cast<uintptr_t>(a.P_out)) & 15) == 0;
+  const int it = a.it >= 0 ? a.it : a.st->it_dev;
+  const double* En = a.st->E[(it + 1) & 1];
+  const T coef = (a.lam0 + a.mu0) / (a.mu0 * (a.lam0 + T(2) * a.mu0));
   if constexpr (kPencil) {
-    // forward z transform: both steps, then the result in natural order in b0
+    const C2<T>* twg = a.tw;  // e^(-2 pi i e / nz), e < nz (read through L1)
     const int SP = 6 * a.HC, S = 6 * hc;
     const int s = tid % SP, n1 = tid / SP;
     const bool mine = s < S && n1 < N1;  // the CTA has N1 * SP threads rounded up to warps
-    C2<T> v[N2];
+    // forward z transform: first step from the global rows n1 + N1 n2, second step in place
     if (mine) {
+      C2<T> v[N2];
 #pragma unroll
       for (int q = 0; q < N2; ++q) v[q] = gz[(size_t)(n1 + N1 * q) * gs + s];
-    }
-    for (int i = tid; i < nz; i += nthr) tw[i] = a.tw[i];
-    __syncthreads();
-    if (mine) pencil_step1<T, -1, N1, N2>(v, n1, b0 + (size_t)s * ps, tw);
-    __syncthreads();
-    constexpr int kCols = (N2 + N1 - 1) / N1;  // columns per thread (N2 * SP columns, N1 * SP threads)
-    C2<T> w[kCols][N1];
-#pragma unroll
-    for (int r = 0; r < kCols; ++r) {
-      const int col = tid + r * nthr;
-      const int s2 = col % SP, k2 = col / SP;
-      if (col < N2 * SP && s2 < S) pencil_step2<T, -1, N1, N2>(w[r], k2, b0 + (size_t)s2 * ps);
+      pencil_step1<T, -1, N1, N2>(v, n1, b0 + (size_t)s * ps, twg);
     }
     __syncthreads();
+    pencil_cols_inplace<T, -1, N1, N2>(b0, ps, SP, S, twg, tid, nthr);
+    __syncthreads();
+    // Green step per point, in slot order (consecutive threads on consecutive slots of
+    // the chunk's columns)
+    for (int w = tid; w < hc * nz; w += nthr) {
+      const int hh = w % hc, sl = w / hc;
+      const int kz = sl / N1 + N2 * (sl % N1);
+      C2<T> t[6];
 #pragma unroll
-    for (int r = 0; r < kCols; ++r) {
-      const int col = tid + r * nthr;
-      const int s2 = col % SP, k2 = col / SP;
-      if (col < N2 * SP && s2 < S) {
+      for (int c = 0; c < 6; ++c) t[c] = b0[(size_t)(hh * 6 + c) * ps + sl];
+      cres[hh * nz + kz] = green_point<T>(a, h0 + hh, j, kz, En, coef, vec, t);
 #pragma unroll
-        for (int q = 0; q < N1; ++q) b0[(size_t)s2 * ps + k2 + N2 * q] = w[r][q];
-      }
+      for (int c = 0; c < 6; ++c) b0[(size_t)(hh * 6 + c) * ps + sl] = t[c];
     }
     __syncthreads();
-    res = b0;
+    // inverse z transform: the columns' N1-point DFTs in place, then each thread's
+    // N2-point DFT of its column n1 over k2, written to the global rows n1 + N1 n2
+    pencil_cols_inplace<T, +1, N1, N2>(b0, ps, SP, S, twg, tid, nthr);
+    __syncthreads();
+    if (mine) {
+      const C2<T>* line = b0 + (size_t)s * ps;
+      C2<T> v[N2];
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) v[k2] = line[k2 * N1 + n1];
+      dft_reg<T, +1, N2>(v);
+#pragma unroll
+      for (int q = 0; q < N2; ++q) gz[(size_t)(n1 + N1 * q) * gs + s] = v[q];
+    }
   } else {
     for (int i = tid; i < nz; i += nthr) tw[i] = a.tw[i];
     // component-interleaved spectra: for each kz the CTA's hc * 6 values are contiguous
     tile_move<T, true>(b0, ps, gz, gs, nz, 6 * hc, 6, hc, tid, nthr);
     __syncthreads();
-    res = smem_fft<T, -1>(b0, b1, a.dz, 6 * hc, ps, tw, tid, nthr);
-    oth = (res == b0) ? b1 : b0;
-  }
-
-  const int it = a.it >= 0 ? a.it : a.st->it_dev;
-  const double* En = a.st->E[(it + 1) & 1];
-  const T coef = (a.lam0 + a.mu0) / (a.mu0 * (a.lam0 + T(2) * a.mu0));
-  for (int w = tid; w < hc * nz; w += nthr) {
-    const int hh = w % hc, kz = w / hc;
-    const int h = h0 + hh;
-    T k0, k1, k2;
-    if (a.scheme == 0) {
-      const T sx = a.kx[2 * h], cx = a.kx[2 * h + 1];
-      const T sy = a.ky[2 * j], cy = a.ky[2 * j + 1];
-      const T sz = a.kzt[2 * kz], cz = a.kzt[2 * kz + 1];
-      k0 = sx * cy * cz;
-      k1 = cx * sy * cz;
-      k2 = cx * cy * sz;
-    } else {
-      k0 = a.kx[2 * h];
-      k1 = a.ky[2 * j];
-      k2 = a.kzt[2 * kz];
-    }
-    C2<T> t[6];
-    const size_t g0 = (((size_t)kz * ny + j) * H + h) * 6;
+    C2<T>* res = smem_fft<T, -1>(b0, b1, a.dz, 6 * hc, ps, tw, tid, nthr);
+    C2<T>* oth = (res == b0) ? b1 : b0;
+    for (int w = tid; w < hc * nz; w += nthr) {
+      const int hh = w % hc, kz = w / hc;
+      C2<T> t[6];
 #pragma unroll
-    for (int c = 0; c < 6; ++c) t[c] = res[line(c, hh) + kz];
-    // equilibrium residual kappa . sigma_hat = kappa . (tau_hat - tau_hat_prev)
-    {
-      C2<T> d[6];
+      for (int c = 0; c < 6; ++c) t[c] = res[(size_t)(c * hc + hh) * ps + kz];
+      cres[hh * nz + kz] = green_point<T>(a, h0 + hh, j, kz, En, coef, vec, t);
 #pragma unroll
-      for (int c = 0; c < 6; ++c) {
-        const C2<T> p = a.P_prev[g0 + c];
-        d[c] = csub<T>(t[c], p);
-        a.P_out[g0 + c] = t[c];
-      }
-      // symmetric order (11,22,33,23,13,12): row i of d times kappa.  The point's term and
-      // its column's sum over kz are formed in the field precision (relative rounding
-      // below 1e-5 in float, on an error compared with tolerances of 1e-6 and above); the
-      // sum over columns is FP64.
-      const T r0x = d[0].x * k0 + d[5].x * k1 + d[4].x * k2;
-      const T r0y = d[0].y * k0 + d[5].y * k1 + d[4].y * k2;
-      const T r1x = d[5].x * k0 + d[1].x * k1 + d[3].x * k2;
-      const T r1y = d[5].y * k0 + d[1].y * k1 + d[3].y * k2;
-      const T r2x = d[4].x * k0 + d[3].x * k1 + d[2].x * k2;
-      const T r2y = d[4].y * k0 + d[3].y * k1 + d[2].y * k2;
-      const T wgt = (h == 0 || 2 * h == a.nx) ? T(1) : T(2);
-      cres[hh * nz + kz] = wgt * (r0x * r0x + r0y * r0y + r1x * r1x + r1y * r1y + r2x * r2x + r2y * r2y);
-    }
-    const T kk = k0 * k0 + k1 * k1 + k2 * k2;
-    C2<T> e[6];
-    if (h == 0 && j == 0 && kz == 0) {
-#pragma unroll
-      for (int c = 0; c < 6; ++c) e[c] = mk<T>(T(En[c]), T(0));
-    } else if (!(kk > T(0))) {
-#pragma unroll
-      for (int c = 0; c < 6; ++c) e[c] = mk<T>(T(0), T(0));
-    } else {
-      // Gamma0 is homogeneous of degree 0 in kappa: with the unit direction n = kappa/|kappa|,
-      // eps_hat = -[ (n_i u_j + n_j u_i) / (2 mu0) - coef n_i n_j (n.u) ] / N,  u = tau_hat n
-      const T inv_k = T(1) / sqrt(kk);
-      const T n0 = k0 * inv_k, n1 = k1 * inv_k, n2 = k2 * inv_k;
-      const C2<T> u0 = mk<T>(t[0].x * n0 + t[5].x * n1 + t[4].x * n2, t[0].y * n0 + t[5].y * n1 + t[4].y * n2);
-      const C2<T> u1 = mk<T>(t[5].x * n0 + t[1].x * n1 + t[3].x * n2, t[5].y * n0 + t[1].y * n1 + t[3].y * n2);
-      const C2<T> u2 = mk<T>(t[4].x * n0 + t[3].x * n1 + t[2].x * n2, t[4].y * n0 + t[3].y * n1 + t[2].y * n2);
-      const C2<T> nun = mk<T>(n0 * u0.x + n1 * u1.x + n2 * u2.x, n0 * u0.y + n1 * u1.y + n2 * u2.y);
-      const T ia = -a.invN / (T(2) * a.mu0);
-      const T ib = a.invN * coef;
-      const T nv[3] = {n0, n1, n2};
-      const C2<T> uv[3] = {u0, u1, u2};
-      const int ii[6] = {0, 1, 2, 1, 0, 0};
-      const int jj[6] = {0, 1, 2, 2, 2, 1};
-#pragma unroll
-      for (int c = 0; c < 6; ++c) {
-        const T ni = nv[ii[c]], nj = nv[jj[c]];
-        const C2<T> ui = uv[ii[c]], uj = uv[jj[c]];
-        const T nij = ni * nj;
-        e[c] = mk<T>(ia * (ni * uj.x + nj * ui.x) + ib * nij * nun.x, ia * (ni * uj.y + nj * ui.y) + ib * nij * nun.y);
-      }
-    }
-#pragma unroll
-    for (int c = 0; c < 6; ++c) res[line(c, hh) + kz] = e[c];
-  }
-  __syncthreads();
-  if constexpr (kPencil) {
-    // inverse z transform: step 1 reads its column from b0 (all reads before the writes),
-    // step 2 writes the rows to global memory
-    const int SP = 6 * a.HC, S = 6 * hc;
-    const int s = tid % SP, n1 = tid / SP;
-    const bool mine = s < S && n1 < N1;
-    C2<T> v[N2];
-    if (mine) {
-#pragma unroll
-      for (int q = 0; q < N2; ++q) v[q] = b0[(size_t)s * ps + n1 + N1 * q];
+      for (int c = 0; c < 6; ++c) res[(size_t)(c * hc + hh) * ps + kz] = t[c];
     }
     __syncthreads();
-    if (mine) pencil_step1<T, +1, N1, N2>(v, n1, b0 + (size_t)s * ps, tw);
-    __syncthreads();
-    for (int col = tid; col < N2 * SP; col += nthr) {
-      const int s2 = col % SP, k2 = col / SP;
-      if (s2 < S) {
-        C2<T> w2[N1];
-        pencil_step2<T, +1, N1, N2>(w2, k2, b0 + (size_t)s2 * ps);
-#pragma unroll
-        for (int q = 0; q < N1; ++q) gz[(size_t)(k2 + N2 * q) * gs + s2] = w2[q];
-      }
-    }
-  } else {
     C2<T>* out = smem_fft<T, +1>(res, oth, a.dz, 6 * hc, ps, tw, tid, nthr);
     tile_move<T, false>(out, ps, gz, gs, nz, 6 * hc, 6, hc, tid, nthr);
   }
@@ -895,8 +949,16 @@ __device__ __forceinline__ void zgreen_cta(const ZArgs<T>& a, const Cta& cta, do
   }
 }
 
+// Resident CTAs per SM the float z pass is compiled for (register cap; its shared memory
+// fits as many); double keeps the compiler's choice.
+template <typename T, int N1>
+struct ZMinBlocks {
+  static constexpr int value = sizeof(T) == 4 ? (N1 > 0 ? 3 : 4) : 1;
+};
+
 template <typename T, int N1, int N2>
-__global__ void __launch_bounds__(N1 > 0 ? kPencilThreads : kZThreads) k_zgreen(const ZArgs<T> a) {
+__global__ void __launch_bounds__(N1 > 0 ? kPencilThreads : kZThreads, ZMinBlocks<T, N1>::value)
+    k_zgreen(const ZArgs<T> a) {
   __shared__ double red[32][kNumRed];
   __shared__ int s_last;
   zgreen_cta<T, N1, N2>(a, own_grid(), red, s_last);

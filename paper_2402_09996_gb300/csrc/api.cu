@@ -456,16 +456,21 @@ rve_status check_material(rve_s* h, const rve_material& m) {
   return RVE_OK;
 }
 
+// Twiddles e^{-2 pi i m / n}, m = 0 .. n - 1, as interleaved (re, im) pairs at out.
+template <typename T>
+void fill_twiddles(int n, T* out) {
+  for (int m = 0; m < n; ++m) {
+    const double a = 2.0 * kPi * (double)m / (double)n;
+    out[2 * m] = (T)std::cos(a);
+    out[2 * m + 1] = (T)(-std::sin(a));
+  }
+}
+
 template <typename T>
 rve_status upload_tables(rve_s* h) {
-  // twiddles e^{-2 pi i m / n}
   auto tw = [&](int n, void** dst) -> rve_status {
     std::vector<T> t(2 * n);
-    for (int m = 0; m < n; ++m) {
-      const double a = 2.0 * kPi * (double)m / (double)n;
-      t[2 * m] = (T)std::cos(a);
-      t[2 * m + 1] = (T)(-std::sin(a));
-    }
+    fill_twiddles<T>(n, t.data());
     rve_status s = dalloc(h, dst, t.size() * sizeof(T));
     if (s) return s;
     RVE_CUDA(h, cudaMemcpyAsync(*dst, t.data(), t.size() * sizeof(T), cudaMemcpyHostToDevice, h->stream));
@@ -2281,34 +2286,60 @@ rve_status rve_material_point_vjp(int precision, const rve_material* mat, long l
 template <typename T>
 static rve_status fft_t(int nx, int ny, int nz, int ncomp, const void* in, void* spec, void* out, int sign,
                         cudaStream_t st) {
-  rve_s h;
-  h.nx = nx; h.ny = ny; h.nz = nz; h.H = nx / 2 + 1; h.NL = (long long)ny * nz;
-  factor_radices(nx, &h.dx);
-  factor_radices(ny, &h.dy);
-  factor_radices(nz, &h.dz);
-  h.stream = st;
-  rve_status s;
-  if ((s = upload_tables<T>(&h))) { release(&h); return fail(nullptr, s, h.err); }
-  const int L = std::max(1, x_threads() / nx);
+  FftDim dx, dy, dz;
+  factor_radices(nx, &dx);
+  factor_radices(ny, &dy);
+  factor_radices(nz, &dz);
+  const int H = nx / 2 + 1;
+  const long long NL = (long long)ny * nz;
+  // the three twiddle tables in one stream-ordered allocation (no device-wide synchronisation)
+  const size_t ntab = 2 * (size_t)(nx + ny + nz);
+  std::vector<T> host(ntab);
+  fill_twiddles<T>(nx, host.data());
+  fill_twiddles<T>(ny, host.data() + 2 * nx);
+  fill_twiddles<T>(nz, host.data() + 2 * (nx + ny));
+  void* dtab = nullptr;
+  cudaError_t e = cudaMallocAsync(&dtab, ntab * sizeof(T), st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(nullptr, RVE_ERR_OOM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
+  }
+  e = cudaMemcpyAsync(dtab, host.data(), ntab * sizeof(T), cudaMemcpyHostToDevice, st);
+  const C2<T>* tw_x = (const C2<T>*)dtab;
+  const C2<T>* tw_y = tw_x + nx;
+  const C2<T>* tw_z = tw_y + ny;
+  // x: up to 16 lines of one component per CTA (2048 points at most)
+  const int L = std::max(1, std::min(16, 2048 / nx));
   XFftArgs<T> xa{};
-  xa.nx = nx; xa.H = h.H; xa.L = L; xa.ncomp = ncomp; xa.NL = h.NL;
-  xa.dx = h.dx;
-  xa.tw = (const C2<T>*)h.tw_x;
+  xa.nx = nx; xa.H = H; xa.L = L; xa.ncomp = ncomp; xa.NL = NL;
+  xa.dx = dx;
+  xa.tw = tw_x;
   xa.real = (const T*)in;
   xa.spec = (C2<T>*)spec;
   xa.real_out = (T*)out;
-  const size_t xsm = (size_t)(nx + 2 * L * nx) * 2 * sizeof(T);
-  const dim3 xg((unsigned)((h.NL + L - 1) / L), ncomp);
+  const size_t xsm = (size_t)(nx + 2 * L * (nx + 1)) * sizeof(C2<T>);
+  const dim3 xg((unsigned)((NL + L - 1) / L), ncomp);
   const size_t budget = 96 * 1024;
-  auto pass = [&](const FftDim& d, void* tw, long long stride, int n_o2, long long A, long long B, int n_outer) {
+  // y and z: one component's kx chunk per CTA; lengths with a register split take the
+  // two-step kernel with the chunks of H split evenly (at most 384 / N1 columns each), the
+  // others Stockham passes on a chunk sized for the shared-memory budget
+  auto pass = [&](const FftDim& d, const C2<T>* tw, long long stride, int n_o2, long long A, long long B,
+                  int n_outer) {
     LineArgs<T> la{};
     la.done = nullptr;  // stand-alone transform: always runs
     la.d = d;
-    la.tw = (const C2<T>*)tw;
+    la.tw = tw;
     la.spec = (C2<T>*)spec;
-    la.H = h.H;
-    la.HC = (int)std::max<size_t>(1, std::min<size_t>(16, (budget / (4 * sizeof(T))) / d.n));
-    la.HC = std::min(la.HC, h.H);
+    la.H = H;
+    const int n1 = pencil_n1(d.n);
+    if (n1 > 0) {
+      const int cmax = 384 / n1;
+      const int chunks = (H + cmax - 1) / cmax;
+      la.HC = (H + chunks - 1) / chunks;
+    } else {
+      la.HC = (int)std::max<size_t>(1, std::min<size_t>(16, (budget / (4 * sizeof(T))) / d.n));
+      la.HC = std::min(la.HC, H);
+    }
     la.n_o2 = n_o2;
     la.NC = 1;
     la.hstride = 1;
@@ -2316,21 +2347,23 @@ static rve_status fft_t(int nx, int ny, int nz, int ncomp, const void* in, void*
     la.A = A;
     la.B = B;
     const size_t sm = (size_t)(d.n + 2 * la.HC * (d.n + 1)) * 2 * sizeof(T);
-    return launch_line<T>(la, sign, dim3((h.H + la.HC - 1) / la.HC, n_outer), sm, st);
+    return launch_line<T>(la, sign, dim3((H + la.HC - 1) / la.HC, n_outer), sm, st);
   };
-  const long long plane = (long long)nz * ny * h.H;
-  cudaError_t e = cudaSuccess;
-  if (sign < 0) {
-    e = launch_xfft<T>(xa, -1, xg, xsm, st);
-    if (e == cudaSuccess) e = pass(h.dy, h.tw_y, h.H, nz, plane, (long long)ny * h.H, ncomp * nz);
-    if (e == cudaSuccess) e = pass(h.dz, h.tw_z, (long long)ny * h.H, ny, plane, h.H, ncomp * ny);
-  } else {
-    e = pass(h.dz, h.tw_z, (long long)ny * h.H, ny, plane, h.H, ncomp * ny);
-    if (e == cudaSuccess) e = pass(h.dy, h.tw_y, h.H, nz, plane, (long long)ny * h.H, ncomp * nz);
-    if (e == cudaSuccess) e = launch_xfft<T>(xa, +1, xg, xsm, st);
+  const long long plane = (long long)nz * ny * H;
+  if (e == cudaSuccess) {
+    if (sign < 0) {
+      e = launch_xfft<T>(xa, -1, xg, xsm, st);
+      if (e == cudaSuccess) e = pass(dy, tw_y, H, nz, plane, (long long)ny * H, ncomp * nz);
+      if (e == cudaSuccess) e = pass(dz, tw_z, (long long)ny * H, ny, plane, H, ncomp * ny);
+    } else {
+      e = pass(dz, tw_z, (long long)ny * H, ny, plane, H, ncomp * ny);
+      if (e == cudaSuccess) e = pass(dy, tw_y, H, nz, plane, (long long)ny * H, ncomp * nz);
+      if (e == cudaSuccess) e = launch_xfft<T>(xa, +1, xg, xsm, st);
+    }
   }
+  const cudaError_t ef = cudaFreeAsync(dtab, st);
+  if (e == cudaSuccess) e = ef;
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  release(&h);
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "fft");
   return RVE_OK;
 }

@@ -106,39 +106,49 @@ cudaError_t launch_adj_tangent_np(const MatDev<T>& M, long long nvox, const T* R
                                                     const T*, T, int, const double*, T*, T*, T*, T*, T*, T*,       \
                                                     const T*, cudaStream_t);
 
-// Threads of a pencil-pass CTA: N1 per line of the chunk, rounded up to whole warps.
-inline int pencil_threads(int n, int HC) { return (pencil_n1(n) * 6 * HC + 31) / 32 * 32; }
+// Threads of a pencil-pass CTA: N1 per line of the chunk (NC components of HC columns),
+// rounded up to whole warps.
+inline int pencil_threads(int n, int HC, int NC = 6) { return (pencil_n1(n) * NC * HC + 31) / 32 * 32; }
 // The pencil kernels serve the component-interleaved passes whose length has a split and
 // whose chunk fits one CTA.
 inline bool pencil_ok(int n, int HC) { return HC <= pencil_max_hc(n); }
 
-template <typename T, int SIGN, int N1, int N2>
+template <typename T, int SIGN, int N1, int N2, int NC>
 static cudaError_t launch_line_pencil(const LineArgs<T>& a, dim3 grid, cudaStream_t s) {
   constexpr int N = N1 * N2;
-  const size_t smem = ((size_t)N + (size_t)6 * a.HC * (N + 1)) * sizeof(C2<T>);
-  cudaError_t e = set_smem<T>((const void*)k_line_pencil<T, SIGN, N1, N2>, smem);
+  const size_t smem = ((size_t)N + (size_t)NC * a.HC * (N + 1)) * sizeof(C2<T>);
+  cudaError_t e = set_smem<T>((const void*)k_line_pencil<T, SIGN, N1, N2, NC>, smem);
   if (e != cudaSuccess) return e;
-  k_line_pencil<T, SIGN, N1, N2><<<grid, pencil_threads(N, a.HC), smem, s>>>(a);
+  k_line_pencil<T, SIGN, N1, N2, NC><<<grid, pencil_threads(N, a.HC, NC), smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <typename T, int N>
+template <typename T, int N, int NC>
 static cudaError_t launch_line_pencil_n(const LineArgs<T>& a, int sign, dim3 grid, cudaStream_t s) {
   constexpr int N1 = PencilSplit<N>::N1, N2 = PencilSplit<N>::N2;
-  return sign < 0 ? launch_line_pencil<T, -1, N1, N2>(a, grid, s) : launch_line_pencil<T, 1, N1, N2>(a, grid, s);
+  return sign < 0 ? launch_line_pencil<T, -1, N1, N2, NC>(a, grid, s)
+                  : launch_line_pencil<T, 1, N1, N2, NC>(a, grid, s);
 }
 
+template <typename T, int NC>
+static cudaError_t launch_line_pencil_any(const LineArgs<T>& a, int sign, dim3 grid, cudaStream_t s) {
+  switch (a.d.n) {
+    case 64: return launch_line_pencil_n<T, 64, NC>(a, sign, grid, s);
+    case 96: return launch_line_pencil_n<T, 96, NC>(a, sign, grid, s);
+    case 128: return launch_line_pencil_n<T, 128, NC>(a, sign, grid, s);
+    case 160: return launch_line_pencil_n<T, 160, NC>(a, sign, grid, s);
+    default: return launch_line_pencil_n<T, 256, NC>(a, sign, grid, s);
+  }
+}
+
+// The register two-step kernel serves a line length with a split when the chunk's lines fit
+// one CTA: the solver's component-interleaved spectra (NC = hstride = 6) and the stand-alone
+// transforms' component-major spectra (NC = hstride = 1).
 template <typename T>
 cudaError_t launch_line(const LineArgs<T>& a, int sign, dim3 grid, size_t smem, cudaStream_t s) {
-  if (a.NC == 6 && a.hstride == 6 && pencil_ok(a.d.n, a.HC)) {
-    switch (a.d.n) {
-      case 64: return launch_line_pencil_n<T, 64>(a, sign, grid, s);
-      case 96: return launch_line_pencil_n<T, 96>(a, sign, grid, s);
-      case 128: return launch_line_pencil_n<T, 128>(a, sign, grid, s);
-      case 160: return launch_line_pencil_n<T, 160>(a, sign, grid, s);
-      default: return launch_line_pencil_n<T, 256>(a, sign, grid, s);
-    }
-  }
+  if (a.NC == 6 && a.hstride == 6 && pencil_ok(a.d.n, a.HC)) return launch_line_pencil_any<T, 6>(a, sign, grid, s);
+  if (a.NC == 1 && a.hstride == 1 && pencil_n1(a.d.n) > 0 && pencil_n1(a.d.n) * a.HC <= kPencilThreads)
+    return launch_line_pencil_any<T, 1>(a, sign, grid, s);
   if (sign < 0) {
     cudaError_t e = set_smem<T>((const void*)k_line<T, -1>, smem);
     if (e != cudaSuccess) return e;

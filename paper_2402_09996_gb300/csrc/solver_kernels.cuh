@@ -567,9 +567,11 @@ __global__ void __launch_bounds__(kLineThreads) k_line(const LineArgs<T> a) {
 // (SP = 6 HC) loads column n1 of line s straight from global memory (rows n1 + N1 n2),
 // transforms it in registers and parks it in shared memory; then each column k2 of a line
 // is transformed and written back to rows k2 + N2 k1.  One barrier between the steps.
-constexpr int kPencilThreads = 384;  // at most N1 * 6 * HC threads per CTA
+constexpr int kPencilThreads = 384;  // at most N1 * NC * HC threads per CTA
 
-template <typename T, int SIGN, int N1, int N2>
+// NC = 6 serves the solver's component-interleaved spectra; NC = 1 (hstride 1) the
+// stand-alone transforms' component-major spectra, one component per CTA.
+template <typename T, int SIGN, int N1, int N2, int NC = 6>
 __device__ __forceinline__ void line_pencil_cta(const LineArgs<T>& a, const Cta& cta) {
   constexpr int N = N1 * N2;
   constexpr int ps = N + 1;  // padded line stride in shared memory
@@ -578,11 +580,11 @@ __device__ __forceinline__ void line_pencil_cta(const LineArgs<T>& a, const Cta&
   C2<T>* buf = tw + N;
   if (a.done && *a.done) return;
   const int tid = threadIdx.x, nthr = blockDim.x;
-  const int SP = 6 * a.HC;
+  const int SP = NC * a.HC;
   const int h0 = (int)cta.bx * a.HC;
-  const int S = 6 * min(a.HC, a.H - h0);
+  const int S = NC * min(a.HC, a.H - h0);
   const int o = (int)cta.by;
-  C2<T>* g = a.spec + (size_t)(o / a.n_o2) * a.A + (size_t)(o % a.n_o2) * a.B + (size_t)h0 * 6;
+  C2<T>* g = a.spec + (size_t)(o / a.n_o2) * a.A + (size_t)(o % a.n_o2) * a.B + (size_t)h0 * NC;
   const size_t gs = (size_t)a.stride;
   const int s = tid % SP, n1 = tid / SP;
   const bool mine = s < S && n1 < N1;  // the CTA has N1 * SP threads rounded up to warps
@@ -606,9 +608,9 @@ __device__ __forceinline__ void line_pencil_cta(const LineArgs<T>& a, const Cta&
   }
 }
 
-template <typename T, int SIGN, int N1, int N2>
+template <typename T, int SIGN, int N1, int N2, int NC>
 __global__ void __launch_bounds__(kPencilThreads) k_line_pencil(const LineArgs<T> a) {
-  line_pencil_cta<T, SIGN, N1, N2>(a, own_grid());
+  line_pencil_cta<T, SIGN, N1, N2, NC>(a, own_grid());
 }
 
 // ---------------------------------------------------------------- z pass + Green ----
@@ -1119,7 +1121,10 @@ __global__ void k_material_point(const MatDev<T> M, long long nvox, const T* __r
   for (int c = 0; c < 6; ++c) sigma[c * n + i] = s[c];
 }
 
-// Stand-alone x transforms of ncomp real lines (FFT entry points; same packing as k_xpass).
+// Stand-alone x transforms of ncomp real lines (FFT entry points): L lines of one
+// component per CTA, each a complex transform of the real line at stride nx + 1 in shared
+// memory (register two-step transforms for the lengths of the PencilSplit table, Stockham
+// passes otherwise); the forward transform keeps kx in [0, nx/2].
 template <typename T>
 struct XFftArgs {
   int nx, H, L, ncomp;
@@ -1134,34 +1139,43 @@ struct XFftArgs {
 template <typename T, int SIGN>
 __global__ void __launch_bounds__(kXThreads) k_xfft(const XFftArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nx = a.nx, xs = nx + 1;
   C2<T>* tw = reinterpret_cast<C2<T>*>(smem_raw);
-  C2<T>* b0 = tw + a.nx;
-  C2<T>* b1 = b0 + (size_t)a.L * a.nx;
-  const int tid = threadIdx.x, nthr = blockDim.x, nx = a.nx, H = a.H, half = nx / 2;
+  C2<T>* b0 = tw + nx;
+  C2<T>* b1 = b0 + (size_t)a.L * xs;
+  const int tid = threadIdx.x, nthr = blockDim.x, H = a.H, half = nx / 2;
   const long long line0 = (long long)blockIdx.x * a.L;
   const int nl = (int)min((long long)a.L, a.NL - line0);
   const int c = blockIdx.y;  // component
   const size_t nvox = (size_t)a.NL * nx;
   for (int i = tid; i < nx; i += nthr) tw[i] = a.tw[i];
   if (SIGN < 0) {
-    for (int t = tid; t < nl * nx; t += nthr) b0[t] = mk<T>(a.real[c * nvox + (size_t)line0 * nx + t], T(0));
+    const T* src = a.real + c * nvox + (size_t)line0 * nx;
+    for (int t = tid; t < nl * nx; t += nthr) {
+      const int l = t / nx, x = t - l * nx;
+      b0[(size_t)l * xs + x] = mk<T>(src[t], T(0));
+    }
     __syncthreads();
-    C2<T>* r = smem_fft<T, -1>(b0, b1, a.dx, nl, nx, tw, tid, nthr);
+    C2<T>* r = xlines_fft<T, -1>(b0, b1, a.dx, nl, xs, tw, tid, nthr);
     for (int w = tid; w < nl * H; w += nthr) {
       const int l = w / H, xi = w - l * H;
-      a.spec[((size_t)c * a.NL + line0 + l) * H + xi] = r[(size_t)l * nx + xi];
+      a.spec[((size_t)c * a.NL + line0 + l) * H + xi] = r[(size_t)l * xs + xi];
     }
   } else {
     for (int w = tid; w < nl * H; w += nthr) {
       const int l = w / H, xi = w - l * H;
       C2<T> A = a.spec[((size_t)c * a.NL + line0 + l) * H + xi];
       if (xi == 0 || xi == half) A.y = T(0);
-      b0[(size_t)l * nx + xi] = A;
-      if (xi > 0 && xi < half) b0[(size_t)l * nx + nx - xi] = mk<T>(A.x, -A.y);
+      b0[(size_t)l * xs + xi] = A;
+      if (xi > 0 && xi < half) b0[(size_t)l * xs + nx - xi] = mk<T>(A.x, -A.y);
     }
     __syncthreads();
-    C2<T>* r = smem_fft<T, +1>(b0, b1, a.dx, nl, nx, tw, tid, nthr);
-    for (int t = tid; t < nl * nx; t += nthr) a.real_out[c * nvox + (size_t)line0 * nx + t] = r[t].x;
+    C2<T>* r = xlines_fft<T, +1>(b0, b1, a.dx, nl, xs, tw, tid, nthr);
+    T* dst = a.real_out + c * nvox + (size_t)line0 * nx;
+    for (int t = tid; t < nl * nx; t += nthr) {
+      const int l = t / nx, x = t - l * nx;
+      dst[t] = r[(size_t)l * xs + x].x;
+    }
   }
 }
 

@@ -328,9 +328,9 @@ rve_status rve_material_point_vjp(int precision, const rve_material* mat, long l
  * (the transform used in the Green-operator step, Sec. 3).  in: ncomp*nvox reals;
  * out: ncomp*nz*ny*(nx/2+1) complex (interleaved re, im); both device pointers.  Lines of
  * 64, 96, 128, 160 and 256 points take register two-step transforms, other lengths
- * Stockham passes.  Each call takes one stream-ordered allocation for its twiddle tables
- * (cudaMallocAsync / cudaFreeAsync on `stream`) and synchronises `stream` before
- * returning. */
+ * Stockham passes.  The twiddle tables are built on the first call for a (device,
+ * precision, length) and kept until the process exits (2 n values each; that first call
+ * allocates and copies synchronously); the call synchronises `stream` before returning. */
 rve_status rve_fft_r2c(int precision, int nx, int ny, int nz, int ncomp, const void* in,
                        void* out, void* stream);
 /* Inverse of rve_fft_r2c, unnormalised (multiply by 1/nvox to invert). The input

@@ -12,6 +12,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <vector>
@@ -2283,6 +2284,40 @@ rve_status rve_material_point_vjp(int precision, const rve_material* mat, long l
 
 }  // extern "C"
 
+// Twiddle tables of the stand-alone transforms, cached per (device, precision, length) like
+// an FFT plan: built on first use (cudaMalloc and a synchronous copy), never modified
+// afterwards, kept until the process exits (2 n values each).
+struct TwiddleEntry {
+  int dev, elem, n;
+  void* ptr;
+};
+std::mutex g_twiddle_mu;
+std::vector<TwiddleEntry> g_twiddles;
+
+template <typename T>
+static cudaError_t cached_twiddles(int n, const C2<T>** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(g_twiddle_mu);
+  for (const TwiddleEntry& t : g_twiddles)
+    if (t.dev == dev && t.elem == (int)sizeof(T) && t.n == n) {
+      *out = (const C2<T>*)t.ptr;
+      return cudaSuccess;
+    }
+  std::vector<T> host(2 * (size_t)n);
+  fill_twiddles<T>(n, host.data());
+  void* p = nullptr;
+  if ((e = cudaMalloc(&p, host.size() * sizeof(T))) != cudaSuccess) return e;
+  if ((e = cudaMemcpy(p, host.data(), host.size() * sizeof(T), cudaMemcpyHostToDevice)) != cudaSuccess) {
+    cudaFree(p);
+    return e;
+  }
+  g_twiddles.push_back(TwiddleEntry{dev, (int)sizeof(T), n, p});
+  *out = (const C2<T>*)p;
+  return cudaSuccess;
+}
+
 template <typename T>
 static rve_status fft_t(int nx, int ny, int nz, int ncomp, const void* in, void* spec, void* out, int sign,
                         cudaStream_t st) {
@@ -2292,22 +2327,11 @@ static rve_status fft_t(int nx, int ny, int nz, int ncomp, const void* in, void*
   factor_radices(nz, &dz);
   const int H = nx / 2 + 1;
   const long long NL = (long long)ny * nz;
-  // the three twiddle tables in one stream-ordered allocation (no device-wide synchronisation)
-  const size_t ntab = 2 * (size_t)(nx + ny + nz);
-  std::vector<T> host(ntab);
-  fill_twiddles<T>(nx, host.data());
-  fill_twiddles<T>(ny, host.data() + 2 * nx);
-  fill_twiddles<T>(nz, host.data() + 2 * (nx + ny));
-  void* dtab = nullptr;
-  cudaError_t e = cudaMallocAsync(&dtab, ntab * sizeof(T), st);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return fail(nullptr, RVE_ERR_OOM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
-  }
-  e = cudaMemcpyAsync(dtab, host.data(), ntab * sizeof(T), cudaMemcpyHostToDevice, st);
-  const C2<T>* tw_x = (const C2<T>*)dtab;
-  const C2<T>* tw_y = tw_x + nx;
-  const C2<T>* tw_z = tw_y + ny;
+  const C2<T> *tw_x = nullptr, *tw_y = nullptr, *tw_z = nullptr;
+  cudaError_t e = cached_twiddles<T>(nx, &tw_x);
+  if (e == cudaSuccess) e = cached_twiddles<T>(ny, &tw_y);
+  if (e == cudaSuccess) e = cached_twiddles<T>(nz, &tw_z);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "fft twiddle tables");
   // x: up to 16 lines of one component per CTA (2048 points at most)
   const int L = std::max(1, std::min(16, 2048 / nx));
   XFftArgs<T> xa{};
@@ -2361,8 +2385,6 @@ static rve_status fft_t(int nx, int ny, int nz, int ncomp, const void* in, void*
       if (e == cudaSuccess) e = launch_xfft<T>(xa, +1, xg, xsm, st);
     }
   }
-  const cudaError_t ef = cudaFreeAsync(dtab, st);
-  if (e == cudaSuccess) e = ef;
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "fft");
   return RVE_OK;

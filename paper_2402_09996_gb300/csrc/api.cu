@@ -2332,8 +2332,8 @@ static rve_status fft_t(int nx, int ny, int nz, int ncomp, const void* in, void*
   if (e == cudaSuccess) e = cached_twiddles<T>(ny, &tw_y);
   if (e == cudaSuccess) e = cached_twiddles<T>(nz, &tw_z);
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "fft twiddle tables");
-  // x: up to 16 lines of one component per CTA (2048 points at most)
-  const int L = std::max(1, std::min(16, 2048 / nx));
+  // x: up to 32 lines (16 packed pairs) of one component per CTA
+  const int L = std::max(1, std::min(32, 4096 / nx));
   XFftArgs<T> xa{};
   xa.nx = nx; xa.H = H; xa.L = L; xa.ncomp = ncomp; xa.NL = NL;
   xa.dx = dx;
@@ -2341,7 +2341,7 @@ static rve_status fft_t(int nx, int ny, int nz, int ncomp, const void* in, void*
   xa.real = (const T*)in;
   xa.spec = (C2<T>*)spec;
   xa.real_out = (T*)out;
-  const size_t xsm = (size_t)(nx + 2 * L * (nx + 1)) * sizeof(C2<T>);
+  const size_t xsm = (size_t)(nx + 2 * ((L + 1) / 2) * (nx + 1)) * sizeof(C2<T>);
   const dim3 xg((unsigned)((NL + L - 1) / L), ncomp);
   const size_t budget = 96 * 1024;
   // y and z: one component's kx chunk per CTA; lengths with a register split take the

@@ -1122,9 +1122,10 @@ __global__ void k_material_point(const MatDev<T> M, long long nvox, const T* __r
 }
 
 // Stand-alone x transforms of ncomp real lines (FFT entry points): L lines of one
-// component per CTA, each a complex transform of the real line at stride nx + 1 in shared
-// memory (register two-step transforms for the lengths of the PencilSplit table, Stockham
-// passes otherwise); the forward transform keeps kx in [0, nx/2].
+// component per CTA, packed in pairs (lines 2q, 2q + 1) as one complex sequence
+// Z = A + iB at stride nx + 1 in shared memory, as in the x pass (register two-step
+// transforms for the lengths of the PencilSplit table, Stockham passes otherwise); the
+// forward transform keeps kx in [0, nx/2].
 template <typename T>
 struct XFftArgs {
   int nx, H, L, ncomp;
@@ -1142,39 +1143,57 @@ __global__ void __launch_bounds__(kXThreads) k_xfft(const XFftArgs<T> a) {
   const int nx = a.nx, xs = nx + 1;
   C2<T>* tw = reinterpret_cast<C2<T>*>(smem_raw);
   C2<T>* b0 = tw + nx;
-  C2<T>* b1 = b0 + (size_t)a.L * xs;
+  C2<T>* b1 = b0 + (size_t)((a.L + 1) / 2) * xs;
   const int tid = threadIdx.x, nthr = blockDim.x, H = a.H, half = nx / 2;
   const long long line0 = (long long)blockIdx.x * a.L;
   const int nl = (int)min((long long)a.L, a.NL - line0);
-  const int c = blockIdx.y;  // component
+  const int nq = (nl + 1) / 2;  // packed sequences (the last one holds one line when nl is odd)
+  const int c = blockIdx.y;     // component
   const size_t nvox = (size_t)a.NL * nx;
   for (int i = tid; i < nx; i += nthr) tw[i] = a.tw[i];
   if (SIGN < 0) {
     const T* src = a.real + c * nvox + (size_t)line0 * nx;
-    for (int t = tid; t < nl * nx; t += nthr) {
-      const int l = t / nx, x = t - l * nx;
-      b0[(size_t)l * xs + x] = mk<T>(src[t], T(0));
+    for (int t = tid; t < nq * nx; t += nthr) {
+      const int q = t / nx, x = t - q * nx;
+      const T re = src[(size_t)(2 * q) * nx + x];
+      const T im = 2 * q + 1 < nl ? src[(size_t)(2 * q + 1) * nx + x] : T(0);
+      b0[(size_t)q * xs + x] = mk<T>(re, im);
     }
     __syncthreads();
-    C2<T>* r = xlines_fft<T, -1>(b0, b1, a.dx, nl, xs, tw, tid, nthr);
+    C2<T>* r = xlines_fft<T, -1>(b0, b1, a.dx, nq, xs, tw, tid, nthr);
+    // unpack: A = (Z_k + conj Z_{n-k}) / 2, B = (Z_k - conj Z_{n-k}) / (2i)
     for (int w = tid; w < nl * H; w += nthr) {
       const int l = w / H, xi = w - l * H;
-      a.spec[((size_t)c * a.NL + line0 + l) * H + xi] = r[(size_t)l * xs + xi];
+      const int q = l >> 1;
+      const C2<T> Z = r[(size_t)q * xs + xi];
+      const C2<T> Zm = r[(size_t)q * xs + (xi == 0 ? 0 : nx - xi)];
+      const C2<T> X = (l & 1) ? mk<T>(T(0.5) * (Z.y + Zm.y), T(-0.5) * (Z.x - Zm.x))
+                              : mk<T>(T(0.5) * (Z.x + Zm.x), T(0.5) * (Z.y - Zm.y));
+      a.spec[((size_t)c * a.NL + line0 + l) * H + xi] = X;
     }
   } else {
-    for (int w = tid; w < nl * H; w += nthr) {
-      const int l = w / H, xi = w - l * H;
-      C2<T> A = a.spec[((size_t)c * a.NL + line0 + l) * H + xi];
-      if (xi == 0 || xi == half) A.y = T(0);
-      b0[(size_t)l * xs + xi] = A;
-      if (xi > 0 && xi < half) b0[(size_t)l * xs + nx - xi] = mk<T>(A.x, -A.y);
+    // pack: Z_k = A_k + i B_k on the Hermitian-extended sequence (imaginary parts of the
+    // kx = 0 and Nyquist entries dropped)
+    for (int w = tid; w < nq * H; w += nthr) {
+      const int q = w / H, xi = w - q * H;
+      const size_t e0 = ((size_t)c * a.NL + line0 + 2 * q) * H + xi;
+      C2<T> A = a.spec[e0];
+      C2<T> B = 2 * q + 1 < nl ? a.spec[e0 + H] : mk<T>(T(0), T(0));
+      if (xi == 0 || xi == half) {
+        A.y = T(0);
+        B.y = T(0);
+      }
+      C2<T>* seq = b0 + (size_t)q * xs;
+      seq[xi] = mk<T>(A.x - B.y, A.y + B.x);
+      if (xi > 0 && xi < half) seq[nx - xi] = mk<T>(A.x + B.y, B.x - A.y);
     }
     __syncthreads();
-    C2<T>* r = xlines_fft<T, +1>(b0, b1, a.dx, nl, xs, tw, tid, nthr);
+    C2<T>* r = xlines_fft<T, +1>(b0, b1, a.dx, nq, xs, tw, tid, nthr);
     T* dst = a.real_out + c * nvox + (size_t)line0 * nx;
     for (int t = tid; t < nl * nx; t += nthr) {
       const int l = t / nx, x = t - l * nx;
-      dst[t] = r[(size_t)l * xs + x].x;
+      const C2<T> z = r[(size_t)(l >> 1) * xs + x];
+      dst[t] = (l & 1) ? z.y : z.x;
     }
   }
 }

@@ -12,7 +12,7 @@ pytestmark = pytest.mark.gpu
 # two-step transforms) in each direction, with kx ranges split into several uneven chunks
 SHAPES = [(4, 4, 4), (16, 16, 16), (6, 10, 12), (12, 20, 30), (5, 9, 16), (8, 6, 96), (4, 4, 160), (3, 128, 4),
           (1, 4, 6), (1, 1, 8), (2, 1, 2), (64, 5, 6), (4, 96, 8), (256, 2, 4), (2, 4, 256), (160, 2, 2),
-          (3, 64, 64), (8, 128, 96), (64, 3, 256)]
+          (3, 64, 64), (8, 128, 96), (64, 3, 256), (3, 5, 128)]
 
 
 @pytest.mark.parametrize("shape", SHAPES)
